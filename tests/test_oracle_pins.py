@@ -1,0 +1,303 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by the mathematics, not by itself.
+
+Each test names the fact it checks.  None of these tests needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cmcg, direct, wave
+from oracle.grid import ABC, DIRICHLET, NEUMANN, Discretization
+from paper_1903_12522_gb300 import workloads as wl
+
+
+def make(w: wl.Workload) -> Discretization:
+    return Discretization(w.n, w.h, w.c, w.omega, w.faces, w.dt_target, order=w.order, mask=w.mask)
+
+
+def wnorm(dz, a):
+    return math.sqrt(float(np.sum(dz.W * dz.act * np.abs(a) ** 2)))
+
+
+def rel_err(dz, a, b):
+    return wnorm(dz, a - b) / wnorm(dz, b)
+
+
+def cosine_mode(n, h, ks):
+    xs = wl.coords(n, h)
+    out = 1.0
+    for a, k in enumerate(ks):
+        out = out * np.cos(math.pi * k * xs[a] / (n[a] * h))
+    return out * np.ones(tuple(m + 1 for m in reversed(n)))
+
+
+def neumann_symbol(order, h, n_a, k):
+    th = math.pi * k / n_a
+    if order == 2:
+        return 4.0 / h ** 2 * math.sin(th / 2.0) ** 2
+    return (2.5 - (8.0 / 3.0) * math.cos(th) + (1.0 / 6.0) * math.cos(2 * th)) / h ** 2
+
+
+def box(n, order=2, c=None, faces=None, omega=3.0, dt_frac=0.3, mask=None):
+    h = 1.0 / max(n)
+    shape = tuple(m + 1 for m in reversed(n))
+    c = np.ones(shape) if c is None else c
+    faces = faces or (ABC,) * 6
+    return Discretization(n, h, c, omega, faces, dt_frac * h, order=order, mask=mask)
+
+
+# ----------------------------------------------------------------------------------------
+# P5a: the stiffness K is W times the Neumann (mirror) Laplacian; every cosine mode
+# prod_a cos(pi k_a j_a / n_a) is an eigenvector with eigenvalue sum_a symbol(k_a).
+# Closed form of the textbook Neumann problem; a wrong boundary weight, a transposed axis or
+# a wrong 4th-order coefficient fails it.
+@pytest.mark.parametrize("n,order", [((6, 9), 2), ((4, 5, 7), 2), ((8, 10), 4), ((6, 7, 5), 4)])
+def test_K_cosine_eigenmodes(n, order):
+    dz = box(n, order=order, faces=(NEUMANN,) * 6)
+    rng = np.random.default_rng(1)
+    for _ in range(12):
+        ks = [int(rng.integers(0, m + 1)) for m in n]
+        phi = cosine_mode(n, dz.h, ks)
+        lam = sum(neumann_symbol(order, dz.h, n[a], ks[a]) for a in range(len(n)))
+        lhs = dz.K(phi)
+        rhs = dz.W * lam * phi
+        scale = max(np.abs(rhs).max(), dz.W.max() / dz.h ** 2)
+        assert np.abs(lhs - rhs).max() <= 1e-12 * scale, (ks, order)
+
+
+# P5b: Riesz map on an obstacle-free box = closed-form cosine synthesis with W-mean zero.
+@pytest.mark.parametrize("n", [(8, 12), (6, 4, 8)])
+def test_riesz_closed_form(n):
+    from oracle.riesz import RieszSolver
+
+    dz = box(n)
+    rng = np.random.default_rng(2)
+    s_true = np.zeros(dz.shape)
+    rhs = np.zeros(dz.shape)
+    for _ in range(6):
+        ks = [int(rng.integers(0, m + 1)) for m in n]
+        if all(k == 0 for k in ks):
+            continue
+        a = rng.standard_normal()
+        phi = cosine_mode(n, dz.h, ks)
+        lam = sum(neumann_symbol(2, dz.h, n[ax], ks[ax]) for ax in range(len(n)))
+        s_true += a * phi
+        rhs += a * lam * dz.W * phi
+    s = RieszSolver(dz).solve(rhs)
+    assert abs(float(np.sum(dz.W * s))) <= 1e-13 * wnorm(dz, s_true)
+    assert rel_err(dz, s, s_true) <= 1e-12
+
+
+def test_riesz_dirichlet_residual():
+    from oracle.riesz import RieszSolver
+
+    w = wl.sphere_3d(n=8)
+    dz = make(w)
+    rhs = np.random.default_rng(3).standard_normal(dz.shape) * dz.act
+    s = RieszSolver(dz).solve(rhs)
+    assert np.all(s[dz.dirichlet] == 0)
+    assert np.linalg.norm(dz.K(s) - rhs) <= 1e-12 * np.linalg.norm(rhs)
+
+
+# ----------------------------------------------------------------------------------------
+# P2: discrete energy identity of leapfrog.  With E^{n+1/2} = 1/2 v^{n+1/2}.M v^{n+1/2}
+# + 1/2 y^n.K y^{n+1}: E^{n+1/2} - E^{n-1/2} = dt v^n.(F^n - B v^n), v^n = (v^{n-1/2}+v^{n+1/2})/2.
+@pytest.mark.parametrize("closed", [True, False])
+def test_energy_identity(closed):
+    n = (10, 8, 6)
+    shape = tuple(m + 1 for m in reversed(n))
+    rng = np.random.default_rng(4)
+    c = 1.0 + 0.3 * rng.random(shape)
+    faces = (NEUMANN,) * 6 if closed else (ABC, ABC, NEUMANN, ABC, ABC, NEUMANN)
+    dz = box(n, c=c, faces=faces, omega=5.0, dt_frac=0.25)
+    F_hat = None if closed else dz.load(rng.standard_normal(shape) + 1j * rng.standard_normal(shape), None)
+    y = rng.standard_normal(shape)
+    v = rng.standard_normal(shape)
+    E_prev = None
+    vh_prev = None
+    y_prev = None
+    E0 = None
+    for n_step in range(dz.N):
+        y_new, v_new, vh = wave.step(dz, y, v, n_step, F_hat)
+        E = 0.5 * np.sum(vh * dz.M * vh) + 0.5 * np.sum(y * dz.K(y_new))
+        if E0 is None:
+            E0 = abs(E)
+        if E_prev is not None:
+            vn = 0.5 * (vh_prev + vh)
+            Fn = dz.forcing(F_hat, n_step)
+            expected = dz.dt * np.sum(vn * (Fn - dz.B * vn))
+            assert abs((E - E_prev) - expected) <= 1e-13 * E0
+        E_prev, vh_prev, y_prev = E, vh, y
+        y, v = y_new, v_new
+    if closed:
+        assert abs(E_prev - E0) <= 1e-13 * dz.N * E0
+
+
+# ----------------------------------------------------------------------------------------
+# P4: <P x, y> = <x, P^T y> for the homogeneous period map.
+@pytest.mark.parametrize("case", ["abc2d", "mixed2d", "sphere3d", "order4"])
+def test_adjoint_dot_product(case):
+    if case == "abc2d":
+        w = wl.gaussian_2d(n=12)
+        dz = make(w)
+    elif case == "mixed2d":
+        n = (10, 13)
+        c = 1.0 + 0.5 * np.random.default_rng(5).random((14, 11))
+        dz = box(n, c=c, faces=(ABC, DIRICHLET, NEUMANN, ABC, ABC, ABC))
+    elif case == "sphere3d":
+        dz = make(wl.sphere_3d(n=8))
+    else:
+        dz = box((6, 7, 8), order=4, dt_frac=0.2)
+    rng = np.random.default_rng(6)
+    x0, x1, y0, y1 = [rng.standard_normal(dz.shape) * dz.act for _ in range(4)]
+    p0, p1 = wave.period(dz, x0, x1)
+    q0, q1 = wave.transposed_period(dz, y0, y1)
+    lhs = np.sum(p0 * y0) + np.sum(p1 * y1)
+    rhs = np.sum(x0 * q0) + np.sum(x1 * q1)
+    scale = math.sqrt(np.sum(p0 ** 2) + np.sum(p1 ** 2)) * math.sqrt(np.sum(y0 ** 2) + np.sum(y1 ** 2))
+    assert abs(lhs - rhs) <= 1e-13 * scale
+
+
+# ----------------------------------------------------------------------------------------
+# P1: CMCG converges to the direct solve of the same (time-)discretisation -- the paper's own
+# verification (Sec. 4.1, tol 1e-14 there).
+def _p1_cases():
+    return ["gauss2d_8", "gauss2d_16", "sphere3d_8", "order4_3d", "mixed2d_hetero"]
+
+
+@pytest.mark.parametrize("case", _p1_cases())
+def test_cmcg_matches_direct(case):
+    if case.startswith("gauss2d"):
+        w = wl.gaussian_2d(n=int(case.split("_")[1]))
+        dz, F = make(w), None
+        F = dz.load(w.f, w.g)
+    elif case == "sphere3d_8":
+        w = wl.sphere_3d(n=8)
+        dz = make(w)
+        F = dz.load(w.f, w.g)
+    elif case == "order4_3d":
+        w = wl.layered_3d(n=8)
+        dz = make(w)
+        F = dz.load(w.f, w.g)
+    else:
+        n = (12, 10)
+        rng = np.random.default_rng(7)
+        c = 1.0 + rng.random((11, 13))
+        dz = box(n, c=c, faces=(ABC, DIRICHLET, NEUMANN, ABC, ABC, ABC), omega=9.0)
+        F = dz.load(rng.standard_normal(dz.shape) + 1j * rng.standard_normal(dz.shape),
+                    rng.standard_normal(dz.shape) + 0j)
+    U = direct.solve(dz, F)
+    res = cmcg.solve(dz, F, tol=1e-13)
+    assert res.rel_residual <= 1e-13
+    assert rel_err(dz, res.u, U) <= 1e-10, case
+    # J decreases along CG and vanishes at the solution (Eq. cost_functional_J is zero
+    # exactly at the periodic solution).
+    J = np.array(res.J_history)
+    assert J[-1] <= 1e-20 * J[0]
+    assert np.all(np.diff(J) <= 1e-12 * J[0])
+
+
+# ----------------------------------------------------------------------------------------
+# P3: manufactured discrete plane wave U = exp(i kt x) with (2c/h) sin(kt h/2) = wt.
+# The time-discrete Helmholtz residual is zero at every interior node (closed form of the
+# 5-point dispersion relation), and CMCG given the boundary residual returns U.
+def test_manufactured_plane_wave():
+    n = (16, 12)
+    dz = box(n, omega=6.0, dt_frac=0.4)
+    kt = 2.0 / dz.h * math.asin(dz.omega_tilde * dz.h / 2.0)
+    U = wl.manufactured_plane_wave_field(n, dz.h, kt)
+    A, ia = direct.helmholtz_matrix(dz)
+    F = np.zeros(dz.size, dtype=np.complex128)
+    F[ia] = A @ U.ravel()[ia]
+    F = F.reshape(dz.shape)
+    interior = np.zeros(dz.shape, dtype=bool)
+    interior[1:-1, 1:-1] = True
+    assert np.abs(F[interior]).max() <= 1e-12 * np.abs(F).max()
+    res = cmcg.solve(dz, F, tol=1e-13)
+    assert rel_err(dz, res.u, U) <= 1e-10
+
+
+# ----------------------------------------------------------------------------------------
+# P6: the compatibility-condition shift is real (Theorem 1: lambda is a real constant), and
+# the fundamental-frequency filter (Sec. 2.2, rectangle rule over one period, exact for the
+# discrete time-harmonic solution) removes it to the same answer.
+def test_lambda_real_and_filter_agrees():
+    w = wl.gaussian_2d(n=16)
+    c = 1.0 + 0.4 * np.random.default_rng(8).random(w.c.shape)
+    dz = Discretization(w.n, w.h, c, w.omega, w.faces, w.dt_target)
+    F = dz.load(w.f, None)
+    res = cmcg.solve(dz, F, tol=1e-13)
+    lam = res.lam
+    assert abs(lam) > 1e-8
+    assert abs(lam.imag) <= 1e-10 * abs(lam)
+    y, v = res.v0.copy(), res.v1.copy()
+    acc = np.zeros(dz.shape, dtype=np.complex128)
+    for n_step in range(dz.N):
+        t = n_step * dz.dt
+        acc += (y + 1j / dz.omega_hat * v) * np.exp(1j * dz.omega * t)
+        y, v, _ = wave.step(dz, y, v, n_step, F)
+    u_filter = acc / dz.N
+    assert rel_err(dz, u_filter, res.u) <= 1e-10
+
+
+# ----------------------------------------------------------------------------------------
+# P8: continuum check.  With g_S = (d/dn - i k) u_in and no obstacle, u = u_in exactly solves
+# the Helmholtz problem of Eq. HE; the discrete solution converges at second order in h
+# (dt proportional to h).  Checks M, B, A at faces/corners, the load and the sign conventions.
+@pytest.mark.parametrize("dim", [2, 3])
+def test_plane_wave_continuum_order(dim):
+    errs = []
+    grids = [8, 16, 32] if dim == 3 else [16, 32, 64]
+    theta = math.radians(135.0)
+    dvec = (math.cos(theta), math.sin(theta)) if dim == 2 else (0.5, 0.0, math.sqrt(3.0) / 2.0)
+    omega = 2.0 * math.pi * (1.0 if dim == 3 else 2.0)
+    for m in grids:
+        n = (m,) * dim
+        h = 1.0 / m
+        faces = (ABC,) * 6
+        dz = Discretization(n, h, np.ones(tuple(k + 1 for k in n)), omega, faces, 0.4 * h)
+        g = wl.plane_wave_boundary_datum(n, h, omega, 1.0, dvec, faces)
+        U = direct.solve(dz, dz.load(None, g))
+        xs = wl.coords(n, h)
+        uin = np.exp(1j * omega * sum(x * dd for x, dd in zip(xs, dvec))) * np.ones(dz.shape)
+        errs.append(rel_err(dz, U, uin))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert abs(rates[-1] - 2.0) <= 0.2, (errs, rates)
+
+
+# P9: the paper's recovery u = v0 + (i/omega) v1 differs from the discrete-exact one by
+# O((omega dt)^2) -- the Sec. 4.1 observation that CMCG approaches the direct solve as dt -> 0.
+def test_paper_recovery_converges_second_order():
+    w = wl.gaussian_2d(n=16)
+    errs = []
+    for frac in (0.4, 0.2, 0.1):
+        dz = Discretization(w.n, w.h, w.c, w.omega, w.faces, frac * w.h)
+        U = direct.solve(dz, dz.load(w.f, None))
+        v0, v1 = direct.periodic_state(dz, U)
+        u_paper = v0 + 1j * v1 / dz.omega
+        errs.append(rel_err(dz, u_paper, U))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r - 2.0) <= 0.2 for r in rates), rates
+
+
+# ----------------------------------------------------------------------------------------
+def test_period_rounding_and_cfl():
+    # T/dt is an integer: config with omega = 16 pi, dt = h/2, h = 1/128 -> N = 32.
+    w = wl.gaussian_2d(n=128)
+    dz = Discretization(w.n, w.h, w.c, w.omega, w.faces, w.dt_target)
+    assert dz.N == 32 and abs(dz.N * dz.dt - 2 * math.pi / w.omega) < 1e-15
+    # 3D sphere recipe: T = 14.2857 h, dt_target = 0.4 h -> N = 36 (independent of n).
+    w3 = wl.sphere_3d(n=8)
+    assert make(w3).N == 36
+    with pytest.raises(ValueError):
+        box((8, 8), dt_frac=0.8)
+
+
+def test_oracle_is_not_imported_by_the_package():
+    import pathlib
+
+    pkg = pathlib.Path(__file__).resolve().parents[1] / "paper_1903_12522_gb300"
+    for p in pkg.rglob("*.py"):
+        src = p.read_text()
+        assert "import oracle" not in src and "from oracle" not in src, p
