@@ -1,0 +1,185 @@
+/*
+ * cmcg.h -- C ABI of the GB300 controllability conjugate-gradient (CMCG) Helmholtz solver.
+ *
+ * The solver computes the time-harmonic field u of the Helmholtz problem of Sec. 2.1
+ * (Eq. HE: -Lap u - k^2 u = f in Omega, du/dn - i k u = g_S on the absorbing faces,
+ * du/dn = 0 on Neumann faces, u = 0 on Dirichlet faces and obstacle nodes, k = omega/c)
+ * by the CMCG Algorithm of Sec. 2.3: conjugate gradients on the initial data (v0, v1) of
+ * the wave equation of Eq. WE so that its solution is T-periodic, T = 2 pi / omega.
+ *
+ * Discretisation (fixed by this library, identical for every entry point):
+ *   - nodes x_j = j h, j in {0..n_x} x {0..n_y} (x {0..n_z}); node index
+ *     j = ix + (n_x+1) (iy + (n_y+1) iz), x fastest.  N_p = prod (n_a + 1).
+ *   - mass-lumped vertex-centred finite differences: lumped volume W_j = h^d prod_a w(j_a),
+ *     w = 1/2 on the two end nodes of an axis, 1 elsewhere; stiffness K = W (-Lap_h) with
+ *     mirror (Neumann) ghosts, 2nd order (5/7-point) or 4th order (9/13-point, even
+ *     reflection); M = diag(W/c^2); absorbing faces add B = diag(A/c), A = lumped face area.
+ *   - leapfrog in time with the absorbing term centred (Sec. 4.4.1: explicit, T/dt an
+ *     integer): N = ceil(T/dt_target - 1e-9) steps of dt = T/N per period.
+ *   - discrete time-harmonic solution: (K - wt^2 M - i wh B) U = W f + A g with
+ *     wt = (2/dt) sin(omega dt/2), wh = sin(omega dt)/dt; returned U = v0 + i v1 / wh
+ *     after removing the constant shift lambda of Theorem 1 when there is no Dirichlet
+ *     node (compatibility condition of Sec. 2.1, discrete form).
+ *
+ * Memory: every array argument is a DEVICE pointer to caller-owned memory unless its name
+ * ends in _host.  Real fields are double[N_p]; complex fields are interleaved (re, im)
+ * double[2 N_p] (C99 double _Complex layout).  The library allocates no device memory
+ * itself: all state lives in the caller-allocated workspace passed to cmcg_create (size
+ * from cmcg_workspace_size).  Work is enqueued on the handle's stream; the calls return
+ * after the stream has finished the call's work.  A handle is not thread-safe; use one
+ * handle per stream.
+ *
+ * Errors: every int-returning call returns CMCG_OK (0), CMCG_NOT_CONVERGED (1, output holds
+ * the last iterate) or a negative error code; cmcg_status_string names it.  A call that
+ * fails leaves its outputs unspecified and the handle usable unless the code is
+ * CMCG_ERR_CUDA.
+ */
+#ifndef CMCG_H
+#define CMCG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define CMCG_OK 0
+#define CMCG_NOT_CONVERGED 1
+#define CMCG_ERR_INVALID_ARG (-1)
+#define CMCG_ERR_CFL (-2)
+#define CMCG_ERR_WORKSPACE (-3)
+#define CMCG_ERR_UNSUPPORTED (-4)
+#define CMCG_ERR_CUDA (-5)
+#define CMCG_ERR_DIVERGED (-6)
+
+/* ---- boundary codes (face order -x, +x, -y, +y, -z, +z) --------------------------- */
+#define CMCG_BC_ABC 0       /* first-order absorbing (impedance) face, Eq. HE_ABC      */
+#define CMCG_BC_NEUMANN 1   /* homogeneous Neumann face, Eq. HE_NBC                      */
+#define CMCG_BC_DIRICHLET 2 /* homogeneous Dirichlet face, Eq. HE_DBC                    */
+
+/* ---- option flags ------------------------------------------------------------------ */
+#define CMCG_FLAG_HOST_IO 1 /* reserve a staging buffer in the workspace for cmcg_solve_host */
+
+/* ---- precision of the wave stepping ------------------------------------------------ */
+#define CMCG_FP64 0  /* every operation in FP64                                            */
+#define CMCG_FP32 1  /* leapfrog fields and stencil arithmetic in FP32; CG vectors, inner
+                        products, energy functional and Riesz solve in FP64               */
+#define CMCG_MIXED 2 /* CMCG_FP32 inner CG inside an FP64 defect-correction loop whose
+                        residual (gradient of J) is evaluated with FP64 stepping         */
+
+typedef struct cmcg_handle cmcg_handle;
+
+typedef struct {
+    int dim;      /* 2 or 3                                                              */
+    int n[3];     /* intervals per axis (n[2] ignored in 2D); nodes per axis = n + 1      */
+    double h;     /* grid spacing, equal on all axes                                      */
+    int order;    /* spatial order of the Laplacian: 2 or 4                               */
+} cmcg_grid;
+
+typedef struct {
+    unsigned char face[6];               /* CMCG_BC_* per face (-x,+x,-y,+y,-z,+z)        */
+    const unsigned char* dirichlet_mask; /* device uint8[N_p], 1 = sound-soft obstacle
+                                            node (u = 0); NULL = none.  Read at create.  */
+} cmcg_bc;
+
+typedef struct {
+    int precision;          /* CMCG_FP64 / CMCG_FP32 / CMCG_MIXED                        */
+    double dt;              /* target time step; 0 = 0.5 h / (sqrt(d) c_max)             */
+    int max_iter;           /* CG iteration cap (0 = 10000)                                */
+    double riesz_tol;       /* relative residual of the Riesz (Laplace) solve (0 = 1e-12) */
+    int riesz_max_iter;     /* PCG iteration cap of the Riesz solve (0 = 60)              */
+    double inner_tol;       /* CMCG_MIXED: relative tolerance of each inner FP32 solve
+                               (0 = 1e-3)                                                 */
+    int flags;              /* CMCG_FLAG_* bits; other bits must be 0                      */
+} cmcg_options;
+
+typedef struct {
+    int iterations;          /* CG iterations (CMCG_MIXED: summed over inner solves)       */
+    int outer_iterations;    /* CMCG_MIXED defect-correction rounds (else 0)              */
+    int periods;             /* wave periods integrated (forward + adjoint)               */
+    int riesz_iterations;    /* PCG iterations summed over all Riesz solves               */
+    int steps_per_period;    /* N                                                         */
+    double dt;               /* T / N                                                     */
+    double omega_tilde;      /* (2/dt) sin(omega dt / 2)                                  */
+    double omega_hat;        /* sin(omega dt) / dt                                        */
+    double rel_residual;     /* sqrt(||r||_E^2 / ||r0||_E^2) at exit (Step 5.8)             */
+    double J0;               /* J at the initial guess (Eq. cost_functional_J)            */
+    double J_final;          /* J at the returned iterate (one extra forward period)      */
+    double lambda_re;        /* removed constant shift (0 if Dirichlet nodes exist)       */
+    double lambda_im;
+    long long point_updates; /* grid-point leapfrog updates performed                      */
+    double seconds;          /* wall time of the call                                     */
+    long long kernel_launches; /* CUDA kernels this library launched during the call       */
+} cmcg_stats;
+
+typedef struct {
+    int steps_per_period;    /* N                                                         */
+    double dt, omega_tilde, omega_hat;
+    long long num_nodes;     /* N_p                                                       */
+    int mg_levels;           /* levels of the multigrid preconditioner of the Riesz solve */
+    int has_dirichlet;       /* 1 if any node is Dirichlet                                */
+} cmcg_info;
+
+/* Bytes of device workspace cmcg_create needs for this grid and options (0 on invalid
+ * arguments).  Exact: serving code admits solves by this number. */
+size_t cmcg_workspace_size(const cmcg_grid* grid, const cmcg_options* opts);
+
+/* Build a solver.  c: device double[N_p] wave speed c(x) > 0 (copied).  omega > 0: angular
+ * frequency (T = 2 pi / omega).  workspace: device memory of ws_bytes >= cmcg_workspace_size,
+ * 256-byte aligned, owned by the caller and kept alive until cmcg_destroy.  stream: a
+ * cudaStream_t (NULL = default stream).  Validates sizes and the CFL condition
+ * dt^2 c_max^2 rho < 4 (rho = 4d/h^2, 2nd order; 16d/(3h^2), 4th order) and returns
+ * CMCG_ERR_CFL if violated.  4th order with Dirichlet nodes is CMCG_ERR_UNSUPPORTED.
+ * Sec. 2.1 (problem), Sec. 4.4.1 (leapfrog, mass lumping, T/dt integer). */
+int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg_bc* bc,
+                const cmcg_options* opts, void* workspace, size_t ws_bytes, void* stream,
+                cmcg_handle** out);
+
+int cmcg_destroy(cmcg_handle* h);
+
+int cmcg_get_info(const cmcg_handle* h, cmcg_info* info);
+
+/* One period of the forced wave equation (Eq. WE) by leapfrog: from y(0) = u0, y_t(0) = v0
+ * to (uT, vT) = (y(T), y_t(T)).  f: interior source amplitude, g: boundary datum g_S on
+ * absorbing nodes (complex double[N_p] each, NULL = 0); the forcing is
+ * Re((W f + A g) exp(-i omega t)).  At edge and corner nodes g is the mean of the faces'
+ * values.  Dirichlet entries of the inputs are ignored and zero in the outputs.  Runs in the
+ * handle's stepping precision (CMCG_MIXED steps in FP64 here).  Outputs must not alias
+ * inputs. */
+int cmcg_wave_period(cmcg_handle* h, const double* u0, const double* v0, const double* f,
+                     const double* g, double* uT, double* vT);
+
+/* Transpose of the homogeneous period map, P^T (a, b): the discrete backward (adjoint) wave
+ * equation of Eq. AWE that yields J' (Eq. J1_derivative_final).  a, b: dual vectors (the
+ * cotangents of y(T) and y_t(T)); q0, q1: cotangents of y(0), y_t(0).  Satisfies
+ * <P x, (a,b)> = <x, (q0,q1)> to rounding. */
+int cmcg_adjoint_period(cmcg_handle* h, const double* a, const double* b, double* q0, double* q1);
+
+/* Riesz map of Eq. CMCG_PRECONDITIONIER for the v0 component: s = K^+ rhs (K = W (-Lap_h),
+ * Dirichlet rows removed).  Without Dirichlet nodes K is singular; rhs is projected onto
+ * range(K) and s has W-weighted mean zero.  FP64 flexible PCG preconditioned by a geometric
+ * multigrid V-cycle.  Returns CMCG_NOT_CONVERGED if riesz_tol is not met. */
+int cmcg_riesz(cmcg_handle* h, const double* rhs, double* s);
+
+/* Full CMCG solve (Sec. 2.3, steps (1)-(6)).  f, g as in cmcg_wave_period.  tol: Step 5.8
+ * relative E-norm residual.  u: device complex double[N_p] output U.  stats: host, nullable.
+ * Returns CMCG_OK, CMCG_NOT_CONVERGED (max_iter reached, u holds the last iterate) or an
+ * error (CMCG_ERR_DIVERGED if a CG scalar becomes NaN/Inf or non-positive). */
+int cmcg_solve(cmcg_handle* h, const double* f, const double* g, double tol, double* u,
+               cmcg_stats* stats);
+
+/* cmcg_solve with HOST buffers: f_host, g_host (nullable) and u_host are host complex
+ * double[N_p] arrays (pinned memory gives full copy speed).  Copies the inputs into the
+ * workspace, solves, copies U back; all copies are on the handle's stream.  Needs a handle
+ * created with CMCG_FLAG_HOST_IO (else CMCG_ERR_INVALID_ARG). */
+int cmcg_solve_host(cmcg_handle* h, const double* f_host, const double* g_host, double tol,
+                    double* u_host, cmcg_stats* stats);
+
+const char* cmcg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMCG_H */

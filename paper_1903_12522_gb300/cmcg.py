@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libcmcg (C ABI in include/cmcg.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.  Torch is used
+for device memory and streams.  The functions keep the C names (cmcg_create, cmcg_wave_period,
+cmcg_solve, ...); ``Solver`` bundles a handle with its workspace.
+
+Loading fails loudly (``RuntimeError``) when libcmcg.so has not been built; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcmcg.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_CFL, ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_CUDA, ERR_DIVERGED = -1, -2, -3, -4, -5, -6
+BC_ABC, BC_NEUMANN, BC_DIRICHLET = 0, 1, 2
+FP64, FP32, MIXED = 0, 1, 2
+FLAG_HOST_IO = 1
+
+EXPORTED = (
+    "cmcg_workspace_size", "cmcg_create", "cmcg_destroy", "cmcg_get_info", "cmcg_wave_period",
+    "cmcg_adjoint_period", "cmcg_riesz", "cmcg_solve", "cmcg_solve_host", "cmcg_status_string",
+)
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double), ("order", C.c_int)]
+
+
+class BC(C.Structure):
+    _fields_ = [("face", C.c_ubyte * 6), ("dirichlet_mask", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("dt", C.c_double), ("max_iter", C.c_int), ("riesz_tol", C.c_double),
+                ("riesz_max_iter", C.c_int), ("inner_tol", C.c_double), ("flags", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer_iterations", C.c_int), ("periods", C.c_int),
+                ("riesz_iterations", C.c_int), ("steps_per_period", C.c_int), ("dt", C.c_double),
+                ("omega_tilde", C.c_double), ("omega_hat", C.c_double), ("rel_residual", C.c_double),
+                ("J0", C.c_double), ("J_final", C.c_double), ("lambda_re", C.c_double),
+                ("lambda_im", C.c_double), ("point_updates", C.c_longlong), ("seconds", C.c_double),
+                ("kernel_launches", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(C.Structure):
+    _fields_ = [("steps_per_period", C.c_int), ("dt", C.c_double), ("omega_tilde", C.c_double),
+                ("omega_hat", C.c_double), ("num_nodes", C.c_longlong), ("mg_levels", C.c_int),
+                ("has_dirichlet", C.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcmcg.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcmcg.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    lib.cmcg_workspace_size.argtypes = [C.POINTER(Grid), C.POINTER(Options)]
+    lib.cmcg_workspace_size.restype = S
+    lib.cmcg_create.argtypes = [C.POINTER(Grid), P, D, C.POINTER(BC), C.POINTER(Options), P, S, P, C.POINTER(P)]
+    lib.cmcg_create.restype = I
+    lib.cmcg_destroy.argtypes = [P]
+    lib.cmcg_destroy.restype = I
+    lib.cmcg_get_info.argtypes = [P, C.POINTER(Info)]
+    lib.cmcg_get_info.restype = I
+    lib.cmcg_wave_period.argtypes = [P, P, P, P, P, P, P]
+    lib.cmcg_wave_period.restype = I
+    lib.cmcg_adjoint_period.argtypes = [P, P, P, P, P]
+    lib.cmcg_adjoint_period.restype = I
+    lib.cmcg_riesz.argtypes = [P, P, P]
+    lib.cmcg_riesz.restype = I
+    lib.cmcg_solve.argtypes = [P, P, P, D, P, C.POINTER(Stats)]
+    lib.cmcg_solve.restype = I
+    lib.cmcg_solve_host.argtypes = [P, P, P, D, P, C.POINTER(Stats)]
+    lib.cmcg_solve_host.restype = I
+    lib.cmcg_status_string.argtypes = [I]
+    lib.cmcg_status_string.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class CMCGError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = load().cmcg_status_string(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+def _check(code: int, where: str, allow_not_converged: bool = False) -> int:
+    if code == OK or (allow_not_converged and code == NOT_CONVERGED):
+        return code
+    raise CMCGError(code, where)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def make_grid(n, h, order=2) -> Grid:
+    g = Grid()
+    g.dim = len(n)
+    for a in range(3):
+        g.n[a] = int(n[a]) if a < len(n) else 0
+    g.h = float(h)
+    g.order = int(order)
+    return g
+
+
+def make_options(precision=FP64, dt=0.0, max_iter=0, riesz_tol=0.0, riesz_max_iter=0, inner_tol=0.0, flags=0):
+    o = Options()
+    o.precision, o.dt, o.max_iter = int(precision), float(dt), int(max_iter)
+    o.riesz_tol, o.riesz_max_iter, o.inner_tol, o.flags = float(riesz_tol), int(riesz_max_iter), float(inner_tol), int(flags)
+    return o
+
+
+# ---- C-named entry points -----------------------------------------------------------------
+def cmcg_workspace_size(grid: Grid, opts: Options) -> int:
+    return int(load().cmcg_workspace_size(C.byref(grid), C.byref(opts)))
+
+
+def cmcg_create(grid: Grid, c, omega: float, bc: BC, opts: Options, workspace, stream) -> C.c_void_p:
+    h = C.c_void_p()
+    code = load().cmcg_create(C.byref(grid), _ptr(c), float(omega), C.byref(bc), C.byref(opts), _ptr(workspace),
+                              int(workspace.numel() * workspace.element_size()), stream, C.byref(h))
+    _check(code, "cmcg_create")
+    return h
+
+
+def cmcg_destroy(h) -> None:
+    _check(load().cmcg_destroy(h), "cmcg_destroy")
+
+
+def cmcg_get_info(h) -> dict:
+    info = Info()
+    _check(load().cmcg_get_info(h, C.byref(info)), "cmcg_get_info")
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def cmcg_wave_period(h, u0, v0, f, g, uT, vT) -> None:
+    _check(load().cmcg_wave_period(h, _ptr(u0), _ptr(v0), _ptr(f), _ptr(g), _ptr(uT), _ptr(vT)), "cmcg_wave_period")
+
+
+def cmcg_adjoint_period(h, a, b, q0, q1) -> None:
+    _check(load().cmcg_adjoint_period(h, _ptr(a), _ptr(b), _ptr(q0), _ptr(q1)), "cmcg_adjoint_period")
+
+
+def cmcg_riesz(h, rhs, s) -> int:
+    return _check(load().cmcg_riesz(h, _ptr(rhs), _ptr(s)), "cmcg_riesz", allow_not_converged=True)
+
+
+def cmcg_solve(h, f, g, tol, u, stats: Optional[Stats] = None) -> int:
+    st = stats if stats is not None else Stats()
+    return _check(load().cmcg_solve(h, _ptr(f), _ptr(g), float(tol), _ptr(u), C.byref(st)), "cmcg_solve",
+                  allow_not_converged=True)
+
+
+def cmcg_solve_host(h, f_host: Optional[np.ndarray], g_host: Optional[np.ndarray], tol, u_host: np.ndarray,
+                    stats: Optional[Stats] = None) -> int:
+    def hp(a):
+        if a is None:
+            return None
+        assert a.dtype == np.complex128 and a.flags.c_contiguous
+        return a.ctypes.data
+    st = stats if stats is not None else Stats()
+    return _check(load().cmcg_solve_host(h, hp(f_host), hp(g_host), float(tol), hp(u_host), C.byref(st)),
+                  "cmcg_solve_host", allow_not_converged=True)
+
+
+def cmcg_status_string(code: int) -> str:
+    return load().cmcg_status_string(int(code)).decode()
+
+
+# ---- convenience wrapper ------------------------------------------------------------------
+class Solver:
+    """A handle plus its caller-owned workspace (torch uint8 tensor on the device)."""
+
+    def __init__(self, n, h, c, omega, faces, mask=None, order=2, precision=FP64, dt=0.0, max_iter=0,
+                 riesz_tol=0.0, riesz_max_iter=0, inner_tol=0.0, flags=0, device="cuda", stream=None):
+        import torch
+
+        load()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n = tuple(int(m) for m in n)
+        self.shape = tuple(m + 1 for m in reversed(self.n))
+        self.grid = make_grid(self.n, h, order)
+        self.opts = make_options(precision, dt, max_iter, riesz_tol, riesz_max_iter, inner_tol, flags)
+        nbytes = cmcg_workspace_size(self.grid, self.opts)
+        if nbytes == 0:
+            raise CMCGError(ERR_INVALID_ARG, "cmcg_workspace_size")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.c = self._dev(c, torch.float64)
+        self.bc = BC()
+        for f in range(6):
+            self.bc.face[f] = int(faces[f])
+        self.mask = None if mask is None else self._dev(mask, torch.uint8)
+        self.bc.dirichlet_mask = _ptr(self.mask)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.handle = cmcg_create(self.grid, self.c, omega, self.bc, self.opts, self.workspace, self.stream.cuda_stream)
+        self.info = cmcg_get_info(self.handle)
+
+    def _dev(self, a, dtype):
+        torch = self.torch
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            return a.to(device=self.device, dtype=dtype).contiguous().reshape(-1)
+        return torch.as_tensor(np.ascontiguousarray(a)).to(device=self.device, dtype=dtype).reshape(-1)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            cmcg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def wave_period(self, u0, v0, f=None, g=None):
+        torch = self.torch
+        u0, v0 = self._dev(u0, torch.float64), self._dev(v0, torch.float64)
+        f, g = self._dev(f, torch.complex128), self._dev(g, torch.complex128)
+        uT, vT = torch.empty_like(u0), torch.empty_like(v0)
+        cmcg_wave_period(self.handle, u0, v0, f, g, uT, vT)
+        return uT.reshape(self.shape), vT.reshape(self.shape)
+
+    def adjoint_period(self, a, b):
+        torch = self.torch
+        a, b = self._dev(a, torch.float64), self._dev(b, torch.float64)
+        q0, q1 = torch.empty_like(a), torch.empty_like(b)
+        cmcg_adjoint_period(self.handle, a, b, q0, q1)
+        return q0.reshape(self.shape), q1.reshape(self.shape)
+
+    def riesz(self, rhs):
+        torch = self.torch
+        rhs = self._dev(rhs, torch.float64)
+        s = torch.empty_like(rhs)
+        code = cmcg_riesz(self.handle, rhs, s)
+        return s.reshape(self.shape), code
+
+    def solve(self, f=None, g=None, tol=1e-6):
+        torch = self.torch
+        f, g = self._dev(f, torch.complex128), self._dev(g, torch.complex128)
+        u = torch.empty(int(np.prod(self.shape)), dtype=torch.complex128, device=self.device)
+        st = Stats()
+        code = cmcg_solve(self.handle, f, g, tol, u, st)
+        out = st.as_dict()
+        out["status"] = code
+        return u.reshape(self.shape), out

@@ -1,0 +1,695 @@
+// Host runtime and C ABI of libcmcg: handle, workspace carve-up, the forward / adjoint period
+// drivers, the Riesz (MG-PCG) driver, and the CMCG Algorithm of Sec. 2.3 with its CG
+// recurrences on the device (the host reads one convergence word per iteration).
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <type_traits>
+
+#include "cmcg.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace cmcg;
+
+namespace cmcg {
+static std::atomic<long long> g_launches{0};
+void note_launch(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace cmcg
+
+namespace {
+
+constexpr int kMaxLevels = 16;
+constexpr int kZcStep3D = 16;  // z-planes per thread in the leapfrog step (3D)
+constexpr int kZcEnds = 8;     // z-planes per thread in the period endpoint kernels
+constexpr double kPi = 3.14159265358979323846;
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+struct cmcg_handle {
+    Geom g{};
+    int order = 2;
+    cmcg_options opt{};
+    cudaStream_t st = nullptr;
+    double omega = 0, T = 0, dt = 0, wt = 0, wh = 0, volume = 0;
+    int N = 0;
+    bool has_dir = false;
+    double sumM = 0, sumB = 0, sumW = 0;
+    // coefficients
+    double *kap64 = nullptr, *mass = nullptr, *S = nullptr;
+    float* kap32 = nullptr;
+    unsigned char* mask = nullptr;
+    // wave buffers (sized for double; FP32 stepping uses the first half) + FP64 temp
+    void *ya = nullptr, *yb = nullptr;
+    double* tmp = nullptr;
+    // CG state
+    double *w0, *w1, *r0, *r1, *rh0, *rh1, *d0, *d1, *gh0, *gh1, *gt0, *gt1, *z0, *z1;
+    double *wo0 = nullptr, *wo1 = nullptr;  // CMCG_MIXED outer iterate
+    // Riesz PCG
+    double *pr, *pp, *pAp, *pzd;
+    MGLevel lv[kMaxLevels];
+    int nlev = 0;
+    // host staging
+    double* stage = nullptr;
+    // reductions
+    double* partials = nullptr;
+    unsigned* tickets = nullptr;
+    double* sc = nullptr;
+    double* hsc = nullptr;  // pinned host mirror of sc
+    // counters of the current call
+    long long riesz_iters = 0;
+    long long periods = 0;
+    Red red() const { return Red{partials, tickets, sc}; }
+};
+
+namespace {
+
+bool valid_grid(const cmcg_grid* gr) {
+    if (!gr) return false;
+    if (gr->dim != 2 && gr->dim != 3) return false;
+    if (!(gr->h > 0) || !isfinite(gr->h)) return false;
+    if (gr->order != 2 && gr->order != 4) return false;
+    for (int a = 0; a < gr->dim; ++a)
+        if (gr->n[a] < 2 || gr->n[a] > (1 << 20)) return false;
+    long long np = 1;
+    for (int a = 0; a < gr->dim; ++a) np *= (long long)(gr->n[a] + 1);
+    return np < (1ll << 31);
+}
+
+Geom make_geom(const cmcg_grid* gr, unsigned abc) {
+    Geom g{};
+    g.dim = gr->dim;
+    g.nx = gr->n[0];
+    g.ny = gr->n[1];
+    g.nz = gr->dim == 3 ? gr->n[2] : 0;
+    g.sx = g.nx + 1;
+    g.sy = g.ny + 1;
+    g.sz = g.nz + 1;
+    g.np = (long long)g.sx * g.sy * g.sz;
+    g.h = gr->h;
+    g.abc = abc;
+    return g;
+}
+
+void fill_defaults(cmcg_options* o) {
+    if (o->max_iter <= 0) o->max_iter = 10000;
+    if (!(o->riesz_tol > 0)) o->riesz_tol = 1e-12;
+    if (o->riesz_max_iter <= 0) o->riesz_max_iter = 60;
+    if (!(o->inner_tol > 0)) o->inner_tol = 1e-3;
+}
+
+// Multigrid level geometries: halve every axis while all are even and stay >= 2.
+int mg_geometries(const Geom& fine, Geom* out) {
+    int n = 0;
+    out[n++] = fine;
+    while (n < kMaxLevels) {
+        const Geom& p = out[n - 1];
+        const bool even = (p.nx % 2 == 0) && (p.ny % 2 == 0) && (p.dim == 2 || p.nz % 2 == 0);
+        const bool big = p.nx / 2 >= 2 && p.ny / 2 >= 2 && (p.dim == 2 || p.nz / 2 >= 2);
+        if (!even || !big || p.np <= 64) break;
+        Geom c = p;
+        c.nx = p.nx / 2;
+        c.ny = p.ny / 2;
+        c.nz = p.dim == 3 ? p.nz / 2 : 0;
+        c.sx = c.nx + 1;
+        c.sy = c.ny + 1;
+        c.sz = c.nz + 1;
+        c.np = (long long)c.sx * c.sy * c.sz;
+        c.h = p.h * 2.0;
+        out[n++] = c;
+    }
+    return n;
+}
+
+// Workspace layout.  The same function sizes (base == nullptr) and carves the workspace.
+size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) {
+    Carver c{base};
+    const size_t np = (size_t)g.np;
+    H->kap64 = c.take<double>(np);
+    H->mass = c.take<double>(np);
+    H->mask = c.take<unsigned char>(np);
+    H->kap32 = o.precision != CMCG_FP64 ? c.take<float>(np) : nullptr;
+    H->S = c.take<double>(2 * np);
+    H->ya = c.take<double>(np);
+    H->yb = c.take<double>(np);
+    H->tmp = c.take<double>(np);
+    double** cg[] = {&H->w0, &H->w1, &H->r0, &H->r1, &H->rh0, &H->rh1, &H->d0,
+                     &H->d1, &H->gh0, &H->gh1, &H->gt0, &H->gt1, &H->z0, &H->z1};
+    for (double** p : cg) *p = c.take<double>(np);
+    if (o.precision == CMCG_MIXED) {
+        H->wo0 = c.take<double>(np);
+        H->wo1 = c.take<double>(np);
+    }
+    H->pr = c.take<double>(np);
+    H->pp = c.take<double>(np);
+    H->pAp = c.take<double>(np);
+    H->pzd = c.take<double>(np);
+    Geom lg[kMaxLevels];
+    H->nlev = mg_geometries(g, lg);
+    for (int l = 0; l < H->nlev; ++l) {
+        MGLevel& L = H->lv[l];
+        L.g = lg[l];
+        const size_t n = (size_t)lg[l].np;
+        L.mask = l == 0 ? H->mask : c.take<unsigned char>(n);
+        L.x = c.take<float>(n);
+        L.x2 = c.take<float>(n);
+        L.b = c.take<float>(n);
+        L.r = c.take<float>(n);
+    }
+    H->stage = (o.flags & CMCG_FLAG_HOST_IO) ? c.take<double>(2 * np) : nullptr;
+    long long nb = std::max<long long>(kMaxBlocksReduce, plane_blocks(g, kZcEnds));
+    H->partials = c.take<double>((size_t)8 * nb);
+    H->tickets = c.take<unsigned>(kNumTickets);
+    H->sc = c.take<double>(SC_COUNT);
+    return c.off + 256;
+}
+
+int cuda_status() { return cudaGetLastError() == cudaSuccess ? CMCG_OK : CMCG_ERR_CUDA; }
+
+int sync_read(cmcg_handle* H) {
+    cudaMemcpyAsync(H->hsc, H->sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, H->st);
+    if (cudaStreamSynchronize(H->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return cuda_status();
+}
+
+// ---- period drivers ------------------------------------------------------------------------
+// Forward period from (w0, w1).  mode 0: z = E (Pi(w) - w) into (out0, out1) and J into
+// sc[SC_J]; mode 1: (y(T), y_t(T)) into (out0, out1).
+template <typename T>
+void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src, int mode, double* out0,
+                    double* out1) {
+    const Geom& g = H->g;
+    const int zc = g.dim == 3 ? kZcStep3D : 1;
+    const int zce = g.dim == 3 ? kZcEnds : 1;
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    T* cur = (T*)H->yb;
+    T* prev = (T*)H->ya;
+    const double* S = src ? H->S : nullptr;
+    launch_start<T>(g, H->order, w0, w1, prev, cur, H->kap64, S, H->dt, zce, H->st);
+    for (int n = 1; n < H->N; ++n) {
+        const double th = H->omega * n * H->dt;
+        launch_step<T>(g, H->order, cur, prev, kap, S, cos(th), sin(th), src ? kStepSrc : 0, zc, H->st);
+        std::swap(cur, prev);
+    }
+    const double thN = H->omega * H->N * H->dt;
+    launch_end<T>(g, H->order, mode, cur, prev, w0, w1, H->kap64, H->mass, S, cos(thN), sin(thN), out0, out1,
+                  H->red(), H->dt, zce, H->st);
+    H->periods += 1;
+}
+
+// Adjoint (transposed) period of the cotangents (a, b).  mode 1: q = P^T (a, b) into
+// (o0, o1).  mode 0: ghat = P^T z - z into (o0, o1), g~1 = ghat1 / M into gt1, and the
+// reductions ghat . d -> sc[SC_GD], sum ghat0 -> sc[SC_GSUM].
+template <typename T>
+void adjoint_period(cmcg_handle* H, const double* a, const double* b, int mode, const double* d0, const double* d1,
+                    double* o0, double* o1, double* gt1) {
+    const Geom& g = H->g;
+    const int zc = g.dim == 3 ? kZcStep3D : 1;
+    const int zce = g.dim == 3 ? kZcEnds : 1;
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    T* cur = (T*)H->ya;
+    T* prev = (T*)H->yb;
+    launch_adj_prep(g, b, H->mass, H->kap64, H->tmp, zce, H->st);
+    launch_adj_start<T>(g, H->order, a, H->tmp, H->mass, H->kap64, cur, prev, H->dt, zce, H->st);
+    for (int k = 0; k < H->N - 1; ++k) {
+        int flags = 0;
+        if (k == 0) flags |= kStepPrevScaled;
+        if (k == H->N - 2) flags |= kStepNoDiv;
+        launch_step<T>(g, H->order, cur, prev, kap, nullptr, 0.0, 0.0, flags, zc, H->st);
+        std::swap(cur, prev);
+    }
+    launch_adj_final<T>(g, H->order, mode, cur, prev, H->mass, H->kap64, a, b, d0, d1, o0, o1, gt1, H->red(), H->dt,
+                        zce, H->st);
+    H->periods += 1;
+}
+
+// ---- Riesz map: FP64 flexible PCG with a FP32 multigrid V-cycle --------------------------
+float jacobi_omega(const Geom& g) { return g.dim == 3 ? 6.0f / 7.0f : 0.8f; }
+
+void vcycle(cmcg_handle* H, int l) {
+    MGLevel& L = H->lv[l];
+    const float om = jacobi_omega(L.g);
+    if (l == H->nlev - 1) {
+        if (L.g.np <= mg_coarse_max_nodes()) {
+            const int nmax = std::max(L.g.nx, std::max(L.g.ny, L.g.nz));
+            const int sweeps = std::min(400, std::max(16, 4 * nmax * nmax));
+            launch_mg_coarse_solve(L, L.x, L.b, sweeps, om, H->st);
+        } else {
+            launch_mg_jacobi(L, nullptr, L.x, L.b, om, true, H->st);
+            for (int s = 0; s < 7; ++s) {
+                launch_mg_jacobi(L, L.x, L.x2, L.b, om, false, H->st);
+                std::swap(L.x, L.x2);
+            }
+        }
+        return;
+    }
+    const int nu = 2;
+    launch_mg_jacobi(L, nullptr, L.x, L.b, om, true, H->st);
+    for (int s = 1; s < nu; ++s) {
+        launch_mg_jacobi(L, L.x, L.x2, L.b, om, false, H->st);
+        std::swap(L.x, L.x2);
+    }
+    MGLevel& C = H->lv[l + 1];
+    launch_mg_residual(L, L.x, L.b, L.r, H->st);
+    launch_mg_restrict(L, L.r, C, C.b, H->st);
+    vcycle(H, l + 1);
+    launch_mg_prolong_add(C, C.x, L, L.x, H->st);
+    for (int s = 0; s < nu; ++s) {
+        launch_mg_jacobi(L, L.x, L.x2, L.b, om, false, H->st);
+        std::swap(L.x, L.x2);
+    }
+}
+
+void precondition(cmcg_handle* H, const double* r) {
+    launch_to_float(H->g.np, r, H->lv[0].b, H->st);
+    vcycle(H, 0);
+}
+
+// K s = rhs (K singular without Dirichlet nodes: rhs projected, s with W-mean zero).
+int riesz_solve(cmcg_handle* H, const double* rhs, double* x, int* iters_out) {
+    const Geom& g = H->g;
+    const long long n = g.np;
+    const bool project = !H->has_dir;
+    const double tol = H->opt.riesz_tol;
+    Red red = H->red();
+    launch_pcg_project(g, rhs, H->pr, H->mask, H->volume, red, project, H->st);
+    launch_fill(x, n, 0.0, H->st);
+    precondition(H, H->pr);
+    launch_pcg_dots_after_precond(n, H->pr, H->lv[0].x, nullptr, H->pzd, red, H->st);
+    launch_pcg_p_update(n, H->pp, H->pzd, red, true, H->st);
+    int it = 0;
+    bool converged = false;
+    double bb = -1.0;
+    for (it = 1; it <= H->opt.riesz_max_iter; ++it) {
+        launch_applyK(g, H->order, H->mask, H->pp, H->pAp, H->pp, red, SC_P_PAP, H->st);
+        launch_pcg_xr_update(n, x, H->pr, H->pp, H->pAp, red, H->st);
+        int rc = sync_read(H);
+        if (rc != CMCG_OK) return rc;
+        bb = H->hsc[SC_P_BB];
+        const double rr = H->hsc[SC_P_RR];
+        if (!(rr == rr)) return CMCG_ERR_DIVERGED;
+        if (bb == 0.0 || rr <= tol * tol * bb) {
+            converged = true;
+            break;
+        }
+        precondition(H, H->pr);
+        launch_pcg_dots_after_precond(n, H->pr, H->lv[0].x, H->pAp, H->pzd, red, H->st);
+        launch_pcg_p_update(n, H->pp, H->pzd, red, false, H->st);
+    }
+    if (project) launch_mean_remove(g, x, H->volume, red, H->st);
+    H->riesz_iters += std::min(it, H->opt.riesz_max_iter);
+    if (iters_out) *iters_out = std::min(it, H->opt.riesz_max_iter);
+    int rc = cuda_status();
+    if (rc != CMCG_OK) return rc;
+    return converged ? CMCG_OK : CMCG_NOT_CONVERGED;
+}
+
+// ---- CMCG ---------------------------------------------------------------------------------
+// Gradient of J at (w0, w1) (with the sources if src): ghat -> (gh0, gh1), g~ -> (gt0, gt1),
+// z -> (z0, z1); J -> sc[SC_J].
+template <typename T>
+int gradient(cmcg_handle* H, const double* w0, const double* w1, bool src, const double* dd0, const double* dd1) {
+    forward_period<T>(H, w0, w1, src, 0, H->z0, H->z1);
+    adjoint_period<T>(H, H->z0, H->z1, 0, dd0, dd1, H->gh0, H->gh1, H->gt1);
+    int rc = riesz_solve(H, H->gh0, H->gt0, nullptr);
+    return rc < 0 ? rc : CMCG_OK;
+}
+
+// CG loop of Steps (4)-(5) on the current gradient (gh, gt) with homogeneous periods in
+// precision T; iterate accumulated into (w0, w1) (v -= alpha d).
+template <typename T>
+int cg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_out) {
+    const long long n = H->g.np;
+    Red red = H->red();
+    launch_cg_init(n, H->gt0, H->gt1, H->gh0, H->gh1, H->r0, H->r1, H->rh0, H->rh1, H->d0, H->d1, red, H->st);
+    int rc = sync_read(H);
+    if (rc != CMCG_OK) return rc;
+    if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
+    double rel = H->hsc[SC_REL];
+    int it = 0;
+    if (rel > tol) {
+        for (it = 1; it <= max_iter; ++it) {
+            // 5.1: homogeneous forward + adjoint period from d; 5.2: Riesz
+            rc = gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1);
+            if (rc < 0) return rc;
+            // 5.3-5.6
+            launch_cg_update(n, H->w0, H->w1, H->r0, H->r1, H->rh0, H->rh1, H->d0, H->d1, H->gt0, H->gt1, H->gh0,
+                             H->gh1, -1.0, red, H->st);
+            // 5.7
+            launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st);
+            // 5.8
+            rc = sync_read(H);
+            if (rc != CMCG_OK) return rc;
+            if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
+            rel = H->hsc[SC_REL];
+            if (rel <= tol) break;
+        }
+        if (it > max_iter) it = max_iter;
+    }
+    *iters = it;
+    *rel_out = rel;
+    return rel <= tol ? CMCG_OK : CMCG_NOT_CONVERGED;
+}
+
+template <typename T>
+int solve_plain(cmcg_handle* H, double tol, cmcg_stats* stats) {
+    const long long n = H->g.np;
+    // (1) v = 0; (2)-(3) gradient with the sources and its Riesz representer
+    launch_fill(H->w0, n, 0.0, H->st);
+    launch_fill(H->w1, n, 0.0, H->st);
+    int rc = gradient<T>(H, H->w0, H->w1, true, H->w0, H->w1);
+    if (rc < 0) return rc;
+    rc = sync_read(H);
+    if (rc != CMCG_OK) return rc;
+    stats->J0 = H->hsc[SC_J];
+    int iters = 0;
+    double rel = 1.0;
+    rc = cg_loop<T>(H, tol, H->opt.max_iter, &iters, &rel);
+    stats->iterations = iters;
+    stats->rel_residual = rel;
+    return rc;
+}
+
+// CMCG_MIXED: defect correction.  Outer: FP64 gradient at the FP64 iterate W; inner: CG with
+// FP32 periods on the correction, started from that gradient, to inner_tol; W += correction.
+int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
+    const long long n = H->g.np;
+    Red red = H->red();
+    launch_fill(H->wo0, n, 0.0, H->st);
+    launch_fill(H->wo1, n, 0.0, H->st);
+    double gamma_ref = -1.0;
+    int total = 0, outer = 0;
+    double rel = 1.0;
+    int rc = CMCG_OK;
+    const int max_outer = 50;
+    for (outer = 0; outer < max_outer; ++outer) {
+        rc = gradient<double>(H, H->wo0, H->wo1, true, H->wo0, H->wo1);
+        if (rc < 0) return rc;
+        launch_scalar_residual(n, H->gt0, H->gt1, H->gh0, H->gh1, red, SC_R7, H->st);
+        rc = sync_read(H);
+        if (rc != CMCG_OK) return rc;
+        const double gam = H->hsc[SC_R7];
+        if (!(gam == gam) || gam < 0) return CMCG_ERR_DIVERGED;
+        if (outer == 0) {
+            gamma_ref = gam;
+            stats->J0 = H->hsc[SC_J];
+        }
+        rel = gamma_ref > 0 ? sqrt(gam / gamma_ref) : 0.0;
+        if (rel <= tol || total >= H->opt.max_iter) break;
+        // inner solve: relative tolerance inner_tol, but not below what the outer needs
+        const double inner = std::max(H->opt.inner_tol, 0.5 * tol / std::max(rel, 1e-300));
+        launch_fill(H->w0, n, 0.0, H->st);
+        launch_fill(H->w1, n, 0.0, H->st);
+        int it = 0;
+        double irel = 1.0;
+        rc = cg_loop<float>(H, std::min(inner, 0.5), H->opt.max_iter - total, &it, &irel);
+        if (rc < 0) return rc;
+        total += it;
+        launch_axpy(n, 1.0, H->w0, H->wo0, H->st);
+        launch_axpy(n, 1.0, H->w1, H->wo1, H->st);
+    }
+    // the returned iterate lives in (w0, w1)
+    cudaMemcpyAsync(H->w0, H->wo0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+    cudaMemcpyAsync(H->w1, H->wo1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+    stats->iterations = total;
+    stats->outer_iterations = outer;
+    stats->rel_residual = rel;
+    if (cuda_status() != CMCG_OK) return CMCG_ERR_CUDA;
+    return rel <= tol ? CMCG_OK : CMCG_NOT_CONVERGED;
+}
+
+// Steps (1)-(6) with the source S already in the workspace; U into u (device).
+int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool want_J) {
+    memset(st, 0, sizeof(*st));
+    const long long launches0 = launch_count();
+    h->riesz_iters = 0;
+    h->periods = 0;
+    const long long n = h->g.np;
+    int rc;
+    if (h->opt.precision == CMCG_FP64)
+        rc = solve_plain<double>(h, tol, st);
+    else if (h->opt.precision == CMCG_FP32)
+        rc = solve_plain<float>(h, tol, st);
+    else
+        rc = solve_mixed(h, tol, st);
+    if (rc < 0) return rc;
+    const long long periods_solve = h->periods;
+    // J at the returned iterate (FP64 period with the sources)
+    if (want_J) {
+        forward_period<double>(h, h->w0, h->w1, true, 0, h->z0, h->z1);
+        if (sync_read(h) != CMCG_OK) return CMCG_ERR_CUDA;
+        st->J_final = h->hsc[SC_J];
+    }
+    // (6) recovery and the compatibility-condition shift
+    launch_recover(h->g, h->w0, h->w1, h->wh, h->S, h->kap64, h->mass, u, h->red(), h->st);
+    if (sync_read(h) != CMCG_OK) return CMCG_ERR_CUDA;
+    double lre = 0.0, lim = 0.0;
+    if (!h->has_dir) {
+        const double* r = h->hsc + SC_R0;
+        const double wt2 = h->wt * h->wt;
+        // lambda = (1.F + wt^2 1.M u + i wh 1.B u) / (wt^2 sum M + i wh sum B)
+        const double nre = r[0] + wt2 * r[2] - h->wh * r[5];
+        const double nim = r[1] + wt2 * r[3] + h->wh * r[4];
+        const double dre = wt2 * h->sumM, dim = h->wh * h->sumB;
+        const double den = dre * dre + dim * dim;
+        lre = (nre * dre + nim * dim) / den;
+        lim = (nim * dre - nre * dim) / den;
+        launch_shift(n, u, h->kap64, lre, lim, h->st);
+    }
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    if (cuda_status() != CMCG_OK) return CMCG_ERR_CUDA;
+    st->lambda_re = lre;
+    st->lambda_im = lim;
+    st->steps_per_period = h->N;
+    st->dt = h->dt;
+    st->omega_tilde = h->wt;
+    st->omega_hat = h->wh;
+    st->periods = (int)periods_solve;
+    st->riesz_iterations = (int)h->riesz_iters;
+    st->point_updates = periods_solve * (long long)h->N * n;
+    st->kernel_launches = launch_count() - launches0;
+    return rc;
+}
+
+
+}  // namespace
+
+// ======================================================================================
+extern "C" {
+
+size_t cmcg_workspace_size(const cmcg_grid* grid, const cmcg_options* opts) {
+    if (!valid_grid(grid)) return 0;
+    cmcg_options o{};
+    if (opts) o = *opts;
+    if (o.precision < CMCG_FP64 || o.precision > CMCG_MIXED) return 0;
+    cmcg_handle tmp;
+    Geom g = make_geom(grid, 0);
+    return layout(&tmp, g, o, nullptr);
+}
+
+int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg_bc* bc, const cmcg_options* opts,
+                void* workspace, size_t ws_bytes, void* stream, cmcg_handle** out) {
+    if (!out) return CMCG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!valid_grid(grid) || !c || !bc || !workspace || !(omega > 0) || !isfinite(omega))
+        return CMCG_ERR_INVALID_ARG;
+    if (((uintptr_t)workspace & 255u) != 0) return CMCG_ERR_INVALID_ARG;
+    cmcg_options o{};
+    if (opts) o = *opts;
+    if (o.precision < CMCG_FP64 || o.precision > CMCG_MIXED) return CMCG_ERR_INVALID_ARG;
+    if (o.flags & ~CMCG_FLAG_HOST_IO) return CMCG_ERR_INVALID_ARG;
+    if (o.dt < 0 || !isfinite(o.dt)) return CMCG_ERR_INVALID_ARG;
+    fill_defaults(&o);
+    unsigned abc = 0, dir = 0;
+    for (int f = 0; f < 2 * grid->dim; ++f) {
+        const int code = bc->face[f];
+        if (code == CMCG_BC_ABC) abc |= 1u << f;
+        else if (code == CMCG_BC_DIRICHLET) dir |= 1u << f;
+        else if (code != CMCG_BC_NEUMANN) return CMCG_ERR_INVALID_ARG;
+    }
+    const size_t need = cmcg_workspace_size(grid, &o);
+    if (ws_bytes < need) return CMCG_ERR_WORKSPACE;
+
+    cmcg_handle* H = new cmcg_handle();
+    H->g = make_geom(grid, abc);
+    H->order = grid->order;
+    H->opt = o;
+    H->st = (cudaStream_t)stream;
+    H->omega = omega;
+    H->T = 2.0 * kPi / omega;
+    layout(H, H->g, o, (char*)workspace);
+    H->volume = 1.0;
+    for (int a = 0; a < grid->dim; ++a) H->volume *= grid->n[a] * grid->h;
+    if (cudaMallocHost((void**)&H->hsc, sizeof(double) * SC_COUNT) != cudaSuccess) {
+        delete H;
+        return CMCG_ERR_CUDA;
+    }
+    auto fail = [&](int code) {
+        cudaFreeHost(H->hsc);
+        delete H;
+        return code;
+    };
+    cudaMemsetAsync(H->tickets, 0, sizeof(unsigned) * kNumTickets, H->st);
+    cudaMemsetAsync(H->sc, 0, sizeof(double) * SC_COUNT, H->st);
+    // pass 1 (dt = 1): validity, sums, c_max
+    launch_setup_coeffs(H->g, c, bc->dirichlet_mask, dir, 1.0, H->kap64, H->kap32, H->mass, H->mask, H->red(), H->st);
+    if (sync_read(H) != CMCG_OK) return fail(CMCG_ERR_CUDA);
+    if (H->hsc[3] != 0.0) return fail(CMCG_ERR_INVALID_ARG);
+    H->sumM = H->hsc[0];
+    H->sumB = H->hsc[1];
+    H->sumW = H->hsc[2];
+    H->has_dir = H->hsc[4] > 0.0;
+    uint64_t bits;
+    memcpy(&bits, &H->hsc[5], sizeof(bits));
+    double cmax;
+    memcpy(&cmax, &bits, sizeof(cmax));
+    if (H->has_dir && H->order == 4) return fail(CMCG_ERR_UNSUPPORTED);
+    if (H->has_dir && H->sumW <= 0) return fail(CMCG_ERR_INVALID_ARG);
+    // time step: N = ceil(T / dt_target - 1e-9), dt = T / N
+    const double dt_target = o.dt > 0 ? o.dt : 0.5 * grid->h / (sqrt((double)grid->dim) * cmax);
+    H->N = (int)ceil(H->T / dt_target - 1e-9);
+    if (H->N < 2) H->N = 2;
+    H->dt = H->T / H->N;
+    const double rho = (grid->order == 2 ? 4.0 * grid->dim : 16.0 * grid->dim / 3.0) / (grid->h * grid->h);
+    if (H->dt * H->dt * cmax * cmax * rho >= 4.0) return fail(CMCG_ERR_CFL);
+    H->wt = 2.0 / H->dt * sin(omega * H->dt / 2.0);
+    H->wh = sin(omega * H->dt) / H->dt;
+    // pass 2 with the final dt
+    cudaMemsetAsync(H->sc, 0, sizeof(double) * SC_COUNT, H->st);
+    launch_setup_coeffs(H->g, c, bc->dirichlet_mask, dir, H->dt, H->kap64, H->kap32, H->mass, H->mask, H->red(),
+                        H->st);
+    for (int l = 1; l < H->nlev; ++l) launch_mg_coarsen_mask(H->lv[l - 1], H->lv[l], H->st);
+    if (!H->has_dir)
+        for (int l = 0; l < H->nlev; ++l) H->lv[l].mask = nullptr;
+    if (sync_read(H) != CMCG_OK) return fail(CMCG_ERR_CUDA);
+    *out = H;
+    return CMCG_OK;
+}
+
+int cmcg_destroy(cmcg_handle* h) {
+    if (!h) return CMCG_ERR_INVALID_ARG;
+    cudaFreeHost(h->hsc);
+    delete h;
+    return CMCG_OK;
+}
+
+int cmcg_get_info(const cmcg_handle* h, cmcg_info* info) {
+    if (!h || !info) return CMCG_ERR_INVALID_ARG;
+    info->steps_per_period = h->N;
+    info->dt = h->dt;
+    info->omega_tilde = h->wt;
+    info->omega_hat = h->wh;
+    info->num_nodes = h->g.np;
+    info->mg_levels = h->nlev;
+    info->has_dirichlet = h->has_dir ? 1 : 0;
+    return CMCG_OK;
+}
+
+int cmcg_wave_period(cmcg_handle* h, const double* u0, const double* v0, const double* f, const double* g,
+                     double* uT, double* vT) {
+    if (!h || !u0 || !v0 || !uT || !vT) return CMCG_ERR_INVALID_ARG;
+    const bool src = f || g;
+    if (src) launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
+    launch_mask_copy(h->g, u0, h->kap64, h->z0, h->st);
+    launch_mask_copy(h->g, v0, h->kap64, h->z1, h->st);
+    if (h->opt.precision == CMCG_FP32)
+        forward_period<float>(h, h->z0, h->z1, src, 1, uT, vT);
+    else
+        forward_period<double>(h, h->z0, h->z1, src, 1, uT, vT);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return cuda_status();
+}
+
+int cmcg_adjoint_period(cmcg_handle* h, const double* a, const double* b, double* q0, double* q1) {
+    if (!h || !a || !b || !q0 || !q1) return CMCG_ERR_INVALID_ARG;
+    launch_mask_copy(h->g, a, h->kap64, h->z0, h->st);
+    launch_mask_copy(h->g, b, h->kap64, h->z1, h->st);
+    if (h->opt.precision == CMCG_FP32)
+        adjoint_period<float>(h, h->z0, h->z1, 1, nullptr, nullptr, q0, q1, nullptr);
+    else
+        adjoint_period<double>(h, h->z0, h->z1, 1, nullptr, nullptr, q0, q1, nullptr);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return cuda_status();
+}
+
+int cmcg_riesz(cmcg_handle* h, const double* rhs, double* s) {
+    if (!h || !rhs || !s) return CMCG_ERR_INVALID_ARG;
+    int rc = riesz_solve(h, rhs, s, nullptr);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return rc;
+}
+
+int cmcg_solve(cmcg_handle* h, const double* f, const double* g, double tol, double* u, cmcg_stats* stats) {
+    if (!h || !u || !(tol > 0)) return CMCG_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (f || g)
+        launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
+    else
+        launch_fill(h->S, 2 * h->g.np, 0.0, h->st);
+    cmcg_stats local{};
+    cmcg_stats* st = stats ? stats : &local;
+    const int rc = solve_prepared(h, tol, u, st, stats != nullptr);
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+int cmcg_solve_host(cmcg_handle* h, const double* f_host, const double* g_host, double tol, double* u_host,
+                    cmcg_stats* stats) {
+    if (!h || !u_host || !h->stage || !(tol > 0)) return CMCG_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long n = h->g.np;
+    const size_t bytes = sizeof(double) * 2 * (size_t)n;
+    const int zce = h->g.dim == 3 ? kZcEnds : 1;
+    // S = kappa h^2 (f + (2 nb / h) g), built through the one staging buffer
+    launch_fill(h->S, 2 * n, 0.0, h->st);
+    if (f_host) {
+        cudaMemcpyAsync(h->stage, f_host, bytes, cudaMemcpyHostToDevice, h->st);
+        launch_make_source(h->g, h->stage, nullptr, h->kap64, h->S, zce, true, h->st);
+    }
+    if (g_host) {
+        cudaMemcpyAsync(h->stage, g_host, bytes, cudaMemcpyHostToDevice, h->st);
+        launch_make_source(h->g, nullptr, h->stage, h->kap64, h->S, zce, true, h->st);
+    }
+    if (cuda_status() != CMCG_OK) return CMCG_ERR_CUDA;
+    cmcg_stats local{};
+    cmcg_stats* st = stats ? stats : &local;
+    const int rc = solve_prepared(h, tol, h->stage, st, stats != nullptr);
+    if (rc < 0) return rc;
+    cudaMemcpyAsync(u_host, h->stage, bytes, cudaMemcpyDeviceToHost, h->st);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+const char* cmcg_status_string(int s) {
+    switch (s) {
+        case CMCG_OK: return "ok";
+        case CMCG_NOT_CONVERGED: return "not converged";
+        case CMCG_ERR_INVALID_ARG: return "invalid argument";
+        case CMCG_ERR_CFL: return "CFL condition violated";
+        case CMCG_ERR_WORKSPACE: return "workspace too small";
+        case CMCG_ERR_UNSUPPORTED: return "unsupported combination";
+        case CMCG_ERR_CUDA: return "CUDA error";
+        case CMCG_ERR_DIVERGED: return "diverged (non-finite or non-positive CG scalar)";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

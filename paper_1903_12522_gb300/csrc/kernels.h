@@ -1,0 +1,103 @@
+// Host-side launcher declarations of libcmcg's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cmcg {
+
+struct Geom;
+
+// Reduction context: per-block partials, a ticket counter and the device scalar slots.
+struct Red {
+    double* partials;
+    unsigned* ticket;
+    double* sc;
+};
+
+enum StepFlags { kStepSrc = 1, kStepPrevScaled = 2, kStepNoDiv = 4 };
+
+// Process-wide count of kernels launched by this library (every launcher records its launches).
+void note_launch(long long k);
+long long launch_count();
+
+// ---- wave.cu --------------------------------------------------------------------------
+template <typename T>
+void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, const double* S, double cs,
+                 double sn, int flags, int zc, cudaStream_t st);
+template <typename T>
+void launch_start(const Geom& g, int order, const double* w0, const double* w1, T* y0, T* y1,
+                  const double* kap64, const double* S, double dt, int zc, cudaStream_t st);
+template <typename T>
+void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const double* w0,
+                const double* w1, const double* kap64, const double* mass, const double* S, double cs,
+                double sn, double* out0, double* out1, Red red, double dt, int zc, cudaStream_t st);
+void launch_adj_prep(const Geom& g, const double* b, const double* mass, const double* kap64, double* t, int zc,
+                     cudaStream_t st);
+template <typename T>
+void launch_adj_start(const Geom& g, int order, const double* a, const double* t, const double* mass,
+                      const double* kap64, T* cur, T* prev, double dt, int zc, cudaStream_t st);
+template <typename T>
+void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass,
+                      const double* kap64, const double* z0, const double* z1, const double* d0, const double* d1,
+                      double* o0, double* o1, double* gt1, Red red, double dt, int zc, cudaStream_t st);
+void launch_make_source(const Geom& g, const double* f, const double* gb, const double* kap64, double* S, int zc,
+                        bool accumulate, cudaStream_t st);
+long long plane_blocks(const Geom& g, int zc);
+
+// ---- linalg.cu ------------------------------------------------------------------------
+// Setup: kappa = c^2 dt^2 / h^2 (0 on Dirichlet nodes), M = W / c^2 (0 on Dirichlet nodes),
+// optional FP32 copy of kappa, Dirichlet byte mask.  sc[0..5) = (sum M, sum B, sum W over
+// active nodes, invalid c count, Dirichlet count); sc[5] = bits of max c (zero it first).
+void launch_setup_coeffs(const Geom& g, const double* c, const unsigned char* user_mask, unsigned face_dir,
+                         double dt, double* kap64, float* kap32, double* mass, unsigned char* mask, Red red,
+                         cudaStream_t st);
+void launch_mask_copy(const Geom& g, const double* in, const double* kap64, double* out, cudaStream_t st);
+void launch_fill(double* p, long long n, double v, cudaStream_t st);
+
+// CG recurrences (Step (4) and Steps 5.3-5.8), scalars on the device.
+void launch_cg_init(long long n, const double* gt0, const double* gt1, const double* gh0, const double* gh1,
+                    double* r0, double* r1, double* rh0, double* rh1, double* d0, double* d1, Red red,
+                    cudaStream_t st);
+void launch_cg_update(long long n, double* w0, double* w1, double* r0, double* r1, double* rh0, double* rh1,
+                      const double* d0, const double* d1, const double* gt0, const double* gt1, const double* gh0,
+                      const double* gh1, double sign, Red red, cudaStream_t st);
+void launch_cg_direction(long long n, const double* r0, const double* r1, double* d0, double* d1, Red red,
+                         cudaStream_t st);
+// Reductions on the solution for the compatibility-condition shift: sums of
+// (F re, F im, (M u) re, (M u) im, (B u) re, (B u) im) into sc[SC_R0..SC_R5].
+void launch_recover(const Geom& g, const double* w0, const double* w1, double omega_hat, const double* S,
+                    const double* kap64, const double* mass, double* u, Red red, cudaStream_t st);
+void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t st);
+void launch_shift(long long n, double* u, const double* kap64, double lre, double lim, cudaStream_t st);
+void launch_scalar_residual(long long n, const double* r0, const double* r1, const double* rh0,
+                            const double* rh1, Red red, int slot, cudaStream_t st);
+
+// ---- riesz.cu -------------------------------------------------------------------------
+struct MGLevel {
+    Geom g;
+    unsigned char* mask;  // Dirichlet bytes (nullptr if the problem has none)
+    float *x, *x2, *b, *r;
+};
+void launch_mg_coarsen_mask(const MGLevel& fine, const MGLevel& coarse, cudaStream_t st);
+void launch_mg_jacobi(const MGLevel& L, const float* xin, float* xout, const float* b, float omega, bool zero_init,
+                      cudaStream_t st);
+void launch_mg_residual(const MGLevel& L, const float* x, const float* b, float* r, cudaStream_t st);
+void launch_mg_restrict(const MGLevel& fine, const float* rf, const MGLevel& coarse, float* bc, cudaStream_t st);
+void launch_mg_prolong_add(const MGLevel& coarse, const float* xc, const MGLevel& fine, float* xf, cudaStream_t st);
+void launch_mg_coarse_solve(const MGLevel& L, float* x, const float* b, int sweeps, float omega, cudaStream_t st);
+int mg_coarse_max_nodes();
+// FP64 PCG pieces on the fine level
+void launch_applyK(const Geom& g, int order, const unsigned char* mask, const double* x, double* y,
+                   const double* dotwith, Red red, int slot, cudaStream_t st);
+void launch_to_float(long long n, const double* in, float* out, cudaStream_t st);
+void launch_pcg_project(const Geom& g, const double* in, double* out, const unsigned char* mask, double volume,
+                        Red red, bool project, cudaStream_t st);
+void launch_pcg_dots_after_precond(long long n, const double* r, const float* z, const double* Ap, double* zd,
+                                   Red red, cudaStream_t st);
+void launch_pcg_xr_update(long long n, double* x, double* r, const double* p, const double* Ap, Red red,
+                          cudaStream_t st);
+void launch_pcg_p_update(long long n, double* p, const double* zd, Red red, bool first, cudaStream_t st);
+void launch_mean_remove(const Geom& g, double* x, double volume, Red red, cudaStream_t st);
+void launch_reduce_sum(long long n, const double* x, Red red, int slot, cudaStream_t st);
+
+}  // namespace cmcg

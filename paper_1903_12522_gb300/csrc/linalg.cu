@@ -1,0 +1,306 @@
+// Coefficient setup, the CG recurrences of the CMCG Algorithm (Sec. 2.3, Steps (4) and
+// 5.3-5.8) with every scalar kept on the device, and the solution recovery of Step (6) with
+// the compatibility-condition shift of Sec. 2.1.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cmcg {
+
+namespace {
+
+constexpr int kT = 256;
+
+inline unsigned vec_blocks(long long n) {
+    long long b = (n + kT - 1) / kT;
+    if (b > kMaxBlocksReduce) b = kMaxBlocksReduce;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+// ---- setup -------------------------------------------------------------------------------
+// kappa = c^2 dt^2 / h^2, M = W / c^2, zero on Dirichlet nodes.  Reduces (sum M, sum B,
+// sum W) over active nodes, the number of invalid c and the number of Dirichlet nodes into
+// sc[0..5), and max c into sc[5] (as the bit pattern of a positive double, which orders like
+// an unsigned integer).
+__global__ void __launch_bounds__(kT) k_setup(const double* __restrict__ c, const unsigned char* __restrict__ umask,
+                                              unsigned face_dir, double dt, double* __restrict__ kap64,
+                                              float* __restrict__ kap32, double* __restrict__ mass,
+                                              unsigned char* __restrict__ mask, Red red, Geom g) {
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    unsigned long long cmax_bits = 0ull;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
+        const unsigned t = (unsigned)j / (unsigned)g.sx;
+        const int ix = (int)((unsigned)j - t * (unsigned)g.sx);
+        const int iz = (int)(t / (unsigned)g.sy);
+        const int iy = (int)(t - (unsigned)iz * (unsigned)g.sy);
+        bool dir = umask ? (umask[j] != 0) : false;
+        dir |= (ix == 0) && (face_dir & 1u);
+        dir |= (ix == g.nx) && (face_dir & 2u);
+        dir |= (iy == 0) && (face_dir & 4u);
+        dir |= (iy == g.ny) && (face_dir & 8u);
+        if (g.dim == 3) {
+            dir |= (iz == 0) && (face_dir & 16u);
+            dir |= (iz == g.nz) && (face_dir & 32u);
+        }
+        const double cj = c[j];
+        if (!(cj > 0.0) || !isfinite(cj)) acc[3] += 1.0;
+        const double W = weight(g, ix, iy, iz);
+        if (dir) {
+            kap64[j] = 0.0;
+            mass[j] = 0.0;
+            if (kap32) kap32[j] = 0.f;
+            mask[j] = 1;
+            acc[4] += 1.0;
+        } else {
+            const double k = cj * cj * dt * dt / (g.h * g.h);
+            kap64[j] = k;
+            mass[j] = W / (cj * cj);
+            if (kap32) kap32[j] = (float)k;
+            mask[j] = 0;
+            acc[0] += W / (cj * cj);
+            acc[1] += W * 2.0 * num_abc(g, ix, iy, iz) / g.h / cj;
+            acc[2] += W;
+        }
+        if (cj > 0.0 && isfinite(cj)) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(cj);
+            cmax_bits = bits > cmax_bits ? bits : cmax_bits;
+        }
+    }
+    // max c: order-independent atomic on the bit pattern of positive doubles
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_down_sync(0xffffffffu, cmax_bits, o);
+        cmax_bits = other > cmax_bits ? other : cmax_bits;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)&red.sc[5], cmax_bits);
+    if (grid_sum<5>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
+        for (int k = 0; k < 5; ++k) red.sc[k] = acc[k];
+    }
+}
+
+__global__ void k_mask_copy(const double* __restrict__ in, const double* __restrict__ kap64, double* __restrict__ out,
+                            long long n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride)
+        out[j] = kap64[j] == 0.0 ? 0.0 : in[j];
+}
+
+__global__ void k_fill(double* p, long long n, double v) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) p[j] = v;
+}
+
+// ---- CG -----------------------------------------------------------------------------------
+// Step (4): r = d = g~, rhat = ghat (= E r), gamma = r . rhat = ||r||_E^2.
+__global__ void __launch_bounds__(kT) k_cg_init(long long n, const double* __restrict__ gt0,
+                                                const double* __restrict__ gt1, const double* __restrict__ gh0,
+                                                const double* __restrict__ gh1, double* __restrict__ r0,
+                                                double* __restrict__ r1, double* __restrict__ rh0,
+                                                double* __restrict__ rh1, double* __restrict__ d0,
+                                                double* __restrict__ d1, Red red) {
+    double acc[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const double a0 = gt0[j], a1 = gt1[j], b0 = gh0[j], b1 = gh1[j];
+        r0[j] = a0;
+        r1[j] = a1;
+        d0[j] = a0;
+        d1[j] = a1;
+        rh0[j] = b0;
+        rh1[j] = b1;
+        acc[0] += a0 * b0 + a1 * b1;
+    }
+    if (grid_sum<1>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
+        red.sc[SC_GAMMA] = acc[0];
+        red.sc[SC_GAMMA0] = acc[0];
+        red.sc[SC_REL] = acc[0] > 0.0 ? 1.0 : 0.0;
+        red.sc[SC_STATUS] = (isfinite(acc[0]) && acc[0] >= 0.0) ? 0.0 : 1.0;
+    }
+}
+
+// Steps 5.3-5.6: alpha = gamma / (ghat . d); v -= alpha d; r -= alpha g~; rhat -= alpha ghat;
+// gamma' = r . rhat; beta = gamma'/gamma (stored for Step 5.7); rel = sqrt(gamma'/gamma0).
+__global__ void __launch_bounds__(kT) k_cg_update(long long n, double* __restrict__ w0, double* __restrict__ w1,
+                                                  double* __restrict__ r0, double* __restrict__ r1,
+                                                  double* __restrict__ rh0, double* __restrict__ rh1,
+                                                  const double* __restrict__ d0, const double* __restrict__ d1,
+                                                  const double* __restrict__ gt0, const double* __restrict__ gt1,
+                                                  const double* __restrict__ gh0, const double* __restrict__ gh1,
+                                                  double sign, Red red) {
+    const double gamma = red.sc[SC_GAMMA];
+    const double gd = red.sc[SC_GD];
+    const double alpha = gamma / gd;
+    double acc[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const double a0 = d0[j], a1 = d1[j];
+        w0[j] += sign * alpha * a0;
+        w1[j] += sign * alpha * a1;
+        const double x0 = r0[j] - alpha * gt0[j];
+        const double x1 = r1[j] - alpha * gt1[j];
+        const double y0 = rh0[j] - alpha * gh0[j];
+        const double y1 = rh1[j] - alpha * gh1[j];
+        r0[j] = x0;
+        r1[j] = x1;
+        rh0[j] = y0;
+        rh1[j] = y1;
+        acc[0] += x0 * y0 + x1 * y1;
+    }
+    if (grid_sum<1>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
+        const double gnew = acc[0];
+        red.sc[SC_ALPHA] = alpha;
+        red.sc[SC_GAMMA_NEW] = gnew;
+        red.sc[SC_BETA] = gnew / gamma;
+        red.sc[SC_GAMMA] = gnew;
+        const double g0 = red.sc[SC_GAMMA0];
+        red.sc[SC_REL] = sqrt(fmax(gnew, 0.0) / g0);
+        const bool bad = !isfinite(alpha) || !(gd > 0.0) || !isfinite(gnew);
+        if (bad) red.sc[SC_STATUS] = 1.0;
+    }
+}
+
+// Step 5.7: d = r + beta d.
+__global__ void __launch_bounds__(kT) k_cg_direction(long long n, const double* __restrict__ r0,
+                                                     const double* __restrict__ r1, double* __restrict__ d0,
+                                                     double* __restrict__ d1, const double* __restrict__ sc) {
+    const double beta = sc[SC_BETA];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        d0[j] = r0[j] + beta * d0[j];
+        d1[j] = r1[j] + beta * d1[j];
+    }
+}
+
+// r . rhat into sc[slot] (used by the defect-correction outer residual).
+__global__ void __launch_bounds__(kT) k_dot2(long long n, const double* __restrict__ a0, const double* __restrict__ a1,
+                                             const double* __restrict__ b0, const double* __restrict__ b1, Red red,
+                                             int slot) {
+    double acc[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride)
+        acc[0] += a0[j] * b0[j] + a1[j] * b1[j];
+    if (grid_sum<1>(acc, red.partials, red.ticket) && threadIdx.x == 0) red.sc[slot] = acc[0];
+}
+
+// Step (6): u = v0 + i v1 / omega_hat (interleaved complex) and the sums entering the
+// compatibility condition: 1.F^, 1.(M u), 1.(B u), with F^ = W S / (kappa h^2) recovered
+// from the stored source S = dt^2 M^-1 F^ (S may be null: no source).
+__global__ void __launch_bounds__(kT) k_recover(Geom g, const double* __restrict__ w0, const double* __restrict__ w1,
+                                                double inv_wh, const double* __restrict__ S,
+                                                const double* __restrict__ kap64, const double* __restrict__ mass,
+                                                double* __restrict__ u, Red red) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
+        const double k = kap64[j];
+        if (k == 0.0) {
+            u[2 * j] = 0.0;
+            u[2 * j + 1] = 0.0;
+            continue;
+        }
+        const unsigned t = (unsigned)j / (unsigned)g.sx;
+        const int ix = (int)((unsigned)j - t * (unsigned)g.sx);
+        const int iz = (int)(t / (unsigned)g.sy);
+        const int iy = (int)(t - (unsigned)iz * (unsigned)g.sy);
+        const double re = w0[j], im = w1[j] * inv_wh;
+        u[2 * j] = re;
+        u[2 * j + 1] = im;
+        const double W = weight(g, ix, iy, iz);
+        const double M = mass[j];
+        const double a = 2.0 * num_abc(g, ix, iy, iz) / g.h;   // A / W
+        const double B = a * sqrt(W * M);                       // A / c
+        if (S) {
+            const double sc = W / (k * g.h * g.h);
+            acc[0] += sc * S[2 * j];
+            acc[1] += sc * S[2 * j + 1];
+        }
+        acc[2] += M * re;
+        acc[3] += M * im;
+        acc[4] += B * re;
+        acc[5] += B * im;
+    }
+    if (grid_sum<6>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) red.sc[SC_R0 + k] = acc[k];
+    }
+}
+
+__global__ void k_axpy(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) y[j] += a * x[j];
+}
+
+__global__ void k_shift(long long n, double* __restrict__ u, const double* __restrict__ kap64, double lre,
+                        double lim) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        if (kap64[j] != 0.0) {
+            u[2 * j] -= lre;
+            u[2 * j + 1] -= lim;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_setup_coeffs(const Geom& g, const double* c, const unsigned char* user_mask, unsigned face_dir,
+                         double dt, double* kap64, float* kap32, double* mass, unsigned char* mask, Red red,
+                         cudaStream_t st) {
+    note_launch(1);
+    k_setup<<<vec_blocks(g.np), kT, 0, st>>>(c, user_mask, face_dir, dt, kap64, kap32, mass, mask, red, g);
+}
+
+void launch_mask_copy(const Geom& g, const double* in, const double* kap64, double* out, cudaStream_t st) {
+    note_launch(1);
+    k_mask_copy<<<vec_blocks(g.np), kT, 0, st>>>(in, kap64, out, g.np);
+}
+
+void launch_fill(double* p, long long n, double v, cudaStream_t st) {
+    note_launch(1);
+    k_fill<<<vec_blocks(n), kT, 0, st>>>(p, n, v);
+}
+
+void launch_cg_init(long long n, const double* gt0, const double* gt1, const double* gh0, const double* gh1,
+                    double* r0, double* r1, double* rh0, double* rh1, double* d0, double* d1, Red red,
+                    cudaStream_t st) {
+    note_launch(1);
+    k_cg_init<<<vec_blocks(n), kT, 0, st>>>(n, gt0, gt1, gh0, gh1, r0, r1, rh0, rh1, d0, d1, red);
+}
+
+void launch_cg_update(long long n, double* w0, double* w1, double* r0, double* r1, double* rh0, double* rh1,
+                      const double* d0, const double* d1, const double* gt0, const double* gt1, const double* gh0,
+                      const double* gh1, double sign, Red red, cudaStream_t st) {
+    note_launch(1);
+    k_cg_update<<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, r0, r1, rh0, rh1, d0, d1, gt0, gt1, gh0, gh1, sign, red);
+}
+
+void launch_cg_direction(long long n, const double* r0, const double* r1, double* d0, double* d1, Red red,
+                         cudaStream_t st) {
+    note_launch(1);
+    k_cg_direction<<<vec_blocks(n), kT, 0, st>>>(n, r0, r1, d0, d1, red.sc);
+}
+
+void launch_scalar_residual(long long n, const double* r0, const double* r1, const double* rh0,
+                            const double* rh1, Red red, int slot, cudaStream_t st) {
+    note_launch(1);
+    k_dot2<<<vec_blocks(n), kT, 0, st>>>(n, r0, r1, rh0, rh1, red, slot);
+}
+
+void launch_recover(const Geom& g, const double* w0, const double* w1, double omega_hat, const double* S,
+                    const double* kap64, const double* mass, double* u, Red red, cudaStream_t st) {
+    note_launch(1);
+    k_recover<<<vec_blocks(g.np), kT, 0, st>>>(g, w0, w1, 1.0 / omega_hat, S, kap64, mass, u, red);
+}
+
+void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t st) {
+    note_launch(1);
+    k_axpy<<<vec_blocks(n), kT, 0, st>>>(n, a, x, y);
+}
+
+void launch_shift(long long n, double* u, const double* kap64, double lre, double lim, cudaStream_t st) {
+    note_launch(1);
+    k_shift<<<vec_blocks(n), kT, 0, st>>>(n, u, kap64, lre, lim);
+}
+
+}  // namespace cmcg

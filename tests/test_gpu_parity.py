@@ -1,0 +1,281 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Sizes span several thread blocks with ragged tails (41^2, 25^3, 17^3) and every boundary
+type; full-size (257^3) checks compare sampled nodes with the oracle run on the node's
+domain of dependence.  Tolerances: FP64 relative L2 <= 1e-12 per period and <= 1e-10 for
+converged solves; FP32 stepping <= 2e-5 per period and <= 1e-4 for solves; the mixed
+defect-correction solve <= 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import cmcg as ocmcg  # noqa: E402
+from oracle import direct, wave  # noqa: E402
+from oracle.grid import Discretization  # noqa: E402
+from oracle.riesz import RieszSolver  # noqa: E402
+from paper_1903_12522_gb300 import cmcg  # noqa: E402
+from paper_1903_12522_gb300 import workloads as wl  # noqa: E402
+
+ABC, NEU, DIR = wl.ABC, wl.NEUMANN, wl.DIRICHLET
+
+
+def mixed_2d():
+    n = (40, 30)
+    h = 1.0 / 40
+    rng = np.random.Generator(np.random.PCG64(11))
+    shape = (31, 41)
+    c = 1.0 + 0.8 * rng.random(shape)
+    f = wl.gaussian_source(n, h, (0.3, 0.4), 0.08) * (1 + 0.5j)
+    g = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex128)
+    return wl.Workload(name="mixed2d", n=n, h=h, c=c, omega=9.0, faces=(ABC, DIR, NEU, ABC, NEU, NEU),
+                       dt_target=0.35 * h / 1.8, f=f, g=g)
+
+
+CASES = {
+    "gauss2d_40": lambda: wl.gaussian_2d(n=40),
+    "sphere3d_24": lambda: wl.sphere_3d(n=24),
+    "layered3d_o4_16": lambda: wl.layered_3d(n=16),
+    "mixed2d": mixed_2d,
+}
+
+
+def dz_of(w):
+    return Discretization(w.n, w.h, w.c, w.omega, w.faces, w.dt_target, order=w.order, mask=w.mask)
+
+
+def solver_of(w, precision=cmcg.FP64, **kw):
+    return cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, order=w.order, precision=precision,
+                       dt=w.dt_target, **kw)
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def wrel(dz, a, b):
+    return math.sqrt(float(np.sum(dz.W * np.abs(a - b) ** 2) / np.sum(dz.W * np.abs(b) ** 2)))
+
+
+def rand_state(dz, seed):
+    a, b = wl.random_fields(dz.shape, 2, seed)
+    return a * dz.act, b * dz.act
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    w = CASES[request.param]()
+    return request.param, w, dz_of(w)
+
+
+def test_steps_per_period_match(case):
+    name, w, dz = case
+    s = solver_of(w)
+    assert s.info["steps_per_period"] == dz.N
+    assert abs(s.info["dt"] - dz.dt) <= 1e-15 * dz.dt
+    assert bool(s.info["has_dirichlet"]) == dz.has_dirichlet
+
+
+@pytest.mark.parametrize("precision,tol", [(cmcg.FP64, 1e-12), (cmcg.FP32, 2e-5)])
+def test_wave_period(case, precision, tol):
+    name, w, dz = case
+    s = solver_of(w, precision)
+    y0, v0 = rand_state(dz, 1)
+    F = dz.load(w.f, w.g)
+    yT, vT = wave.period(dz, y0, v0, F)
+    uT, uV = s.wave_period(y0, v0, w.f, w.g)
+    assert rel(uT.cpu().numpy(), yT) <= tol, name
+    assert rel(uV.cpu().numpy(), vT) <= tol, name
+    # homogeneous period too
+    yT0, vT0 = wave.period(dz, y0, v0, None)
+    uT0, uV0 = s.wave_period(y0, v0)
+    assert rel(uT0.cpu().numpy(), yT0) <= tol and rel(uV0.cpu().numpy(), vT0) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [(cmcg.FP64, 1e-12), (cmcg.FP32, 2e-5)])
+def test_adjoint_period(case, precision, tol):
+    name, w, dz = case
+    s = solver_of(w, precision)
+    a, b = rand_state(dz, 2)
+    q0, q1 = wave.transposed_period(dz, a, b)
+    g0, g1 = s.adjoint_period(a, b)
+    assert rel(g0.cpu().numpy(), q0) <= tol, name
+    assert rel(g1.cpu().numpy(), q1) <= tol, name
+
+
+def test_adjoint_dot_product_on_device(case):
+    name, w, dz = case
+    s = solver_of(w)
+    x0, x1 = rand_state(dz, 3)
+    y0, y1 = rand_state(dz, 4)
+    p0, p1 = [t.cpu().numpy() for t in s.wave_period(x0, x1)]
+    q0, q1 = [t.cpu().numpy() for t in s.adjoint_period(y0, y1)]
+    lhs = np.sum(p0 * y0) + np.sum(p1 * y1)
+    rhs = np.sum(x0 * q0) + np.sum(x1 * q1)
+    scale = math.sqrt(np.sum(p0 ** 2) + np.sum(p1 ** 2)) * math.sqrt(np.sum(y0 ** 2) + np.sum(y1 ** 2))
+    assert abs(lhs - rhs) <= 1e-13 * scale
+
+
+def test_riesz(case):
+    name, w, dz = case
+    s = solver_of(w, riesz_tol=1e-13)
+    rhs = wl.random_fields(dz.shape, 1, 5)[0] * dz.act
+    ref = RieszSolver(dz).solve(rhs)
+    got, code = s.riesz(rhs)
+    assert code == cmcg.OK
+    assert rel(got.cpu().numpy(), ref) <= 1e-10, name
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(cmcg.FP64, 1e-13, 1e-10), (cmcg.FP32, 1e-6, 1e-4),
+                                                 (cmcg.MIXED, 1e-8, 1e-6)])
+def test_solve_matches_direct(case, precision, tol, bound):
+    name, w, dz = case
+    s = solver_of(w, precision)
+    U = direct.solve(dz, dz.load(w.f, w.g))
+    u, st = s.solve(w.f, w.g, tol=tol)
+    assert st["status"] == cmcg.OK, st
+    assert wrel(dz, u.cpu().numpy(), U) <= bound, (name, st)
+    assert st["point_updates"] == st["periods"] * dz.N * dz.size
+    if not dz.has_dirichlet:
+        assert abs(st["lambda_im"]) <= 1e-8 * max(abs(st["lambda_re"]), 1e-300) + 1e-14
+
+
+def test_fp64_iterations_and_shift_match_oracle(case):
+    name, w, dz = case
+    s = solver_of(w)
+    F = dz.load(w.f, w.g)
+    ref = ocmcg.solve(dz, F, tol=1e-10)
+    u, st = s.solve(w.f, w.g, tol=1e-10)
+    assert abs(st["iterations"] - ref.iterations) <= 2, (st["iterations"], ref.iterations)
+    assert abs(st["lambda_re"] - ref.lam.real) <= 1e-8 * max(abs(ref.lam), 1e-12)
+    assert abs(st["J0"] - ref.J_history[0]) <= 1e-10 * ref.J_history[0]
+
+
+def test_solve_host_matches_device():
+    w = wl.gaussian_2d(n=48)
+    s = solver_of(w, flags=cmcg.FLAG_HOST_IO)
+    u_dev, st = s.solve(w.f, None, tol=1e-10)
+    u_host = np.empty(w.shape, dtype=np.complex128)
+    st2 = cmcg.Stats()
+    code = cmcg.cmcg_solve_host(s.handle, np.ascontiguousarray(w.f), None, 1e-10, u_host, st2)
+    assert code == cmcg.OK
+    assert rel(u_host, u_dev.cpu().numpy()) <= 1e-12
+    assert st2.iterations == st["iterations"]
+
+
+def test_deterministic():
+    w = wl.sphere_3d(n=16)
+    s = solver_of(w)
+    u1, _ = s.solve(w.f, w.g, tol=1e-8)
+    u2, _ = s.solve(w.f, w.g, tol=1e-8)
+    assert torch.equal(u1, u2)
+
+
+def test_zero_source_gives_zero():
+    w = wl.gaussian_2d(n=24)
+    s = solver_of(w)
+    u, st = s.solve(None, None, tol=1e-6)
+    assert st["status"] == cmcg.OK and st["iterations"] == 0
+    assert float(u.abs().max()) == 0.0
+
+
+def test_not_converged_returns_last_iterate():
+    w = wl.gaussian_2d(n=24)
+    s = solver_of(w, max_iter=3)
+    u, st = s.solve(w.f, None, tol=1e-12)
+    assert st["status"] == cmcg.NOT_CONVERGED and st["iterations"] == 3
+    assert 0 < st["rel_residual"] < 1 and float(u.abs().max()) > 0
+
+
+def test_invalid_arguments():
+    w = wl.gaussian_2d(n=16)
+    with pytest.raises(cmcg.CMCGError) as e:
+        cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, dt=2.0 * w.h)
+    assert e.value.code == cmcg.ERR_CFL
+    with pytest.raises(cmcg.CMCGError) as e:
+        cmcg.Solver(w.n, w.h, -w.c, w.omega, w.faces, dt=w.dt_target)
+    assert e.value.code == cmcg.ERR_INVALID_ARG
+    w3 = wl.sphere_3d(n=8)
+    with pytest.raises(cmcg.CMCGError) as e:
+        cmcg.Solver(w3.n, w3.h, w3.c, w3.omega, w3.faces, mask=w3.mask, order=4, dt=0.2 * w3.h)
+    assert e.value.code == cmcg.ERR_UNSUPPORTED
+    # workspace too small
+    g = cmcg.make_grid(w.n, w.h)
+    o = cmcg.make_options(dt=w.dt_target)
+    need = cmcg.cmcg_workspace_size(g, o)
+    ws = torch.empty(need - 1024, dtype=torch.uint8, device="cuda")
+    c = torch.as_tensor(w.c.ravel(), device="cuda")
+    bc = cmcg.BC()
+    with pytest.raises(cmcg.CMCGError) as e:
+        cmcg.cmcg_create(g, c, w.omega, bc, o, ws, torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == cmcg.ERR_WORKSPACE
+
+
+# ---------------------------------------------------------------------------------------
+# Full size (257^3 sphere workload, the benchmark's configuration): sampled nodes against the
+# oracle run on each node's domain of dependence (N + 2 nodes in every direction).
+def crop(w, center, margin):
+    lo, hi = [], []
+    for a in range(3):
+        lo.append(max(0, center[a] - margin))
+        hi.append(min(w.n[a], center[a] + margin))
+    sl = tuple(slice(lo[a], hi[a] + 1) for a in reversed(range(3)))
+    faces = []
+    for a in range(3):
+        faces.append(w.faces[2 * a] if lo[a] == 0 else NEU)
+        faces.append(w.faces[2 * a + 1] if hi[a] == w.n[a] else NEU)
+    n = tuple(hi[a] - lo[a] for a in range(3))
+    sub = wl.Workload(name="crop", n=n, h=w.h, c=w.c[sl], omega=w.omega, faces=tuple(faces),
+                      dt_target=w.dt_target, order=w.order,
+                      mask=None if w.mask is None else w.mask[sl],
+                      f=None if w.f is None else w.f[sl], g=None if w.g is None else w.g[sl])
+    local = tuple(center[a] - lo[a] for a in reversed(range(3)))
+    return sub, sl, local
+
+
+@pytest.fixture(scope="module")
+def full_size():
+    w = wl.sphere_3d(n=256)
+    y0, v0 = wl.random_fields(w.shape, 2, 21)
+    act = 1.0 - (w.mask.astype(np.float64))
+    return w, y0 * act, v0 * act
+
+
+@pytest.mark.parametrize("precision,tol", [(cmcg.FP64, 1e-11), (cmcg.FP32, 1e-4)])
+def test_full_size_period_sampled(full_size, precision, tol):
+    w, y0, v0 = full_size
+    s = solver_of(w, precision)
+    uT, vT = [t.cpu().numpy() for t in s.wave_period(y0, v0, None, w.g)]
+    N = s.info["steps_per_period"]
+    samples = [(0, 0, 0), (128, 128, 103), (256, 40, 200), (7, 250, 128), (140, 131, 129)]
+    for cidx in samples:
+        sub, sl, local = crop(w, cidx, N + 3)
+        dz = dz_of(sub)
+        assert dz.N == N
+        yT, vTo = wave.period(dz, y0[sl], v0[sl], dz.load(sub.f, sub.g))
+        scale = max(np.abs(yT).max(), 1e-30)
+        assert abs(uT[sl][local] - yT[local]) <= tol * scale, (cidx, uT[sl][local], yT[local])
+        scale_v = max(np.abs(vTo).max(), 1e-30)
+        assert abs(vT[sl][local] - vTo[local]) <= tol * scale_v, cidx
+
+
+def test_full_size_adjoint_dot(full_size):
+    w, y0, v0 = full_size
+    s = solver_of(w)
+    a, b = wl.random_fields(w.shape, 2, 22)
+    act = 1.0 - w.mask.astype(np.float64)
+    a, b = a * act, b * act
+    p0, p1 = [t.cpu().numpy() for t in s.wave_period(y0, v0)]
+    q0, q1 = [t.cpu().numpy() for t in s.adjoint_period(a, b)]
+    lhs = np.sum(p0 * a) + np.sum(p1 * b)
+    rhs = np.sum(y0 * q0) + np.sum(v0 * q1)
+    scale = math.sqrt(np.sum(p0 ** 2) + np.sum(p1 ** 2)) * math.sqrt(np.sum(a ** 2) + np.sum(b ** 2))
+    assert abs(lhs - rhs) <= 1e-12 * scale
