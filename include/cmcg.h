@@ -60,6 +60,8 @@ extern "C" {
 
 /* ---- option flags ------------------------------------------------------------------ */
 #define CMCG_FLAG_HOST_IO 1 /* reserve a staging buffer in the workspace for cmcg_solve_host */
+#define CMCG_FLAG_TIMING 2  /* time the leapfrog step kernels with CUDA events on the handle's
+                               stream; results in cmcg_stats.step_seconds_* / step_launches_* */
 
 /* ---- precision of the wave stepping ------------------------------------------------ */
 #define CMCG_FP64 0  /* every operation in FP64                                            */
@@ -111,6 +113,10 @@ typedef struct {
     long long point_updates; /* grid-point leapfrog updates performed                      */
     double seconds;          /* wall time of the call                                     */
     long long kernel_launches; /* CUDA kernels this library launched during the call       */
+    /* CMCG_FLAG_TIMING: summed device time and launch count of the leapfrog step kernels
+       (forward and adjoint), split by stepping precision; 0 otherwise */
+    double step_seconds_fp32, step_seconds_fp64;
+    long long step_launches_fp32, step_launches_fp64;
 } cmcg_stats;
 
 typedef struct {

@@ -23,6 +23,7 @@ ERR_INVALID_ARG, ERR_CFL, ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_CUDA, ERR_DIVERGED
 BC_ABC, BC_NEUMANN, BC_DIRICHLET = 0, 1, 2
 FP64, FP32, MIXED = 0, 1, 2
 FLAG_HOST_IO = 1
+FLAG_TIMING = 2
 
 EXPORTED = (
     "cmcg_workspace_size", "cmcg_create", "cmcg_destroy", "cmcg_get_info", "cmcg_wave_period",
@@ -49,7 +50,9 @@ class Stats(C.Structure):
                 ("omega_tilde", C.c_double), ("omega_hat", C.c_double), ("rel_residual", C.c_double),
                 ("J0", C.c_double), ("J_final", C.c_double), ("lambda_re", C.c_double),
                 ("lambda_im", C.c_double), ("point_updates", C.c_longlong), ("seconds", C.c_double),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("step_seconds_fp32", C.c_double),
+                ("step_seconds_fp64", C.c_double), ("step_launches_fp32", C.c_longlong),
+                ("step_launches_fp64", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -76,6 +76,14 @@ struct cmcg_handle {
     // counters of the current call
     long long riesz_iters = 0;
     long long periods = 0;
+    // CMCG_FLAG_TIMING: event pairs around the step loops of the periods since the last sync
+    bool timing = false;
+    cudaEvent_t ev[8] = {};
+    int ev_used = 0;
+    bool ev_fp32[4] = {};
+    int ev_steps[4] = {};
+    double step_s[2] = {0, 0};     // [fp64, fp32]
+    long long step_n[2] = {0, 0};
     Red red() const { return Red{partials, tickets, sc}; }
 };
 
@@ -183,10 +191,41 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
 
 int cuda_status() { return cudaGetLastError() == cudaSuccess ? CMCG_OK : CMCG_ERR_CUDA; }
 
+// Fold completed event pairs into the per-precision step times.
+void collect_timing(cmcg_handle* H) {
+    for (int p = 0; p < H->ev_used; ++p) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, H->ev[2 * p], H->ev[2 * p + 1]) == cudaSuccess) {
+            H->step_s[H->ev_fp32[p] ? 1 : 0] += 1e-3 * ms;
+            H->step_n[H->ev_fp32[p] ? 1 : 0] += H->ev_steps[p];
+        }
+    }
+    H->ev_used = 0;
+}
+
 int sync_read(cmcg_handle* H) {
     cudaMemcpyAsync(H->hsc, H->sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, H->st);
     if (cudaStreamSynchronize(H->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    if (H->timing) collect_timing(H);
     return cuda_status();
+}
+
+// Event pair around a period's step loop (only with CMCG_FLAG_TIMING).  Returns the slot.
+int timing_begin(cmcg_handle* H, bool fp32, int steps) {
+    if (!H->timing) return -1;
+    if (H->ev_used == 4) {  // all slots busy: wait for them
+        cudaStreamSynchronize(H->st);
+        collect_timing(H);
+    }
+    const int p = H->ev_used++;
+    H->ev_fp32[p] = fp32;
+    H->ev_steps[p] = steps;
+    cudaEventRecord(H->ev[2 * p], H->st);
+    return p;
+}
+
+void timing_end(cmcg_handle* H, int p) {
+    if (p >= 0) cudaEventRecord(H->ev[2 * p + 1], H->st);
 }
 
 // ---- period drivers ------------------------------------------------------------------------
@@ -203,11 +242,13 @@ void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src
     T* prev = (T*)H->ya;
     const double* S = src ? H->S : nullptr;
     launch_start<T>(g, H->order, w0, w1, prev, cur, H->kap64, S, H->dt, zce, H->st);
+    const int tp = timing_begin(H, std::is_same<T, float>::value, H->N - 1);
     for (int n = 1; n < H->N; ++n) {
         const double th = H->omega * n * H->dt;
         launch_step<T>(g, H->order, cur, prev, kap, S, cos(th), sin(th), src ? kStepSrc : 0, zc, H->st);
         std::swap(cur, prev);
     }
+    timing_end(H, tp);
     const double thN = H->omega * H->N * H->dt;
     launch_end<T>(g, H->order, mode, cur, prev, w0, w1, H->kap64, H->mass, S, cos(thN), sin(thN), out0, out1,
                   H->red(), H->dt, zce, H->st);
@@ -228,6 +269,7 @@ void adjoint_period(cmcg_handle* H, const double* a, const double* b, int mode, 
     T* prev = (T*)H->yb;
     launch_adj_prep(g, b, H->mass, H->kap64, H->tmp, zce, H->st);
     launch_adj_start<T>(g, H->order, a, H->tmp, H->mass, H->kap64, cur, prev, H->dt, zce, H->st);
+    const int tp = timing_begin(H, std::is_same<T, float>::value, H->N - 1);
     for (int k = 0; k < H->N - 1; ++k) {
         int flags = 0;
         if (k == 0) flags |= kStepPrevScaled;
@@ -235,6 +277,7 @@ void adjoint_period(cmcg_handle* H, const double* a, const double* b, int mode, 
         launch_step<T>(g, H->order, cur, prev, kap, nullptr, 0.0, 0.0, flags, zc, H->st);
         std::swap(cur, prev);
     }
+    timing_end(H, tp);
     launch_adj_final<T>(g, H->order, mode, cur, prev, H->mass, H->kap64, a, b, d0, d1, o0, o1, gt1, H->red(), H->dt,
                         zce, H->st);
     H->periods += 1;
@@ -439,6 +482,9 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
 int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool want_J) {
     memset(st, 0, sizeof(*st));
     const long long launches0 = launch_count();
+    h->step_s[0] = h->step_s[1] = 0.0;
+    h->step_n[0] = h->step_n[1] = 0;
+    h->ev_used = 0;
     h->riesz_iters = 0;
     h->periods = 0;
     const long long n = h->g.np;
@@ -485,6 +531,11 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
     st->riesz_iterations = (int)h->riesz_iters;
     st->point_updates = periods_solve * (long long)h->N * n;
     st->kernel_launches = launch_count() - launches0;
+    if (h->timing) collect_timing(h);
+    st->step_seconds_fp64 = h->step_s[0];
+    st->step_seconds_fp32 = h->step_s[1];
+    st->step_launches_fp64 = h->step_n[0];
+    st->step_launches_fp32 = h->step_n[1];
     return rc;
 }
 
@@ -514,7 +565,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     cmcg_options o{};
     if (opts) o = *opts;
     if (o.precision < CMCG_FP64 || o.precision > CMCG_MIXED) return CMCG_ERR_INVALID_ARG;
-    if (o.flags & ~CMCG_FLAG_HOST_IO) return CMCG_ERR_INVALID_ARG;
+    if (o.flags & ~(CMCG_FLAG_HOST_IO | CMCG_FLAG_TIMING)) return CMCG_ERR_INVALID_ARG;
     if (o.dt < 0 || !isfinite(o.dt)) return CMCG_ERR_INVALID_ARG;
     fill_defaults(&o);
     unsigned abc = 0, dir = 0;
@@ -541,7 +592,12 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
         delete H;
         return CMCG_ERR_CUDA;
     }
+    H->timing = (o.flags & CMCG_FLAG_TIMING) != 0;
+    if (H->timing)
+        for (int e = 0; e < 8; ++e) cudaEventCreate(&H->ev[e]);
     auto fail = [&](int code) {
+        if (H->timing)
+            for (int e = 0; e < 8; ++e) cudaEventDestroy(H->ev[e]);
         cudaFreeHost(H->hsc);
         delete H;
         return code;
@@ -585,6 +641,8 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
 
 int cmcg_destroy(cmcg_handle* h) {
     if (!h) return CMCG_ERR_INVALID_ARG;
+    if (h->timing)
+        for (int e = 0; e < 8; ++e) cudaEventDestroy(h->ev[e]);
     cudaFreeHost(h->hsc);
     delete h;
     return CMCG_OK;

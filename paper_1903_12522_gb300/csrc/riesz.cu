@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(kT) k_dots_after_precond(long long n, const do
     }
     if (grid_sum<2>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
         const double rz_old = red.sc[SC_P_RZ];
-        red.sc[SC_P_BETA] = first ? 0.0 : -red.sc[SC_P_ALPHA] * acc[1] / rz_old;
+        // a zero residual (zero right-hand side) gives rz = 0: no direction update
+        red.sc[SC_P_BETA] = (first || rz_old == 0.0) ? 0.0 : -red.sc[SC_P_ALPHA] * acc[1] / rz_old;
         red.sc[SC_P_RZ] = acc[0];
     }
 }
@@ -271,7 +272,8 @@ __global__ void k_p_update(long long n, double* __restrict__ p, const double* __
 // alpha = rz / pAp; x += alpha p; r -= alpha Ap; rr = r.r.
 __global__ void __launch_bounds__(kT) k_xr_update(long long n, double* __restrict__ x, double* __restrict__ r,
                                                   const double* __restrict__ p, const double* __restrict__ Ap, Red red) {
-    const double alpha = red.sc[SC_P_RZ] / red.sc[SC_P_PAP];
+    const double pap = red.sc[SC_P_PAP];
+    const double alpha = pap != 0.0 ? red.sc[SC_P_RZ] / pap : 0.0;  // p = 0 only for a zero residual
     double acc[1] = {0.0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {

@@ -145,7 +145,8 @@ def test_solve_matches_direct(case, precision, tol, bound):
     assert wrel(dz, u.cpu().numpy(), U) <= bound, (name, st)
     assert st["point_updates"] == st["periods"] * dz.N * dz.size
     if not dz.has_dirichlet:
-        assert abs(st["lambda_im"]) <= 1e-8 * max(abs(st["lambda_re"]), 1e-300) + 1e-14
+        # Im lambda vanishes up to the solve's accuracy relative to the field's size
+        assert abs(st["lambda_im"]) <= bound * max(abs(st["lambda_re"]), float(np.abs(U).max()))
 
 
 def test_fp64_iterations_and_shift_match_oracle(case):
