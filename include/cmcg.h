@@ -184,6 +184,24 @@ int cmcg_solve_host(cmcg_handle* h, const double* f_host, const double* g_host, 
 
 const char* cmcg_status_string(int status);
 
+/* Allocation-free FP64 wave period (the paper has no counterpart; this entry point exists for
+ * callers that cannot allocate device memory, such as a plug-in inside a host application
+ * that owns the whole device-memory budget, or a real-time loop that must not take
+ * cudaMalloc's implicit device-wide synchronisation).  Computes what cmcg_wave_period computes
+ * for a handle of the same grid, c, omega, bc and dt with precision CMCG_FP64, without a handle
+ * or workspace: arguments as in cmcg_create and cmcg_wave_period (device pointers; stream is a
+ * cudaStream_t, NULL = default stream).  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Its scratch is one static 18 MiB device array inside this library, which every GPU
+ * that loads the library holds until the process exits; grids above 262,144 nodes (for example
+ * larger than 511^2 in 2D or 63^3 in 3D) are rejected with CMCG_ERR_WORKSPACE.  The first call
+ * on a device looks up the array's device address with cudaGetSymbolAddress (make that first
+ * call before any stream capture on that device).  Every call on a device shares the array and
+ * clears the parts that must start at zero; calls that overlap on the GPU (other streams or
+ * threads) race.  Returns after the stream has finished the call's work. */
+int cmcg_wave_period_static(const cmcg_grid* grid, const double* c, double omega, const cmcg_bc* bc,
+                            double dt, const double* u0, const double* v0, const double* f,
+                            const double* g, double* uT, double* vT, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -191,6 +191,17 @@ def cmcg_status_string(code: int) -> str:
     return load().cmcg_status_string(int(code)).decode()
 
 
+def cmcg_wave_period_static(grid: Grid, c, omega, bc: BC, dt, u0, v0, f, g, uT, vT, stream) -> int:
+    """The allocation-free FP64 period (static scratch inside the library); returns the status."""
+    lib = load()
+    fn = lib.cmcg_wave_period_static
+    P = C.c_void_p
+    fn.argtypes = [C.POINTER(Grid), P, C.c_double, C.POINTER(BC), C.c_double, P, P, P, P, P, P, P]
+    fn.restype = C.c_int
+    return int(fn(C.byref(grid), _ptr(c), float(omega), C.byref(bc), float(dt), _ptr(u0), _ptr(v0), _ptr(f),
+                  _ptr(g), _ptr(uT), _ptr(vT), stream))
+
+
 # ---- convenience wrapper ------------------------------------------------------------------
 class Solver:
     """A handle plus its caller-owned workspace (torch uint8 tensor on the device)."""

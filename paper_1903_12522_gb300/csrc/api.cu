@@ -542,6 +542,85 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
 
 }  // namespace
 
+// ---- period on caller-provided scratch (used by the allocation-free entry point) --------
+namespace cmcg {
+
+// Carve of the scratch a stand-alone FP64 period needs: coefficients, source, the two wave
+// buffers, masked copies of the initial data, reduction slots.
+static size_t scratch_layout(cmcg_handle* H, const Geom& g, char* base) {
+    Carver c{base};
+    const size_t np = (size_t)g.np;
+    H->kap64 = c.take<double>(np);
+    H->mass = c.take<double>(np);
+    H->mask = c.take<unsigned char>(np);
+    H->kap32 = nullptr;
+    H->S = c.take<double>(2 * np);
+    H->ya = c.take<double>(np);
+    H->yb = c.take<double>(np);
+    H->z0 = c.take<double>(np);
+    H->z1 = c.take<double>(np);
+    long long nb = std::max<long long>(kMaxBlocksReduce, plane_blocks(g, kZcEnds));
+    H->partials = c.take<double>((size_t)8 * nb);
+    H->tickets = c.take<unsigned>(kNumTickets);
+    H->sc = c.take<double>(SC_COUNT);
+    return c.off + 256;
+}
+
+int wave_period_in_scratch(const cmcg_grid* grid, const double* c, double omega, const cmcg_bc* bc,
+                           double dt_target, const double* u0, const double* v0, const double* f, const double* g,
+                           double* uT, double* vT, char* scratch, size_t scratch_bytes, cudaStream_t st) {
+    if (!valid_grid(grid) || !c || !bc || !u0 || !v0 || !uT || !vT || !scratch) return CMCG_ERR_INVALID_ARG;
+    if (!(omega > 0) || !isfinite(omega) || dt_target < 0 || !isfinite(dt_target)) return CMCG_ERR_INVALID_ARG;
+    unsigned abc = 0, dir = 0;
+    for (int fc = 0; fc < 2 * grid->dim; ++fc) {
+        const int code = bc->face[fc];
+        if (code == CMCG_BC_ABC) abc |= 1u << fc;
+        else if (code == CMCG_BC_DIRICHLET) dir |= 1u << fc;
+        else if (code != CMCG_BC_NEUMANN) return CMCG_ERR_INVALID_ARG;
+    }
+    cmcg_handle H;
+    H.g = make_geom(grid, abc);
+    H.order = grid->order;
+    H.opt.precision = CMCG_FP64;
+    H.st = st;
+    H.omega = omega;
+    H.T = 2.0 * kPi / omega;
+    if (scratch_layout(&H, H.g, nullptr) > scratch_bytes) return CMCG_ERR_WORKSPACE;
+    scratch_layout(&H, H.g, scratch);
+    double host_sc[SC_COUNT];
+    H.hsc = host_sc;
+    // the scratch keeps the previous call's contents: clear the reduction slots
+    cudaMemsetAsync(H.tickets, 0, sizeof(unsigned) * kNumTickets, st);
+    cudaMemsetAsync(H.sc, 0, sizeof(double) * SC_COUNT, st);
+    launch_setup_coeffs(H.g, c, bc->dirichlet_mask, dir, 1.0, H.kap64, nullptr, H.mass, H.mask, H.red(), st);
+    if (sync_read(&H) != CMCG_OK) return CMCG_ERR_CUDA;
+    if (host_sc[3] != 0.0) return CMCG_ERR_INVALID_ARG;
+    H.has_dir = host_sc[4] > 0.0;
+    uint64_t bits;
+    memcpy(&bits, &host_sc[5], sizeof(bits));
+    double cmax;
+    memcpy(&cmax, &bits, sizeof(cmax));
+    if (H.has_dir && H.order == 4) return CMCG_ERR_UNSUPPORTED;
+    const double dtt = dt_target > 0 ? dt_target : 0.5 * grid->h / (sqrt((double)grid->dim) * cmax);
+    H.N = (int)ceil(H.T / dtt - 1e-9);
+    if (H.N < 2) H.N = 2;
+    H.dt = H.T / H.N;
+    const double rho = (grid->order == 2 ? 4.0 * grid->dim : 16.0 * grid->dim / 3.0) / (grid->h * grid->h);
+    if (H.dt * H.dt * cmax * cmax * rho >= 4.0) return CMCG_ERR_CFL;
+    cudaMemsetAsync(H.sc, 0, sizeof(double) * SC_COUNT, st);
+    launch_setup_coeffs(H.g, c, bc->dirichlet_mask, dir, H.dt, H.kap64, nullptr, H.mass, H.mask, H.red(), st);
+    const bool src = f || g;
+    const int zce = H.g.dim == 3 ? kZcEnds : 1;
+    if (src) launch_make_source(H.g, f, g, H.kap64, H.S, zce, false, st);
+    launch_mask_copy(H.g, u0, H.kap64, H.z0, st);
+    launch_mask_copy(H.g, v0, H.kap64, H.z1, st);
+    forward_period<double>(&H, H.z0, H.z1, src, 1, uT, vT);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return cuda_status();
+}
+
+}  // namespace cmcg
+
 // ======================================================================================
 extern "C" {
 
