@@ -24,6 +24,7 @@ BC_ABC, BC_NEUMANN, BC_DIRICHLET = 0, 1, 2
 FP64, FP32, MIXED = 0, 1, 2
 FLAG_HOST_IO = 1
 FLAG_TIMING = 2
+FLAG_INEXACT_RIESZ = 4
 
 EXPORTED = (
     "cmcg_workspace_size", "cmcg_create", "cmcg_destroy", "cmcg_get_info", "cmcg_wave_period",

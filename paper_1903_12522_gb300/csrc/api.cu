@@ -53,7 +53,7 @@ struct cmcg_handle {
     bool has_dir = false;
     double sumM = 0, sumB = 0, sumW = 0;
     // coefficients
-    double *kap64 = nullptr, *mass = nullptr, *S = nullptr;
+    double *kap64 = nullptr, *mass = nullptr, *minv = nullptr, *S = nullptr;
     float* kap32 = nullptr;
     unsigned char* mask = nullptr;
     // wave buffers (sized for double; FP32 stepping uses the first half) + FP64 temp
@@ -66,6 +66,9 @@ struct cmcg_handle {
     double *pr, *pp, *pAp, *pzd;
     MGLevel lv[kMaxLevels];
     int nlev = 0;
+    int blk_level = -1;       // first level run inside one thread block (-1: none)
+    BlockLevels blk{};
+    int riesz_guess = 0;      // PCG iterations of the previous Riesz solve
     // host staging
     double* stage = nullptr;
     // reductions
@@ -123,24 +126,27 @@ void fill_defaults(cmcg_options* o) {
     if (!(o->inner_tol > 0)) o->inner_tol = 1e-3;
 }
 
-// Multigrid level geometries: halve every axis while all are even and stay >= 2.
+// Multigrid level geometries: every axis n -> ceil(n/2) while all axes keep >= 2 intervals.
+// The coarse spacing is the mean of the per-axis spacings n_f h / n_c (equal for square grids
+// and for even n; the preconditioner tolerates the small anisotropy otherwise).
 int mg_geometries(const Geom& fine, Geom* out) {
     int n = 0;
     out[n++] = fine;
     while (n < kMaxLevels) {
         const Geom& p = out[n - 1];
-        const bool even = (p.nx % 2 == 0) && (p.ny % 2 == 0) && (p.dim == 2 || p.nz % 2 == 0);
-        const bool big = p.nx / 2 >= 2 && p.ny / 2 >= 2 && (p.dim == 2 || p.nz / 2 >= 2);
-        if (!even || !big || p.np <= 64) break;
+        const bool big = p.nx >= 4 && p.ny >= 4 && (p.dim == 2 || p.nz >= 4);
+        if (!big || p.np <= 64) break;
         Geom c = p;
-        c.nx = p.nx / 2;
-        c.ny = p.ny / 2;
-        c.nz = p.dim == 3 ? p.nz / 2 : 0;
+        c.nx = (p.nx + 1) / 2;
+        c.ny = (p.ny + 1) / 2;
+        c.nz = p.dim == 3 ? (p.nz + 1) / 2 : 0;
         c.sx = c.nx + 1;
         c.sy = c.ny + 1;
         c.sz = c.nz + 1;
         c.np = (long long)c.sx * c.sy * c.sz;
-        c.h = p.h * 2.0;
+        double hs = p.nx * p.h / c.nx + p.ny * p.h / c.ny;
+        if (p.dim == 3) hs += p.nz * p.h / c.nz;
+        c.h = hs / p.dim;
         out[n++] = c;
     }
     return n;
@@ -152,6 +158,7 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
     const size_t np = (size_t)g.np;
     H->kap64 = c.take<double>(np);
     H->mass = c.take<double>(np);
+    H->minv = c.take<double>(np);
     H->mask = c.take<unsigned char>(np);
     H->kap32 = o.precision != CMCG_FP64 ? c.take<float>(np) : nullptr;
     H->S = c.take<double>(2 * np);
@@ -241,7 +248,14 @@ void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src
     T* cur = (T*)H->yb;
     T* prev = (T*)H->ya;
     const double* S = src ? H->S : nullptr;
-    launch_start<T>(g, H->order, w0, w1, prev, cur, H->kap64, S, H->dt, zce, H->st);
+    // T-precision copy of w0 for the endpoint stencils (FP32: second half of the ya buffer)
+    const T* w0t = (const T*)w0;
+    if (std::is_same<T, float>::value) {
+        float* w0f = (float*)H->ya + g.np;
+        launch_to_float(g.np, w0, w0f, H->st);
+        w0t = (const T*)w0f;
+    }
+    launch_start<T>(g, H->order, w0t, w1, prev, cur, kap, S, H->dt, zce, H->st);
     const int tp = timing_begin(H, std::is_same<T, float>::value, H->N - 1);
     for (int n = 1; n < H->N; ++n) {
         const double th = H->omega * n * H->dt;
@@ -250,7 +264,7 @@ void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src
     }
     timing_end(H, tp);
     const double thN = H->omega * H->N * H->dt;
-    launch_end<T>(g, H->order, mode, cur, prev, w0, w1, H->kap64, H->mass, S, cos(thN), sin(thN), out0, out1,
+    launch_end<T>(g, H->order, mode, cur, prev, w0t, w1, kap, H->mass, S, cos(thN), sin(thN), out0, out1,
                   H->red(), H->dt, zce, H->st);
     H->periods += 1;
 }
@@ -267,8 +281,9 @@ void adjoint_period(cmcg_handle* H, const double* a, const double* b, int mode, 
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     T* cur = (T*)H->ya;
     T* prev = (T*)H->yb;
-    launch_adj_prep(g, b, H->mass, H->kap64, H->tmp, zce, H->st);
-    launch_adj_start<T>(g, H->order, a, H->tmp, H->mass, H->kap64, cur, prev, H->dt, zce, H->st);
+    T* t = (T*)H->tmp;
+    launch_adj_prep<T>(g, b, H->mass, kap, t, zce, H->st);
+    launch_adj_start<T>(g, H->order, a, t, H->mass, kap, cur, prev, H->dt, zce, H->st);
     const int tp = timing_begin(H, std::is_same<T, float>::value, H->N - 1);
     for (int k = 0; k < H->N - 1; ++k) {
         int flags = 0;
@@ -278,28 +293,32 @@ void adjoint_period(cmcg_handle* H, const double* a, const double* b, int mode, 
         std::swap(cur, prev);
     }
     timing_end(H, tp);
-    launch_adj_final<T>(g, H->order, mode, cur, prev, H->mass, H->kap64, a, b, d0, d1, o0, o1, gt1, H->red(), H->dt,
-                        zce, H->st);
+    launch_adj_final<T>(g, H->order, mode, cur, prev, H->mass, kap, H->minv, a, b, d0, d1, o0, o1, gt1, H->red(),
+                        H->dt, zce, H->st);
     H->periods += 1;
 }
 
 // ---- Riesz map: FP64 flexible PCG with a FP32 multigrid V-cycle --------------------------
 float jacobi_omega(const Geom& g) { return g.dim == 3 ? 6.0f / 7.0f : 0.8f; }
 
+int coarse_sweeps(const Geom& g) {
+    const int nmax = std::max(g.nx, std::max(g.ny, g.nz));
+    return std::min(512, std::max(32, 8 * nmax * nmax));
+}
+
 void vcycle(cmcg_handle* H, int l) {
     MGLevel& L = H->lv[l];
     const float om = jacobi_omega(L.g);
-    if (l == H->nlev - 1) {
-        if (L.g.np <= mg_coarse_max_nodes()) {
-            const int nmax = std::max(L.g.nx, std::max(L.g.ny, L.g.nz));
-            const int sweeps = std::min(400, std::max(16, 4 * nmax * nmax));
-            launch_mg_coarse_solve(L, L.x, L.b, sweeps, om, H->st);
-        } else {
-            launch_mg_jacobi(L, nullptr, L.x, L.b, om, true, H->st);
-            for (int s = 0; s < 7; ++s) {
-                launch_mg_jacobi(L, L.x, L.x2, L.b, om, false, H->st);
-                std::swap(L.x, L.x2);
-            }
+    if (l == H->blk_level) {
+        const BlockLevels& B = H->blk;
+        launch_mg_block_vcycle(B, L.b, L.x, om, 2, coarse_sweeps(B.g[B.n - 1]), H->st);
+        return;
+    }
+    if (l == H->nlev - 1) {  // coarsest level too large for one block: Jacobi sweeps
+        launch_mg_jacobi(L, nullptr, L.x, L.b, om, true, H->st);
+        for (int s = 0; s < 7; ++s) {
+            launch_mg_jacobi(L, L.x, L.x2, L.b, om, false, H->st);
+            std::swap(L.x, L.x2);
         }
         return;
     }
@@ -340,9 +359,17 @@ int riesz_solve(cmcg_handle* H, const double* rhs, double* x, int* iters_out) {
     int it = 0;
     bool converged = false;
     double bb = -1.0;
+    // the previous solve's iteration count, less a margin, runs without host checks
+    const int blind = std::max(0, std::min(H->riesz_guess - 2, H->opt.riesz_max_iter - 1));
     for (it = 1; it <= H->opt.riesz_max_iter; ++it) {
         launch_applyK(g, H->order, H->mask, H->pp, H->pAp, H->pp, red, SC_P_PAP, H->st);
         launch_pcg_xr_update(n, x, H->pr, H->pp, H->pAp, red, H->st);
+        if (it <= blind) {
+            precondition(H, H->pr);
+            launch_pcg_dots_after_precond(n, H->pr, H->lv[0].x, H->pAp, H->pzd, red, H->st);
+            launch_pcg_p_update(n, H->pp, H->pzd, red, false, H->st);
+            continue;
+        }
         int rc = sync_read(H);
         if (rc != CMCG_OK) return rc;
         bb = H->hsc[SC_P_BB];
@@ -357,6 +384,7 @@ int riesz_solve(cmcg_handle* H, const double* rhs, double* x, int* iters_out) {
         launch_pcg_p_update(n, H->pp, H->pzd, red, false, H->st);
     }
     if (project) launch_mean_remove(g, x, H->volume, red, H->st);
+    if (converged) H->riesz_guess = it;
     H->riesz_iters += std::min(it, H->opt.riesz_max_iter);
     if (iters_out) *iters_out = std::min(it, H->opt.riesz_max_iter);
     int rc = cuda_status();
@@ -368,17 +396,70 @@ int riesz_solve(cmcg_handle* H, const double* rhs, double* x, int* iters_out) {
 // Gradient of J at (w0, w1) (with the sources if src): ghat -> (gh0, gh1), g~ -> (gt0, gt1),
 // z -> (z0, z1); J -> sc[SC_J].
 template <typename T>
-int gradient(cmcg_handle* H, const double* w0, const double* w1, bool src, const double* dd0, const double* dd1) {
+int gradient(cmcg_handle* H, const double* w0, const double* w1, bool src, const double* dd0, const double* dd1,
+             bool riesz = true) {
     forward_period<T>(H, w0, w1, src, 0, H->z0, H->z1);
     adjoint_period<T>(H, H->z0, H->z1, 0, dd0, dd1, H->gh0, H->gh1, H->gt1);
+    if (!riesz) return CMCG_OK;
     int rc = riesz_solve(H, H->gh0, H->gt0, nullptr);
     return rc < 0 ? rc : CMCG_OK;
+}
+
+bool inexact(const cmcg_handle* H) { return (H->opt.flags & CMCG_FLAG_INEXACT_RIESZ) != 0; }
+
+// Approximate Riesz map z = B rhat into (r0, r1): one V-cycle on rhat0 (W-mean removed when K
+// is singular), M^-1 rhat1; reduces gamma = z . rhat (and the Polak-Ribiere beta unless first).
+void apply_B(cmcg_handle* H, bool first) {
+    const Geom& g = H->g;
+    Red red = H->red();
+    launch_to_float(g.np, H->rh0, H->lv[0].b, H->st);
+    vcycle(H, 0);
+    if (!H->has_dir) launch_wsum_float(g, H->lv[0].x, red, H->st);
+    launch_fcg_dots(g, H->lv[0].x, H->volume, !H->has_dir, H->rh0, H->rh1, H->minv, H->gh0, H->gh1, H->r0, H->r1,
+                    red, first, H->st);
+    H->riesz_iters += 1;
+}
+
+// Flexible CG (Polak-Ribiere) on the current gradient in (gh0, gh1) with z = B rhat;
+// iterate accumulated into (w0, w1) (v -= alpha d).
+template <typename T>
+int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_out) {
+    const long long n = H->g.np;
+    Red red = H->red();
+    cudaMemcpyAsync(H->rh0, H->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+    cudaMemcpyAsync(H->rh1, H->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+    apply_B(H, true);
+    cudaMemcpyAsync(H->d0, H->r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+    cudaMemcpyAsync(H->d1, H->r1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+    int rc = sync_read(H);
+    if (rc != CMCG_OK) return rc;
+    if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
+    double rel = H->hsc[SC_REL];
+    int it = 0;
+    if (rel > tol) {
+        for (it = 1; it <= max_iter; ++it) {
+            gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1, false);        // 5.1: ghat_d = H d
+            launch_fcg_update(n, H->w0, H->w1, H->rh0, H->rh1, H->d0, H->d1, H->gh0, H->gh1, red, H->st);
+            apply_B(H, false);                                             // 5.2 on the residual
+            launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st);  // 5.7
+            rc = sync_read(H);
+            if (rc != CMCG_OK) return rc;
+            if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
+            rel = H->hsc[SC_REL];
+            if (rel <= tol) break;
+        }
+        if (it > max_iter) it = max_iter;
+    }
+    *iters = it;
+    *rel_out = rel;
+    return rel <= tol ? CMCG_OK : CMCG_NOT_CONVERGED;
 }
 
 // CG loop of Steps (4)-(5) on the current gradient (gh, gt) with homogeneous periods in
 // precision T; iterate accumulated into (w0, w1) (v -= alpha d).
 template <typename T>
 int cg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_out) {
+    if (inexact(H)) return fcg_loop<T>(H, tol, max_iter, iters, rel_out);
     const long long n = H->g.np;
     Red red = H->red();
     launch_cg_init(n, H->gt0, H->gt1, H->gh0, H->gh1, H->r0, H->r1, H->rh0, H->rh1, H->d0, H->d1, red, H->st);
@@ -417,7 +498,7 @@ int solve_plain(cmcg_handle* H, double tol, cmcg_stats* stats) {
     // (1) v = 0; (2)-(3) gradient with the sources and its Riesz representer
     launch_fill(H->w0, n, 0.0, H->st);
     launch_fill(H->w1, n, 0.0, H->st);
-    int rc = gradient<T>(H, H->w0, H->w1, true, H->w0, H->w1);
+    int rc = gradient<T>(H, H->w0, H->w1, true, H->w0, H->w1, !inexact(H));
     if (rc < 0) return rc;
     rc = sync_read(H);
     if (rc != CMCG_OK) return rc;
@@ -443,9 +524,16 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
     int rc = CMCG_OK;
     const int max_outer = 50;
     for (outer = 0; outer < max_outer; ++outer) {
-        rc = gradient<double>(H, H->wo0, H->wo1, true, H->wo0, H->wo1);
+        rc = gradient<double>(H, H->wo0, H->wo1, true, H->wo0, H->wo1, !inexact(H));
         if (rc < 0) return rc;
-        launch_scalar_residual(n, H->gt0, H->gt1, H->gh0, H->gh1, red, SC_R7, H->st);
+        if (inexact(H)) {
+            cudaMemcpyAsync(H->rh0, H->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+            cudaMemcpyAsync(H->rh1, H->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+            apply_B(H, true);
+            launch_scalar_residual(n, H->r0, H->r1, H->rh0, H->rh1, red, SC_R7, H->st);
+        } else {
+            launch_scalar_residual(n, H->gt0, H->gt1, H->gh0, H->gh1, red, SC_R7, H->st);
+        }
         rc = sync_read(H);
         if (rc != CMCG_OK) return rc;
         const double gam = H->hsc[SC_R7];
@@ -644,7 +732,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     cmcg_options o{};
     if (opts) o = *opts;
     if (o.precision < CMCG_FP64 || o.precision > CMCG_MIXED) return CMCG_ERR_INVALID_ARG;
-    if (o.flags & ~(CMCG_FLAG_HOST_IO | CMCG_FLAG_TIMING)) return CMCG_ERR_INVALID_ARG;
+    if (o.flags & ~(CMCG_FLAG_HOST_IO | CMCG_FLAG_TIMING | CMCG_FLAG_INEXACT_RIESZ)) return CMCG_ERR_INVALID_ARG;
     if (o.dt < 0 || !isfinite(o.dt)) return CMCG_ERR_INVALID_ARG;
     fill_defaults(&o);
     unsigned abc = 0, dir = 0;
@@ -713,6 +801,20 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     for (int l = 1; l < H->nlev; ++l) launch_mg_coarsen_mask(H->lv[l - 1], H->lv[l], H->st);
     if (!H->has_dir)
         for (int l = 0; l < H->nlev; ++l) H->lv[l].mask = nullptr;
+    launch_reciprocal(H->g.np, H->mass, H->minv, H->st);
+    H->blk_level = -1;
+    for (int l = 0; l < H->nlev; ++l)
+        if (H->lv[l].g.np <= mg_block_max_nodes()) {
+            H->blk_level = l;
+            break;
+        }
+    if (H->blk_level >= 0) {
+        H->blk.n = std::min(H->nlev - H->blk_level, kBlockLevelsMax);
+        for (int i = 0; i < H->blk.n; ++i) {
+            H->blk.g[i] = H->lv[H->blk_level + i].g;
+            H->blk.mask[i] = H->lv[H->blk_level + i].mask;
+        }
+    }
     if (sync_read(H) != CMCG_OK) return fail(CMCG_ERR_CUDA);
     *out = H;
     return CMCG_OK;

@@ -3,9 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace cmcg {
 
-struct Geom;
 
 // Reduction context: per-block partials, a ticket counter and the device scalar slots.
 struct Red {
@@ -25,20 +26,21 @@ template <typename T>
 void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, const double* S, double cs,
                  double sn, int flags, int zc, cudaStream_t st);
 template <typename T>
-void launch_start(const Geom& g, int order, const double* w0, const double* w1, T* y0, T* y1,
-                  const double* kap64, const double* S, double dt, int zc, cudaStream_t st);
+void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y0, T* y1, const T* kap,
+                  const double* S, double dt, int zc, cudaStream_t st);
 template <typename T>
-void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const double* w0,
-                const double* w1, const double* kap64, const double* mass, const double* S, double cs,
-                double sn, double* out0, double* out1, Red red, double dt, int zc, cudaStream_t st);
-void launch_adj_prep(const Geom& g, const double* b, const double* mass, const double* kap64, double* t, int zc,
+void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const T* w0t, const double* w1,
+                const T* kap, const double* mass, const double* S, double cs, double sn, double* out0, double* out1,
+                Red red, double dt, int zc, cudaStream_t st);
+template <typename T>
+void launch_adj_prep(const Geom& g, const double* b, const double* mass, const T* kap, T* t, int zc,
                      cudaStream_t st);
 template <typename T>
-void launch_adj_start(const Geom& g, int order, const double* a, const double* t, const double* mass,
-                      const double* kap64, T* cur, T* prev, double dt, int zc, cudaStream_t st);
+void launch_adj_start(const Geom& g, int order, const double* a, const T* t, const double* mass, const T* kap,
+                      T* cur, T* prev, double dt, int zc, cudaStream_t st);
 template <typename T>
-void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass,
-                      const double* kap64, const double* z0, const double* z1, const double* d0, const double* d1,
+void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass, const T* kap,
+                      const double* minv, const double* z0, const double* z1, const double* d0, const double* d1,
                       double* o0, double* o1, double* gt1, Red red, double dt, int zc, cudaStream_t st);
 void launch_make_source(const Geom& g, const double* f, const double* gb, const double* kap64, double* S, int zc,
                         bool accumulate, cudaStream_t st);
@@ -68,6 +70,14 @@ void launch_cg_direction(long long n, const double* r0, const double* r1, double
 void launch_recover(const Geom& g, const double* w0, const double* w1, double omega_hat, const double* S,
                     const double* kap64, const double* mass, double* u, Red red, cudaStream_t st);
 void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t st);
+void launch_reciprocal(long long n, const double* m, double* out, cudaStream_t st);
+// Flexible CG with an approximate Riesz map (one multigrid V-cycle).
+void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double* rh1, const double* d0,
+                       const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st);
+void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, const double* rh0,
+                     const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,
+                     double* z1, Red red, bool first, cudaStream_t st);
+void launch_wsum_float(const Geom& g, const float* x, Red red, cudaStream_t st);
 void launch_shift(long long n, double* u, const double* kap64, double lre, double lim, cudaStream_t st);
 void launch_scalar_residual(long long n, const double* r0, const double* r1, const double* rh0,
                             const double* rh1, Red red, int slot, cudaStream_t st);
@@ -84,8 +94,19 @@ void launch_mg_jacobi(const MGLevel& L, const float* xin, float* xout, const flo
 void launch_mg_residual(const MGLevel& L, const float* x, const float* b, float* r, cudaStream_t st);
 void launch_mg_restrict(const MGLevel& fine, const float* rf, const MGLevel& coarse, float* bc, cudaStream_t st);
 void launch_mg_prolong_add(const MGLevel& coarse, const float* xc, const MGLevel& fine, float* xf, cudaStream_t st);
-void launch_mg_coarse_solve(const MGLevel& L, float* x, const float* b, int sweeps, float omega, cudaStream_t st);
-int mg_coarse_max_nodes();
+// Coarse end of the V-cycle in one thread block (levels up to kBlockLevelsMax, total nodes
+// within the shared-memory budget).
+constexpr int kBlockLevelsMax = 8;
+constexpr int kBlockMaxNodes = 6000;  // nodes of the first in-block level
+struct BlockLevels {
+    int n;
+    Geom g[kBlockLevelsMax];
+    const unsigned char* mask[kBlockLevelsMax];
+};
+void launch_mg_block_vcycle(const BlockLevels& lv, const float* b, float* x, float omega, int nu, int coarse_sweeps,
+                            cudaStream_t st);
+size_t mg_block_smem_bytes(const BlockLevels& lv);
+int mg_block_max_nodes();
 // FP64 PCG pieces on the fine level
 void launch_applyK(const Geom& g, int order, const unsigned char* mask, const double* x, double* y,
                    const double* dotwith, Red red, int slot, cudaStream_t st);

@@ -242,6 +242,91 @@ __global__ void k_shift(long long n, double* __restrict__ u, const double* __res
     }
 }
 
+// 1/M on active nodes (0 on Dirichlet nodes).
+__global__ void k_reciprocal(long long n, const double* __restrict__ m, double* __restrict__ out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride)
+        out[j] = m[j] != 0.0 ? 1.0 / m[j] : 0.0;
+}
+
+// ---- flexible CG with an approximate Riesz map B ~ E^-1 --------------------------------
+// Step 5.3-5.5 with the dual residual: alpha = gamma / (ghat_d . d); v -= alpha d;
+// rhat -= alpha ghat_d.  The primal residual z = B rhat is formed afterwards (k_fcg_dots).
+__global__ void __launch_bounds__(kT) k_fcg_update(long long n, double* __restrict__ w0, double* __restrict__ w1,
+                                                   double* __restrict__ rh0, double* __restrict__ rh1,
+                                                   const double* __restrict__ d0, const double* __restrict__ d1,
+                                                   const double* __restrict__ gh0, const double* __restrict__ gh1,
+                                                   double* __restrict__ sc) {
+    const double alpha = sc[SC_GAMMA] / sc[SC_GD];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        w0[j] -= alpha * d0[j];
+        w1[j] -= alpha * d1[j];
+        rh0[j] -= alpha * gh0[j];
+        rh1[j] -= alpha * gh1[j];
+    }
+}
+
+// z0 from the FP32 V-cycle output with the W-weighted mean removed when K is singular,
+// z1 = M^-1 rhat1; gamma' = z . rhat; for the Polak-Ribiere update also z . ghat_d:
+// beta = -alpha (z . ghat_d) / gamma (= gamma'/gamma when B is exactly E^-1).  first != 0:
+// Step (4), gamma0 = gamma', no beta.
+__global__ void __launch_bounds__(kT) k_fcg_dots(Geom g, const float* __restrict__ zf, double inv_volume,
+                                                 int remove_mean, const double* __restrict__ rh0,
+                                                 const double* __restrict__ rh1, const double* __restrict__ minv,
+                                                 const double* __restrict__ gh0, const double* __restrict__ gh1,
+                                                 double* __restrict__ z0, double* __restrict__ z1, Red red,
+                                                 int first) {
+    const double mu = remove_mean ? red.sc[SC_P_XW] * inv_volume : 0.0;
+    double acc[2] = {0.0, 0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
+        const double m = minv[j];
+        const double a0 = m != 0.0 ? (double)zf[j] - mu : 0.0;
+        const double a1 = rh1[j] * m;
+        z0[j] = a0;
+        z1[j] = a1;
+        acc[0] += a0 * rh0[j] + a1 * rh1[j];
+        if (!first) acc[1] += a0 * gh0[j] + a1 * gh1[j];
+    }
+    if (grid_sum<2>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
+        const double gnew = acc[0];
+        if (first) {
+            red.sc[SC_GAMMA0] = gnew;
+            red.sc[SC_REL] = gnew > 0.0 ? 1.0 : 0.0;
+            red.sc[SC_STATUS] = (isfinite(gnew) && gnew >= 0.0) ? 0.0 : 1.0;
+        } else {
+            const double gamma = red.sc[SC_GAMMA];
+            const double alpha = gamma / red.sc[SC_GD];
+            red.sc[SC_ALPHA] = alpha;
+            red.sc[SC_BETA] = -alpha * acc[1] / gamma;
+            red.sc[SC_REL] = sqrt(fmax(gnew, 0.0) / red.sc[SC_GAMMA0]);
+            if (!isfinite(alpha) || !(red.sc[SC_GD] > 0.0) || !isfinite(gnew)) red.sc[SC_STATUS] = 1.0;
+        }
+        red.sc[SC_GAMMA_NEW] = gnew;
+        red.sc[SC_GAMMA] = gnew;
+    }
+}
+
+// sum_j W_j x_j of an FP32 field into sc[SC_P_XW].
+__global__ void __launch_bounds__(kT) k_wsum_float(Geom g, const float* __restrict__ x, Red red) {
+    double acc[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
+        const unsigned t = (unsigned)j / (unsigned)g.sx;
+        const int ix = (int)((unsigned)j - t * (unsigned)g.sx);
+        const int iz = (int)(t / (unsigned)g.sy);
+        const int iy = (int)(t - (unsigned)iz * (unsigned)g.sy);
+        int e = (ix == 0 || ix == g.nx) + (iy == 0 || iy == g.ny);
+        if (g.dim == 3) e += (iz == 0 || iz == g.nz);
+        acc[0] += (double)(x[j] / (float)(1 << e));
+    }
+    if (grid_sum<1>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
+        const double hd = g.dim == 3 ? g.h * g.h * g.h : g.h * g.h;
+        red.sc[SC_P_XW] = hd * acc[0];
+    }
+}
+
 }  // namespace
 
 void launch_setup_coeffs(const Geom& g, const double* c, const unsigned char* user_mask, unsigned face_dir,
@@ -301,6 +386,34 @@ void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t
 void launch_shift(long long n, double* u, const double* kap64, double lre, double lim, cudaStream_t st) {
     note_launch(1);
     k_shift<<<vec_blocks(n), kT, 0, st>>>(n, u, kap64, lre, lim);
+}
+
+}  // namespace cmcg
+
+namespace cmcg {
+
+void launch_reciprocal(long long n, const double* m, double* out, cudaStream_t st) {
+    note_launch(1);
+    k_reciprocal<<<vec_blocks(n), kT, 0, st>>>(n, m, out);
+}
+
+void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double* rh1, const double* d0,
+                       const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st) {
+    note_launch(1);
+    k_fcg_update<<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, rh0, rh1, d0, d1, gh0, gh1, red.sc);
+}
+
+void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, const double* rh0,
+                     const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,
+                     double* z1, Red red, bool first, cudaStream_t st) {
+    note_launch(1);
+    k_fcg_dots<<<vec_blocks(g.np), kT, 0, st>>>(g, zf, 1.0 / volume, remove_mean ? 1 : 0, rh0, rh1, minv, gh0, gh1,
+                                                z0, z1, red, first ? 1 : 0);
+}
+
+void launch_wsum_float(const Geom& g, const float* x, Red red, cudaStream_t st) {
+    note_launch(1);
+    k_wsum_float<<<vec_blocks(g.np), kT, 0, st>>>(g, x, red);
 }
 
 }  // namespace cmcg

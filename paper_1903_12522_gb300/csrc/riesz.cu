@@ -2,11 +2,13 @@
 // (grad s, grad phi)), solved matrix-free on the GPU.  The paper solves this SPD,
 // omega-independent problem with a two-level Schwarz method (Sec. 4.4); here it is FP64
 // flexible PCG whose preconditioner is one geometric multigrid V-cycle in FP32:
-//   - vertex-centred coarsening n -> n/2 (co-located nodes), rediscretised K on each level,
-//     Dirichlet mask taken from the co-located fine node;
+//   - vertex-centred coarsening n -> ceil(n/2) per axis (nested 2:1 for even n, general
+//     linear interpolation for odd n), rediscretised K on each level, Dirichlet mask taken
+//     from the nearest fine node;
 //   - damped Jacobi smoothing, residual restriction by the transpose of (bi/tri)linear
 //     interpolation, prolongation by that interpolation;
-//   - the coarsest level solved by Jacobi sweeps inside one thread block.
+//   - the levels below kBlockMaxNodes nodes run as one V-cycle inside one thread block in
+//     shared memory; its coarsest level is solved by Jacobi sweeps.
 #include <math.h>
 
 #include "common.cuh"
@@ -17,7 +19,6 @@ namespace cmcg {
 namespace {
 
 constexpr int kT = 256;
-constexpr int kCoarseMax = 4096;
 
 inline unsigned vec_blocks(long long n) {
     long long b = (n + kT - 1) / kT;
@@ -27,6 +28,17 @@ inline unsigned vec_blocks(long long n) {
 }
 
 inline unsigned node_blocks(long long n) { return (unsigned)((n + kT - 1) / kT); }
+
+inline dim3 mg_grid(const Geom& g, int zc) {
+    const long long plane = (long long)g.sx * g.sy;
+    return dim3((unsigned)((plane + kT - 1) / kT), (unsigned)((g.sz + zc - 1) / zc), 1);
+}
+
+template <typename R>
+struct Ld {
+    const R* __restrict__ p;
+    __device__ __forceinline__ R operator()(long long i) const { return p[i]; }
+};
 
 // Node coordinates (node counts stay below 2^31, so 32-bit division suffices).
 __device__ __forceinline__ void coords(const Geom& g, long long j, int& ix, int& iy, int& iz) {
@@ -45,100 +57,202 @@ struct LdM {  // masked load: Dirichlet nodes read as 0
 };
 
 // ---- multigrid (FP32) ---------------------------------------------------------------------
+// K-form on every level: K = (h^d / h^2) s Lt with s = prod_a w(j_a) in {1, 1/2, 1/4, 1/8};
+// diag K = (h^d / h^2) s 2d.  Damped Jacobi: x += omega (b - K x) / diag K.
+// Iterates are kept exactly 0 on Dirichlet nodes, so neighbour loads need no mask.
+__device__ __forceinline__ int axis_ends(const Geom& g, int ix, int iy, int iz) {
+    int e = (ix == 0 || ix == g.nx) + (iy == 0 || iy == g.ny);
+    if (g.dim == 3) e += (iz == 0 || iz == g.nz);
+    return e;
+}
+
+struct MGConst {
+    float cK;     // h^d / h^2
+    float cB;     // h^2 / (2d h^d)
+    float inv2d;  // 1 / (2d)
+};
+
+__device__ __forceinline__ MGConst mg_const(const Geom& g) {
+    MGConst c;
+    const float h = (float)g.h;
+    const float hd = g.dim == 3 ? h * h * h : h * h;
+    c.cK = hd / (h * h);
+    c.inv2d = 1.f / (float)(2 * g.dim);
+    c.cB = (h * h) / (hd * (float)(2 * g.dim));
+    return c;
+}
+
+// One damped Jacobi update at node j (xin == nullptr: from x = 0).
+__device__ __forceinline__ float jacobi_node(const Geom& g, const MGConst& c, const float* xin, float bj, float omega,
+                                             long long j, int ix, int iy, int iz) {
+    const float inv_s = (float)(1 << axis_ends(g, ix, iy, iz));
+    if (!xin) return omega * c.cB * inv_s * bj;
+    Ld<float> f{xin};
+    const float L = lap_t<2, float>(g, f, j, ix, iy, iz);
+    return xin[j] + omega * (c.cB * inv_s * bj - c.inv2d * L);
+}
+
+__device__ __forceinline__ float residual_node(const Geom& g, const MGConst& c, const float* x, float bj, long long j,
+                                               int ix, int iy, int iz) {
+    const float s = 1.f / (float)(1 << axis_ends(g, ix, iy, iz));
+    Ld<float> f{x};
+    return bj - c.cK * s * lap_t<2, float>(g, f, j, ix, iy, iz);
+}
+
+// Coarsening n_f -> n_c = ceil(n_f / 2) per axis: fine node i sits at coarse coordinate
+// xi = i n_c / n_f; it interpolates from coarse nodes J0 = floor(xi) (weight 1 - t) and
+// J0 + 1 (weight t), t = xi - J0.  For even n_f this is the nested 2:1 scheme (t in {0, 1/2}).
+// Restriction is the exact transpose of this interpolation.
+struct Interp1 {
+    int j0;
+    float t;
+};
+
+__device__ __forceinline__ Interp1 interp1(int i, int nf, int nc) {
+    const long long num = (long long)i * nc;
+    Interp1 r;
+    r.j0 = (int)(num / nf);
+    r.t = (float)(num - (long long)r.j0 * nf) / (float)nf;
+    if (r.j0 >= nc) {
+        r.j0 = nc;
+        r.t = 0.f;
+    }
+    return r;
+}
+
+// weight with which fine node i contributes to coarse node J along one axis
+__device__ __forceinline__ float interp_weight(int i, int J, int nf, int nc) {
+    const Interp1 p = interp1(i, nf, nc);
+    if (p.j0 == J) return 1.f - p.t;
+    if (p.j0 + 1 == J) return p.t;
+    return 0.f;
+}
+
+__device__ __forceinline__ void fine_range(int J, int nf, int nc, int& lo, int& hi) {
+    // fine nodes whose interpolation stencil can include coarse node J
+    lo = (int)(((long long)(J - 1) * nf) / nc);
+    hi = (int)(((long long)(J + 1) * nf + nc - 1) / nc);
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > nf ? nf : hi;
+}
+
+__device__ __forceinline__ float restrict_node(const Geom& gf, const Geom& gc, const float* rf, int jx, int jy,
+                                               int jz) {
+    int xlo, xhi, ylo, yhi, zlo = 0, zhi = 0;
+    fine_range(jx, gf.nx, gc.nx, xlo, xhi);
+    fine_range(jy, gf.ny, gc.ny, ylo, yhi);
+    if (gf.dim == 3) fine_range(jz, gf.nz, gc.nz, zlo, zhi);
+    float acc = 0.f;
+    for (int fz = zlo; fz <= zhi; ++fz) {
+        const float wz = gf.dim == 3 ? interp_weight(fz, jz, gf.nz, gc.nz) : 1.f;
+        if (wz == 0.f) continue;
+        for (int fy = ylo; fy <= yhi; ++fy) {
+            const float wy = interp_weight(fy, jy, gf.ny, gc.ny);
+            if (wy == 0.f) continue;
+            for (int fx = xlo; fx <= xhi; ++fx) {
+                const float wx = interp_weight(fx, jx, gf.nx, gc.nx);
+                if (wx == 0.f) continue;
+                acc += wx * wy * wz * rf[node(gf, fx, fy, fz)];
+            }
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ float prolong_node(const Geom& gc, const float* xc, const Geom& gf, int ix, int iy, int iz) {
+    const Interp1 px = interp1(ix, gf.nx, gc.nx), py = interp1(iy, gf.ny, gc.ny);
+    const int x1 = px.t > 0.f ? px.j0 + 1 : px.j0, y1 = py.t > 0.f ? py.j0 + 1 : py.j0;
+    const float ax = 1.f - px.t, ay = 1.f - py.t;
+    float v = ay * (ax * xc[node(gc, px.j0, py.j0, 0)] + px.t * xc[node(gc, x1, py.j0, 0)]) +
+              py.t * (ax * xc[node(gc, px.j0, y1, 0)] + px.t * xc[node(gc, x1, y1, 0)]);
+    if (gf.dim == 3) {
+        const Interp1 pz = interp1(iz, gf.nz, gc.nz);
+        const int z1 = pz.t > 0.f ? pz.j0 + 1 : pz.j0;
+        const long long offz0 = (long long)pz.j0 * gc.sx * gc.sy, offz1 = (long long)z1 * gc.sx * gc.sy;
+        const float* c0 = xc + offz0;
+        const float* c1 = xc + offz1;
+        const float v0 = ay * (ax * c0[node(gc, px.j0, py.j0, 0)] + px.t * c0[node(gc, x1, py.j0, 0)]) +
+                         py.t * (ax * c0[node(gc, px.j0, y1, 0)] + px.t * c0[node(gc, x1, y1, 0)]);
+        const float v1 = ay * (ax * c1[node(gc, px.j0, py.j0, 0)] + px.t * c1[node(gc, x1, py.j0, 0)]) +
+                         py.t * (ax * c1[node(gc, px.j0, y1, 0)] + px.t * c1[node(gc, x1, y1, 0)]);
+        v = (1.f - pz.t) * v0 + pz.t * v1;
+    }
+    return v;
+}
+
+struct PlaneIt {
+    int ix, iy, z0, z1;
+    bool valid;
+};
+
+__device__ __forceinline__ PlaneIt plane_it(const Geom& g, int zc) {
+    PlaneIt m;
+    const unsigned plane = (unsigned)g.sx * (unsigned)g.sy;
+    const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+    m.valid = p < plane;
+    const unsigned pp = m.valid ? p : 0u;
+    m.iy = (int)(pp / (unsigned)g.sx);
+    m.ix = (int)(pp - (unsigned)m.iy * (unsigned)g.sx);
+    m.z0 = blockIdx.y * zc;
+    m.z1 = min(m.z0 + zc, g.sz);
+    return m;
+}
+
 __global__ void __launch_bounds__(kT) k_jacobi(Geom g, const unsigned char* __restrict__ mask,
                                                const float* __restrict__ xin, float* __restrict__ xout,
-                                               const float* __restrict__ b, float omega, int zero_init) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= g.np) return;
-    if (mask && mask[j]) {
-        xout[j] = 0.f;
-        return;
-    }
-    int ix, iy, iz;
-    coords(g, j, ix, iy, iz);
-    const float W = (float)weight(g, ix, iy, iz);
-    const float h2 = (float)(g.h * g.h);
-    const float twod = (float)(2 * g.dim);
-    if (zero_init) {
-        xout[j] = omega * h2 * b[j] / (twod * W);
-    } else {
-        LdM<float> f{xin, mask};
-        const float L = lap_t<2, float>(g, f, j, ix, iy, iz);
-        xout[j] = xin[j] + omega * (h2 * b[j] / W - L) / twod;
+                                               const float* __restrict__ b, float omega, int zc) {
+    const PlaneIt m = plane_it(g, zc);
+    if (!m.valid) return;
+    const MGConst c = mg_const(g);
+    for (int iz = m.z0; iz < m.z1; ++iz) {
+        const long long j = node(g, m.ix, m.iy, iz);
+        if (mask && mask[j]) {
+            xout[j] = 0.f;
+            continue;
+        }
+        xout[j] = jacobi_node(g, c, xin, b[j], omega, j, m.ix, m.iy, iz);
     }
 }
 
 __global__ void __launch_bounds__(kT) k_residual(Geom g, const unsigned char* __restrict__ mask,
                                                  const float* __restrict__ x, const float* __restrict__ b,
-                                                 float* __restrict__ r) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= g.np) return;
-    if (mask && mask[j]) {
-        r[j] = 0.f;
-        return;
+                                                 float* __restrict__ r, int zc) {
+    const PlaneIt m = plane_it(g, zc);
+    if (!m.valid) return;
+    const MGConst c = mg_const(g);
+    for (int iz = m.z0; iz < m.z1; ++iz) {
+        const long long j = node(g, m.ix, m.iy, iz);
+        if (mask && mask[j]) {
+            r[j] = 0.f;
+            continue;
+        }
+        r[j] = residual_node(g, c, x, b[j], j, m.ix, m.iy, iz);
     }
-    int ix, iy, iz;
-    coords(g, j, ix, iy, iz);
-    const float W = (float)weight(g, ix, iy, iz);
-    const float ih2 = (float)(1.0 / (g.h * g.h));
-    LdM<float> f{x, mask};
-    r[j] = b[j] - W * ih2 * lap_t<2, float>(g, f, j, ix, iy, iz);
 }
 
 // b_c[J] = sum over fine nodes i with |i - 2J|_inf <= 1 of prod_a (1 or 1/2) r_f[i].
 __global__ void __launch_bounds__(kT) k_restrict(Geom gf, const float* __restrict__ rf, Geom gc,
-                                                 const unsigned char* __restrict__ maskc, float* __restrict__ bc) {
-    const long long J = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (J >= gc.np) return;
-    if (maskc && maskc[J]) {
-        bc[J] = 0.f;
-        return;
+                                                 const unsigned char* __restrict__ maskc, float* __restrict__ bc,
+                                                 int zc) {
+    const PlaneIt m = plane_it(gc, zc);
+    if (!m.valid) return;
+    for (int iz = m.z0; iz < m.z1; ++iz) {
+        const long long J = node(gc, m.ix, m.iy, iz);
+        bc[J] = (maskc && maskc[J]) ? 0.f : restrict_node(gf, gc, rf, m.ix, m.iy, iz);
     }
-    int jx, jy, jz;
-    coords(gc, J, jx, jy, jz);
-    const int cx = 2 * jx, cy = 2 * jy, cz = 2 * jz;
-    float acc = 0.f;
-    const int zlo = gf.dim == 3 ? -1 : 0, zhi = gf.dim == 3 ? 1 : 0;
-    for (int dz = zlo; dz <= zhi; ++dz) {
-        const int fz = cz + dz;
-        if (fz < 0 || fz > gf.nz) continue;
-        const float wz = dz == 0 ? 1.f : 0.5f;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int fy = cy + dy;
-            if (fy < 0 || fy > gf.ny) continue;
-            const float wy = dy == 0 ? 1.f : 0.5f;
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int fx = cx + dx;
-                if (fx < 0 || fx > gf.nx) continue;
-                const float wx = dx == 0 ? 1.f : 0.5f;
-                acc += wx * wy * wz * rf[node(gf, fx, fy, fz)];
-            }
-        }
-    }
-    bc[J] = acc;
 }
 
 // x_f[i] += interpolated x_c.
 __global__ void __launch_bounds__(kT) k_prolong_add(Geom gc, const float* __restrict__ xc, Geom gf,
-                                                    const unsigned char* __restrict__ maskf, float* __restrict__ xf) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= gf.np) return;
-    if (maskf && maskf[i]) return;
-    int ix, iy, iz;
-    coords(gf, i, ix, iy, iz);
-    const int x0 = ix >> 1, x1 = (ix + 1) >> 1;
-    const int y0 = iy >> 1, y1 = (iy + 1) >> 1;
-    const int z0 = iz >> 1, z1 = (iz + 1) >> 1;
-    float v;
-    if (gf.dim == 3) {
-        v = 0.125f * (xc[node(gc, x0, y0, z0)] + xc[node(gc, x1, y0, z0)] + xc[node(gc, x0, y1, z0)] +
-                      xc[node(gc, x1, y1, z0)] + xc[node(gc, x0, y0, z1)] + xc[node(gc, x1, y0, z1)] +
-                      xc[node(gc, x0, y1, z1)] + xc[node(gc, x1, y1, z1)]);
-    } else {
-        v = 0.25f * (xc[node(gc, x0, y0, 0)] + xc[node(gc, x1, y0, 0)] + xc[node(gc, x0, y1, 0)] +
-                     xc[node(gc, x1, y1, 0)]);
+                                                    const unsigned char* __restrict__ maskf, float* __restrict__ xf,
+                                                    int zc) {
+    const PlaneIt m = plane_it(gf, zc);
+    if (!m.valid) return;
+    for (int iz = m.z0; iz < m.z1; ++iz) {
+        const long long i = node(gf, m.ix, m.iy, iz);
+        if (maskf && maskf[i]) continue;
+        xf[i] += prolong_node(gc, xc, gf, m.ix, m.iy, iz);
     }
-    xf[i] += v;
 }
 
 __global__ void k_coarsen_mask(Geom gf, const unsigned char* __restrict__ mf, Geom gc, unsigned char* __restrict__ mc) {
@@ -146,37 +260,98 @@ __global__ void k_coarsen_mask(Geom gf, const unsigned char* __restrict__ mf, Ge
     if (J >= gc.np) return;
     int jx, jy, jz;
     coords(gc, J, jx, jy, jz);
-    mc[J] = mf[node(gf, 2 * jx, 2 * jy, 2 * jz)];
+    // the fine node nearest to the coarse node's position
+    const int fx = (int)(((long long)jx * gf.nx * 2 + gc.nx) / (2 * gc.nx));
+    const int fy = (int)(((long long)jy * gf.ny * 2 + gc.ny) / (2 * gc.ny));
+    const int fz = gf.dim == 3 ? (int)(((long long)jz * gf.nz * 2 + gc.nz) / (2 * gc.nz)) : 0;
+    mc[J] = mf[node(gf, fx, fy, fz)];
 }
 
-// Coarsest level: damped Jacobi sweeps in shared memory inside one block.
-__global__ void __launch_bounds__(1024) k_coarse(Geom g, const unsigned char* __restrict__ mask, float* __restrict__ xg,
-                                                 const float* __restrict__ b, int sweeps, float omega) {
-    extern __shared__ float sm[];
-    float* x = sm;
-    float* xn = sm + g.np;
-    const float h2 = (float)(g.h * g.h);
-    const float twod = (float)(2 * g.dim);
-    for (long long j = threadIdx.x; j < g.np; j += blockDim.x) x[j] = 0.f;
+// The coarse end of the V-cycle inside one thread block: levels 0..n-1 of BlockLevels live
+// in shared memory (x, x2, b, r per level); b of the first level comes from global memory and
+// its x goes back.  Same smoother, restriction and prolongation as the grid-wide kernels.
+__device__ void blk_jacobi(const Geom& g, const unsigned char* mask, const float* xin, float* xout, const float* b,
+                           float omega) {
+    const MGConst c = mg_const(g);
+    for (int j = threadIdx.x; j < (int)g.np; j += blockDim.x) {
+        if (mask && mask[j]) {
+            xout[j] = 0.f;
+            continue;
+        }
+        int ix, iy, iz;
+        coords(g, j, ix, iy, iz);
+        xout[j] = jacobi_node(g, c, xin, b[j], omega, j, ix, iy, iz);
+    }
     __syncthreads();
-    for (int s = 0; s < sweeps; ++s) {
-        for (long long j = threadIdx.x; j < g.np; j += blockDim.x) {
-            if (mask && mask[j]) {
-                xn[j] = 0.f;
-                continue;
-            }
+}
+
+__global__ void __launch_bounds__(1024) k_block_vcycle(BlockLevels lv, const float* __restrict__ bglob,
+                                                       float* __restrict__ xglob, float omega, int nu,
+                                                       int coarse_sweeps) {
+    extern __shared__ float sm[];
+    float *x[kBlockLevelsMax], *x2[kBlockLevelsMax], *b[kBlockLevelsMax], *r[kBlockLevelsMax];
+    {
+        float* p = sm;
+        for (int l = 0; l < lv.n; ++l) {
+            const int np = (int)lv.g[l].np;
+            x[l] = p;
+            x2[l] = p + np;
+            b[l] = p + 2 * np;
+            r[l] = p + 3 * np;
+            p += 4 * np;
+        }
+    }
+    for (int j = threadIdx.x; j < (int)lv.g[0].np; j += blockDim.x) b[0][j] = bglob[j];
+    __syncthreads();
+    // descend
+    for (int l = 0; l + 1 < lv.n; ++l) {
+        const Geom& g = lv.g[l];
+        blk_jacobi(g, lv.mask[l], nullptr, x[l], b[l], omega);
+        for (int s = 1; s < nu; ++s) {
+            blk_jacobi(g, lv.mask[l], x[l], x2[l], b[l], omega);
+            float* t = x[l]; x[l] = x2[l]; x2[l] = t;
+        }
+        const MGConst c = mg_const(g);
+        for (int j = threadIdx.x; j < (int)g.np; j += blockDim.x) {
             int ix, iy, iz;
             coords(g, j, ix, iy, iz);
-            const float W = (float)weight(g, ix, iy, iz);
-            LdM<float> f{x, mask};
-            const float L = lap_t<2, float>(g, f, j, ix, iy, iz);
-            xn[j] = x[j] + omega * (h2 * b[j] / W - L) / twod;
+            r[l][j] = (lv.mask[l] && lv.mask[l][j]) ? 0.f : residual_node(g, c, x[l], b[l][j], j, ix, iy, iz);
         }
         __syncthreads();
-        for (long long j = threadIdx.x; j < g.np; j += blockDim.x) x[j] = xn[j];
+        const Geom& gc = lv.g[l + 1];
+        for (int J = threadIdx.x; J < (int)gc.np; J += blockDim.x) {
+            int jx, jy, jz;
+            coords(gc, J, jx, jy, jz);
+            b[l + 1][J] = (lv.mask[l + 1] && lv.mask[l + 1][J]) ? 0.f : restrict_node(g, gc, r[l], jx, jy, jz);
+        }
         __syncthreads();
     }
-    for (long long j = threadIdx.x; j < g.np; j += blockDim.x) xg[j] = x[j];
+    // coarsest
+    {
+        const int l = lv.n - 1;
+        blk_jacobi(lv.g[l], lv.mask[l], nullptr, x[l], b[l], omega);
+        for (int s = 1; s < coarse_sweeps; ++s) {
+            blk_jacobi(lv.g[l], lv.mask[l], x[l], x2[l], b[l], omega);
+            float* t = x[l]; x[l] = x2[l]; x2[l] = t;
+        }
+    }
+    // ascend
+    for (int l = lv.n - 2; l >= 0; --l) {
+        const Geom& g = lv.g[l];
+        const Geom& gc = lv.g[l + 1];
+        for (int j = threadIdx.x; j < (int)g.np; j += blockDim.x) {
+            if (lv.mask[l] && lv.mask[l][j]) continue;
+            int ix, iy, iz;
+            coords(g, j, ix, iy, iz);
+            x[l][j] += prolong_node(gc, x[l + 1], g, ix, iy, iz);
+        }
+        __syncthreads();
+        for (int s = 0; s < nu; ++s) {
+            blk_jacobi(g, lv.mask[l], x[l], x2[l], b[l], omega);
+            float* t = x[l]; x[l] = x2[l]; x2[l] = t;
+        }
+    }
+    for (int j = threadIdx.x; j < (int)lv.g[0].np; j += blockDim.x) xglob[j] = x[0][j];
 }
 
 // ---- FP64 PCG pieces ----------------------------------------------------------------------
@@ -195,7 +370,7 @@ __global__ void __launch_bounds__(kT) k_applyK(Geom g, const unsigned char* __re
         }
         int ix, iy, iz;
         coords(g, j, ix, iy, iz);
-        LdM<double> f{x, mask};
+        Ld<double> f{x};  // PCG vectors are zero on Dirichlet nodes
         const double v = weight(g, ix, iy, iz) * ih2 * lap_t<ORDER, double>(g, f, j, ix, iy, iz);
         y[j] = v;
         if (dotwith) acc[0] += dotwith[j] * v;
@@ -317,30 +492,42 @@ void launch_mg_coarsen_mask(const MGLevel& fine, const MGLevel& coarse, cudaStre
 void launch_mg_jacobi(const MGLevel& L, const float* xin, float* xout, const float* b, float omega, bool zero_init,
                       cudaStream_t st) {
     note_launch(1);
-    k_jacobi<<<node_blocks(L.g.np), kT, 0, st>>>(L.g, L.mask, xin, xout, b, omega, zero_init ? 1 : 0);
+    const int zc = L.g.dim == 3 ? 8 : 1;
+    k_jacobi<<<mg_grid(L.g, zc), kT, 0, st>>>(L.g, L.mask, zero_init ? nullptr : xin, xout, b, omega, zc);
 }
 
 void launch_mg_residual(const MGLevel& L, const float* x, const float* b, float* r, cudaStream_t st) {
     note_launch(1);
-    k_residual<<<node_blocks(L.g.np), kT, 0, st>>>(L.g, L.mask, x, b, r);
+    const int zc = L.g.dim == 3 ? 8 : 1;
+    k_residual<<<mg_grid(L.g, zc), kT, 0, st>>>(L.g, L.mask, x, b, r, zc);
 }
 
 void launch_mg_restrict(const MGLevel& fine, const float* rf, const MGLevel& coarse, float* bc, cudaStream_t st) {
     note_launch(1);
-    k_restrict<<<node_blocks(coarse.g.np), kT, 0, st>>>(fine.g, rf, coarse.g, coarse.mask, bc);
+    const int zc = coarse.g.dim == 3 ? 4 : 1;
+    k_restrict<<<mg_grid(coarse.g, zc), kT, 0, st>>>(fine.g, rf, coarse.g, coarse.mask, bc, zc);
 }
 
 void launch_mg_prolong_add(const MGLevel& coarse, const float* xc, const MGLevel& fine, float* xf, cudaStream_t st) {
     note_launch(1);
-    k_prolong_add<<<node_blocks(fine.g.np), kT, 0, st>>>(coarse.g, xc, fine.g, fine.mask, xf);
+    const int zc = fine.g.dim == 3 ? 8 : 1;
+    k_prolong_add<<<mg_grid(fine.g, zc), kT, 0, st>>>(coarse.g, xc, fine.g, fine.mask, xf, zc);
 }
 
-int mg_coarse_max_nodes() { return kCoarseMax; }
+int mg_block_max_nodes() { return kBlockMaxNodes; }
 
-void launch_mg_coarse_solve(const MGLevel& L, float* x, const float* b, int sweeps, float omega, cudaStream_t st) {
+size_t mg_block_smem_bytes(const BlockLevels& lv) {
+    size_t n = 0;
+    for (int l = 0; l < lv.n; ++l) n += 4 * (size_t)lv.g[l].np;
+    return n * sizeof(float);
+}
+
+void launch_mg_block_vcycle(const BlockLevels& lv, const float* b, float* x, float omega, int nu, int coarse_sweeps,
+                            cudaStream_t st) {
     note_launch(1);
-    const size_t smem = 2 * (size_t)L.g.np * sizeof(float);
-    k_coarse<<<1, 1024, smem, st>>>(L.g, L.mask, x, b, sweeps, omega);
+    const size_t smem = mg_block_smem_bytes(lv);
+    cudaFuncSetAttribute(k_block_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_block_vcycle<<<1, 1024, smem, st>>>(lv, b, x, omega, nu, coarse_sweeps);
 }
 
 void launch_applyK(const Geom& g, int order, const unsigned char* mask, const double* x, double* y,

@@ -57,10 +57,10 @@ struct LdD {  // loads T, returns double
 };
 
 template <typename T>
-struct Diff {  // (double) a[i] - b[i]
+struct DiffT {  // a[i] - b[i] in T
     const T* __restrict__ a;
-    const double* __restrict__ b;
-    __device__ __forceinline__ double operator()(long long i) const { return (double)a[i] - b[i]; }
+    const T* __restrict__ b;
+    __device__ __forceinline__ T operator()(long long i) const { return a[i] - b[i]; }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -134,72 +134,88 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
 }
 
 // ---------------------------------------------------------------------------------------
+// The endpoint kernels compute in the stepping precision T: the FP32 path does its stencils
+// and pointwise algebra in FP32 and only its FP64-facing outputs (z, ghat, g~1) and the
+// reductions in FP64.  w0t is the T-precision copy of the initial displacement w0.
+template <typename R>
+__device__ __forceinline__ R weight_t(const Geom& g, int ix, int iy, int iz) {
+    const R h = (R)g.h;
+    R w = (g.dim == 3) ? h * h * h : h * h;
+    if (ix == 0 || ix == g.nx) w *= R(0.5);
+    if (iy == 0 || iy == g.ny) w *= R(0.5);
+    if (g.dim == 3 && (iz == 0 || iz == g.nz)) w *= R(0.5);
+    return w;
+}
+
 // Period start: y0 = w0, y1 = w0 + dt (1 - beta) w1 + (S_re - kappa Lt w0) / 2.
 template <typename T, int ORDER, bool SRC>
-__global__ void __launch_bounds__(kThreads) k_start(const double* __restrict__ w0, const double* __restrict__ w1,
+__global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, const double* __restrict__ w1,
                                                     T* __restrict__ y0, T* __restrict__ y1,
-                                                    const double* __restrict__ kap64, const double* __restrict__ S,
+                                                    const T* __restrict__ kap, const double* __restrict__ S,
                                                     Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid) return;
-    Ld<double> f{w0};
+    Ld<T> f{w0t};
+    const T dtT = (T)dt;
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
-        const double k = kap64[j];
-        if (k == 0.0) {
+        const T k = kap[j];
+        if (k == T(0)) {
             y0[j] = T(0);
             y1[j] = T(0);
             continue;
         }
-        const double L = lap_t<ORDER, double>(g, f, j, m.ix, m.iy, iz);
-        const double beta = num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-        double v = w0[j] + dt * (1.0 - beta) * w1[j] - 0.5 * k * L;
-        if (SRC) v += 0.5 * S[2 * j];
-        y0[j] = (T)w0[j];
-        y1[j] = (T)v;
+        const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+        const T w0j = w0t[j];
+        T v = w0j + dtT * (T(1) - beta) * (T)w1[j] - T(0.5) * k * L;
+        if (SRC) v += (T)(0.5 * S[2 * j]);
+        y0[j] = w0j;
+        y1[j] = v;
     }
 }
 
 // Period end: vN, mismatch, energy operator and J (MODE 0), or (uT, vT) (MODE 1).
 template <typename T, int ORDER, bool SRC, int MODE>
 __global__ void __launch_bounds__(kThreads) k_end(const T* __restrict__ yN, const T* __restrict__ yNm1,
-                                                  const double* __restrict__ w0, const double* __restrict__ w1,
-                                                  const double* __restrict__ kap64, const double* __restrict__ mass,
+                                                  const T* __restrict__ w0t, const double* __restrict__ w1,
+                                                  const T* __restrict__ kap, const double* __restrict__ mass,
                                                   const double* __restrict__ S, double cs, double sn,
                                                   double* __restrict__ out0, double* __restrict__ out1,
                                                   Red red, Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
     double acc[1] = {0.0};
     if (m.valid) {
-        LdD<T> fy{yN};
-        Diff<T> fe{yN, w0};
-        const double ih2 = 1.0 / (g.h * g.h);
+        Ld<T> fy{yN};
+        DiffT<T> fe{yN, w0t};
+        const T ih2 = T(1) / (T)(g.h * g.h);
+        const T dtT = (T)dt;
         for (int iz = m.z0; iz < m.z1; ++iz) {
             const long long j = node(g, m.ix, m.iy, iz);
-            const double k = kap64[j];
-            if (k == 0.0) {
+            const T k = kap[j];
+            if (k == T(0)) {
                 out0[j] = 0.0;
                 out1[j] = 0.0;
                 continue;
             }
-            const double L = lap_t<ORDER, double>(g, fy, j, m.ix, m.iy, iz);
-            const double beta = num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-            double src = 0.0;
-            if (SRC) src = S[2 * j] * cs + S[2 * j + 1] * sn;
-            const double yn = (double)yN[j];
-            const double vN = ((yn - (double)yNm1[j]) / dt + (src - k * L) / (2.0 * dt)) / (1.0 + beta);
+            const T L = lap_t<ORDER, T>(g, fy, j, m.ix, m.iy, iz);
+            const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+            T src = T(0);
+            if (SRC) src = (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
+            const T yn = yN[j];
+            const T vN = ((yn - yNm1[j]) / dtT + (src - k * L) / (T(2) * dtT)) / (T(1) + beta);
             if (MODE == 1) {
-                out0[j] = yn;
-                out1[j] = vN;
+                out0[j] = (double)yn;
+                out1[j] = (double)vN;
             } else {
-                const double e0 = yn - w0[j];
-                const double e1 = vN - w1[j];
-                const double W = weight(g, m.ix, m.iy, iz);
-                const double z0 = W * ih2 * lap_t<ORDER, double>(g, fe, j, m.ix, m.iy, iz);
-                const double z1 = mass[j] * e1;
-                out0[j] = z0;
-                out1[j] = z1;
-                acc[0] += 0.5 * (e0 * z0 + e1 * z1);
+                const T e0 = yn - w0t[j];
+                const T e1 = vN - (T)w1[j];
+                const T W = weight_t<T>(g, m.ix, m.iy, iz);
+                const T z0 = W * ih2 * lap_t<ORDER, T>(g, fe, j, m.ix, m.iy, iz);
+                const T z1 = (T)mass[j] * e1;
+                out0[j] = (double)z0;
+                out1[j] = (double)z1;
+                acc[0] += 0.5 * (double)(e0 * z0 + e1 * z1);
             }
         }
     }
@@ -209,57 +225,59 @@ __global__ void __launch_bounds__(kThreads) k_end(const T* __restrict__ yN, cons
 }
 
 // Adjoint start, part 1: t = D^-1 b = b / (M (1 + beta)).
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_adj_prep(const double* __restrict__ b, const double* __restrict__ mass,
-                                                       const double* __restrict__ kap64, double* __restrict__ t,
-                                                       Geom g, int zc) {
+                                                       const T* __restrict__ kap, T* __restrict__ t, Geom g, int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid) return;
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
-        const double k = kap64[j];
-        if (k == 0.0) {
-            t[j] = 0.0;
+        const T k = kap[j];
+        if (k == T(0)) {
+            t[j] = T(0);
             continue;
         }
-        const double beta = num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-        t[j] = b[j] / (mass[j] * (1.0 + beta));
+        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+        t[j] = (T)b[j] / ((T)mass[j] * (T(1) + beta));
     }
 }
 
 // Adjoint start, part 2 (transposed end velocity):
 //   ybar_N = a + M t / dt - (dt/2) K t,  u_{N-1} = D^-1 ybar_N,  prev = C u_N / M = t / dt.
 template <typename T, int ORDER>
-__global__ void __launch_bounds__(kThreads) k_adj_start(const double* __restrict__ a, const double* __restrict__ t,
-                                                        const double* __restrict__ mass, const double* __restrict__ kap64,
+__global__ void __launch_bounds__(kThreads) k_adj_start(const double* __restrict__ a, const T* __restrict__ t,
+                                                        const double* __restrict__ mass, const T* __restrict__ kap,
                                                         T* __restrict__ cur, T* __restrict__ prev, Geom g, double dt,
                                                         int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid) return;
-    Ld<double> f{t};
+    Ld<T> f{t};
+    const T dtT = (T)dt;
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
-        const double k = kap64[j];
-        if (k == 0.0) {
+        const T k = kap[j];
+        if (k == T(0)) {
             cur[j] = T(0);
             prev[j] = T(0);
             continue;
         }
-        const double L = lap_t<ORDER, double>(g, f, j, m.ix, m.iy, iz);
-        const double beta = num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-        const double tj = t[j];
-        const double u = (a[j] / mass[j] + tj / dt - k * L / (2.0 * dt)) / (1.0 + beta);
-        cur[j] = (T)u;
-        prev[j] = (T)(tj / dt);
+        const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+        const T tj = t[j];
+        const T u = ((T)a[j] / (T)mass[j] + tj / dtT - k * L / (T(2) * dtT)) / (T(1) + beta);
+        cur[j] = u;
+        prev[j] = tj / dtT;
     }
 }
 
 // Adjoint final (transposed start half-kick), from s = M^-1 ybar_1 and u_1:
 //   q0 = M (s - (1 - beta) u_1) - (dt^2/2) K s,   q1 = dt M (1 - beta) s.
 // MODE 1 writes q.  MODE 0 forms the CG gradient ghat = q - z, g~1 = ghat1 / M, and reduces
-// (ghat . d, sum ghat0).
+// (ghat . d, sum ghat0) in FP64.
 template <typename T, int ORDER, int MODE>
 __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s, const T* __restrict__ u1,
-                                                        const double* __restrict__ mass, const double* __restrict__ kap64,
+                                                        const double* __restrict__ mass, const T* __restrict__ kap,
+                                                        const double* __restrict__ minv,
                                                         const double* __restrict__ z0, const double* __restrict__ z1,
                                                         const double* __restrict__ d0, const double* __restrict__ d1,
                                                         double* __restrict__ o0, double* __restrict__ o1,
@@ -267,33 +285,34 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
     const PlaneMap m = plane_map(g, zc);
     double acc[2] = {0.0, 0.0};
     if (m.valid) {
-        LdD<T> f{s};
-        const double ih2 = 1.0 / (g.h * g.h);
+        Ld<T> f{s};
+        const T ih2 = T(1) / (T)(g.h * g.h);
+        const T dtT = (T)dt;
         for (int iz = m.z0; iz < m.z1; ++iz) {
             const long long j = node(g, m.ix, m.iy, iz);
-            const double k = kap64[j];
-            if (k == 0.0) {
+            const T k = kap[j];
+            if (k == T(0)) {
                 o0[j] = 0.0;
                 o1[j] = 0.0;
                 if (MODE == 0) gt1[j] = 0.0;
                 continue;
             }
-            const double L = lap_t<ORDER, double>(g, f, j, m.ix, m.iy, iz);
-            const double beta = num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-            const double W = weight(g, m.ix, m.iy, iz);
-            const double M = mass[j];
-            const double sj = (double)s[j];
-            const double q0 = M * (sj - (1.0 - beta) * (double)u1[j]) - 0.5 * dt * dt * W * ih2 * L;
-            const double q1 = dt * M * (1.0 - beta) * sj;
+            const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+            const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+            const T W = weight_t<T>(g, m.ix, m.iy, iz);
+            const T M = (T)mass[j];
+            const T sj = s[j];
+            const T q0 = M * (sj - (T(1) - beta) * u1[j]) - T(0.5) * dtT * dtT * W * ih2 * L;
+            const T q1 = dtT * M * (T(1) - beta) * sj;
             if (MODE == 1) {
-                o0[j] = q0;
-                o1[j] = q1;
+                o0[j] = (double)q0;
+                o1[j] = (double)q1;
             } else {
-                const double g0 = q0 - z0[j];
-                const double g1 = q1 - z1[j];
+                const double g0 = (double)q0 - z0[j];
+                const double g1 = (double)q1 - z1[j];
                 o0[j] = g0;
                 o1[j] = g1;
-                gt1[j] = g1 / M;
+                gt1[j] = g1 * minv[j];
                 acc[0] += g0 * d0[j] + g1 * d1[j];
                 acc[1] += g0;
             }
@@ -382,28 +401,28 @@ void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, 
 }
 
 template <typename T>
-void launch_start(const Geom& g, int order, const double* w0, const double* w1, T* y0, T* y1,
-                  const double* kap64, const double* S, double dt, int zc, cudaStream_t st) {
+void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y0, T* y1, const T* kap,
+                  const double* S, double dt, int zc, cudaStream_t st) {
     note_launch(1);
     const dim3 grid = plane_grid(g, zc);
     if (order == 2) {
-        if (S) k_start<T, 2, true><<<grid, kThreads, 0, st>>>(w0, w1, y0, y1, kap64, S, g, dt, zc);
-        else k_start<T, 2, false><<<grid, kThreads, 0, st>>>(w0, w1, y0, y1, kap64, S, g, dt, zc);
+        if (S) k_start<T, 2, true><<<grid, kThreads, 0, st>>>(w0t, w1, y0, y1, kap, S, g, dt, zc);
+        else k_start<T, 2, false><<<grid, kThreads, 0, st>>>(w0t, w1, y0, y1, kap, S, g, dt, zc);
     } else {
-        if (S) k_start<T, 4, true><<<grid, kThreads, 0, st>>>(w0, w1, y0, y1, kap64, S, g, dt, zc);
-        else k_start<T, 4, false><<<grid, kThreads, 0, st>>>(w0, w1, y0, y1, kap64, S, g, dt, zc);
+        if (S) k_start<T, 4, true><<<grid, kThreads, 0, st>>>(w0t, w1, y0, y1, kap, S, g, dt, zc);
+        else k_start<T, 4, false><<<grid, kThreads, 0, st>>>(w0t, w1, y0, y1, kap, S, g, dt, zc);
     }
 }
 
 template <typename T>
-void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const double* w0,
-                const double* w1, const double* kap64, const double* mass, const double* S, double cs,
-                double sn, double* out0, double* out1, Red red, double dt, int zc, cudaStream_t st) {
+void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const T* w0t, const double* w1,
+                const T* kap, const double* mass, const double* S, double cs, double sn, double* out0, double* out1,
+                Red red, double dt, int zc, cudaStream_t st) {
     note_launch(1);
     const dim3 grid = plane_grid(g, zc);
-#define CMCG_END(O, SRC, MODE)                                                                              \
-    k_end<T, O, SRC, MODE><<<grid, kThreads, 0, st>>>(yN, yNm1, w0, w1, kap64, mass, S, cs, sn, out0, out1, \
-                                                      red, g, dt, zc)
+#define CMCG_END(O, SRC, MODE)                                                                                \
+    k_end<T, O, SRC, MODE><<<grid, kThreads, 0, st>>>(yN, yNm1, w0t, w1, kap, mass, S, cs, sn, out0, out1, red, \
+                                                      g, dt, zc)
     const bool src = S != nullptr;
     if (order == 2) {
         if (mode == 0) { if (src) CMCG_END(2, true, 0); else CMCG_END(2, false, 0); }
@@ -415,31 +434,32 @@ void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, 
 #undef CMCG_END
 }
 
-void launch_adj_prep(const Geom& g, const double* b, const double* mass, const double* kap64, double* t, int zc,
+template <typename T>
+void launch_adj_prep(const Geom& g, const double* b, const double* mass, const T* kap, T* t, int zc,
                      cudaStream_t st) {
     note_launch(1);
-    k_adj_prep<<<plane_grid(g, zc), kThreads, 0, st>>>(b, mass, kap64, t, g, zc);
+    k_adj_prep<T><<<plane_grid(g, zc), kThreads, 0, st>>>(b, mass, kap, t, g, zc);
 }
 
 template <typename T>
-void launch_adj_start(const Geom& g, int order, const double* a, const double* t, const double* mass,
-                      const double* kap64, T* cur, T* prev, double dt, int zc, cudaStream_t st) {
+void launch_adj_start(const Geom& g, int order, const double* a, const T* t, const double* mass, const T* kap,
+                      T* cur, T* prev, double dt, int zc, cudaStream_t st) {
     note_launch(1);
     if (order == 2)
-        k_adj_start<T, 2><<<plane_grid(g, zc), kThreads, 0, st>>>(a, t, mass, kap64, cur, prev, g, dt, zc);
+        k_adj_start<T, 2><<<plane_grid(g, zc), kThreads, 0, st>>>(a, t, mass, kap, cur, prev, g, dt, zc);
     else
-        k_adj_start<T, 4><<<plane_grid(g, zc), kThreads, 0, st>>>(a, t, mass, kap64, cur, prev, g, dt, zc);
+        k_adj_start<T, 4><<<plane_grid(g, zc), kThreads, 0, st>>>(a, t, mass, kap, cur, prev, g, dt, zc);
 }
 
 template <typename T>
-void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass,
-                      const double* kap64, const double* z0, const double* z1, const double* d0, const double* d1,
+void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass, const T* kap,
+                      const double* minv, const double* z0, const double* z1, const double* d0, const double* d1,
                       double* o0, double* o1, double* gt1, Red red, double dt, int zc, cudaStream_t st) {
     note_launch(1);
     const dim3 grid = plane_grid(g, zc);
-#define CMCG_FIN(O, MODE)                                                                                  \
-    k_adj_final<T, O, MODE><<<grid, kThreads, 0, st>>>(s, u1, mass, kap64, z0, z1, d0, d1, o0, o1, gt1, red, \
-                                                       g, dt, zc)
+#define CMCG_FIN(O, MODE)                                                                                        \
+    k_adj_final<T, O, MODE><<<grid, kThreads, 0, st>>>(s, u1, mass, kap, minv, z0, z1, d0, d1, o0, o1, gt1, red, g, \
+                                                       dt, zc)
     if (order == 2) {
         if (mode == 0) CMCG_FIN(2, 0); else CMCG_FIN(2, 1);
     } else {
@@ -459,19 +479,20 @@ long long plane_blocks(const Geom& g, int zc) {
     return (long long)d.x * d.y;
 }
 
-#define CMCG_INST(T)                                                                                          \
-    template void launch_step<T>(const Geom&, int, const T*, T*, const T*, const double*, double, double, int,  \
-                                 int, cudaStream_t);                                                          \
-    template void launch_start<T>(const Geom&, int, const double*, const double*, T*, T*, const double*,       \
-                                  const double*, double, int, cudaStream_t);                                  \
-    template void launch_end<T>(const Geom&, int, int, const T*, const T*, const double*, const double*,       \
-                                const double*, const double*, const double*, double, double, double*, double*, \
-                                Red, double, int, cudaStream_t);                                              \
-    template void launch_adj_start<T>(const Geom&, int, const double*, const double*, const double*,          \
-                                      const double*, T*, T*, double, int, cudaStream_t);                      \
-    template void launch_adj_final<T>(const Geom&, int, int, const T*, const T*, const double*, const double*, \
-                                      const double*, const double*, const double*, const double*, double*,    \
-                                      double*, double*, Red, double, int, cudaStream_t);
+#define CMCG_INST(T)                                                                                           \
+    template void launch_step<T>(const Geom&, int, const T*, T*, const T*, const double*, double, double, int,   \
+                                 int, cudaStream_t);                                                           \
+    template void launch_start<T>(const Geom&, int, const T*, const double*, T*, T*, const T*, const double*,   \
+                                  double, int, cudaStream_t);                                                  \
+    template void launch_end<T>(const Geom&, int, int, const T*, const T*, const T*, const double*, const T*,   \
+                                const double*, const double*, double, double, double*, double*, Red, double,    \
+                                int, cudaStream_t);                                                            \
+    template void launch_adj_prep<T>(const Geom&, const double*, const double*, const T*, T*, int, cudaStream_t); \
+    template void launch_adj_start<T>(const Geom&, int, const double*, const T*, const double*, const T*, T*,   \
+                                      T*, double, int, cudaStream_t);                                          \
+    template void launch_adj_final<T>(const Geom&, int, int, const T*, const T*, const double*, const T*,       \
+                                      const double*, const double*, const double*, const double*, const double*, \
+                                      double*, double*, double*, Red, double, int, cudaStream_t);
 CMCG_INST(float)
 CMCG_INST(double)
 #undef CMCG_INST

@@ -38,8 +38,33 @@ def mixed_2d():
                        dt_target=0.35 * h / 1.8, f=f, g=g)
 
 
+def odd_3d():
+    n = (13, 11, 15)
+    h = 1.0 / 15
+    rng = np.random.Generator(np.random.PCG64(12))
+    shape = (16, 12, 14)
+    c = 1.0 + 0.5 * rng.random(shape)
+    f = wl.gaussian_source(n, h, (0.4, 0.3, 0.5), 0.1).astype(np.complex128)
+    return wl.Workload(name="odd3d", n=n, h=h, c=c, omega=7.0, faces=(ABC, ABC, NEU, ABC, ABC, ABC),
+                       dt_target=0.3 * h / 1.5, f=f)
+
+
+def odd_2d():
+    n = (37, 29)
+    h = 1.0 / 37
+    shape = (30, 38)
+    rng = np.random.Generator(np.random.PCG64(13))
+    c = 1.0 + rng.random(shape)
+    g = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex128)
+    mask = wl.sphere_mask(n, h, (0.5, 0.4), 0.12)
+    return wl.Workload(name="odd2d", n=n, h=h, c=c, omega=11.0, faces=(ABC,) * 4 + (NEU, NEU),
+                       dt_target=0.4 * h / 2.0, mask=mask, g=g)
+
+
 CASES = {
     "gauss2d_40": lambda: wl.gaussian_2d(n=40),
+    "odd2d_37x29": odd_2d,
+    "odd3d_13x11x15": odd_3d,
     "sphere3d_24": lambda: wl.sphere_3d(n=24),
     "layered3d_o4_16": lambda: wl.layered_3d(n=16),
     "mixed2d": mixed_2d,
@@ -147,6 +172,20 @@ def test_solve_matches_direct(case, precision, tol, bound):
     if not dz.has_dirichlet:
         # Im lambda vanishes up to the solve's accuracy relative to the field's size
         assert abs(st["lambda_im"]) <= bound * max(abs(st["lambda_re"]), float(np.abs(U).max()))
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(cmcg.FP64, 1e-12, 5e-9), (cmcg.FP32, 1e-6, 1e-4),
+                                                 (cmcg.MIXED, 1e-9, 1e-6)])
+def test_inexact_riesz_solve_matches_direct(case, precision, tol, bound):
+    # one V-cycle as the Riesz map inside flexible CG: same fixed point as the exact map; the
+    # recursively updated residual limits the attainable FP64 accuracy to a few 1e-9
+    name, w, dz = case
+    s = solver_of(w, precision, flags=cmcg.FLAG_INEXACT_RIESZ)
+    U = direct.solve(dz, dz.load(w.f, w.g))
+    u, st = s.solve(w.f, w.g, tol=tol)
+    assert st["status"] == cmcg.OK, st
+    assert wrel(dz, u.cpu().numpy(), U) <= bound, (name, st)
+    assert st["riesz_iterations"] >= st["iterations"]
 
 
 def test_fp64_iterations_and_shift_match_oracle(case):
