@@ -80,6 +80,21 @@ def workload_config(w, args):
     }
 
 
+def aggregate_over_ranks(elapsed, updates, device=None):
+    """Whole-job figures across ranks: the slowest rank's time and the sum of all updates
+    (replicas only: the ranks share nothing but this reduction)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return elapsed, updates
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -162,13 +177,17 @@ def kernel_traffic(kernel_src_hash):
         d = json.load(open(p))
     except ValueError:
         return None
-    if d.get("wave_cu_sha256") != kernel_src_hash:
+    if d.get("step_kernel_sha256") != kernel_src_hash:
         return None
     return d.get("dram_bytes_per_launch_full_size")
 
 
-def wave_src_hash():
-    return hashlib.sha256(open(os.path.join(ROOT, "paper_1903_12522_gb300", "csrc", "wave.cu"), "rb").read()).hexdigest()
+def step_kernel_src_hash():
+    """Hash of the 3D 7-point step kernel's source text (the kernel the ncu counters describe)."""
+    src = open(os.path.join(ROOT, "paper_1903_12522_gb300", "csrc", "wave.cu")).read()
+    start = src.index("k_step3d7(")
+    end = src.index("// ----", start)
+    return hashlib.sha256(src[start:end].encode()).hexdigest()
 
 
 # ---------------------------------------------------------------------------------------
@@ -299,12 +318,7 @@ def run_ours(args):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     updates = sum(st.point_updates for st in stats)
     if ws > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        tot = torch.tensor([float(updates)], device=dev, dtype=torch.float64)
-        dist.all_reduce(tot)
-        updates = tot.item()
+        elapsed, updates = aggregate_over_ranks(elapsed, updates, device=dev)
     if u_ref is not None:
         a = u.reshape(w.shape)
         num = torch.linalg.vector_norm(a - u_ref).item()
@@ -322,7 +336,7 @@ def run_ours(args):
         per_launch, bpu, name = s64 / max(n64, 1), STEP_BYTES_FP64, "leapfrog step 3D 7-point FP64"
     peak, peak_src = hbm_peak()
     achieved = bpu * w.num_nodes / per_launch / 1e9
-    traffic = kernel_traffic(wave_src_hash()) if n32 > 0 else None
+    traffic = kernel_traffic(step_kernel_src_hash()) if n32 > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": name, "bytes_per_update": bpu,
                 "avg_launch_us": per_launch * 1e6, "peak_source": f"{peak_src} (copy bandwidth)",

@@ -52,6 +52,7 @@ extern "C" {
 #define CMCG_ERR_UNSUPPORTED (-4)
 #define CMCG_ERR_CUDA (-5)
 #define CMCG_ERR_DIVERGED (-6)
+#define CMCG_ERR_DEVICE_TIMEOUT (-7) /* a bounded device-side wait ran out (batched kernel barrier) */
 
 /* ---- boundary codes (face order -x, +x, -y, +y, -z, +z) --------------------------- */
 #define CMCG_BC_ABC 0       /* first-order absorbing (impedance) face, Eq. HE_ABC      */
@@ -98,6 +99,19 @@ typedef struct {
     double inner_tol;       /* CMCG_MIXED: relative tolerance of each inner FP32 solve
                                (0 = 1e-3)                                                 */
     int flags;              /* CMCG_FLAG_* bits; other bits must be 0                      */
+    int runup_periods;      /* initial run-up of Sec. 4.3: integrate the wave equation from rest
+                               for this many periods with the sources ramped in by
+                               theta(t) = (2 - sin(pi t / (2 t_tr))) sin(pi t / (2 t_tr)),
+                               t_tr = runup_periods T, and start CG from the final state.
+                               0 = none; -1 = ceil(diam(Omega) / (T c_min)).  With a run-up, the
+                               relative tolerance of cmcg_solve refers to the residual of the
+                               zero initial guess (one extra gradient evaluation), so the accuracy
+                               at a given tol does not depend on the run-up.                  */
+    int tile[4];            /* launch shape of the leapfrog kernels, 0 = default: [0] z-planes
+                               per thread of the one-step 3D kernel (16), [1] z-planes per block
+                               of the two-step kernel (24), [2] maximum interior tile height of
+                               the two-step kernel (16, at most 16), [3] reserved (0).  Chosen
+                               per grid class by the autotuner (paper_1903_12522_gb300/autotune.py). */
 } cmcg_options;
 
 typedef struct {
@@ -117,6 +131,7 @@ typedef struct {
     long long point_updates; /* grid-point leapfrog updates performed                      */
     double seconds;          /* wall time of the call                                     */
     long long kernel_launches; /* CUDA kernels this library launched during the call       */
+    int runup_periods;       /* periods integrated by the run-up (0 if none)              */
     /* CMCG_FLAG_TIMING: summed device time and launch count of the leapfrog step kernels
        (forward and adjoint), split by stepping precision; 0 otherwise */
     double step_seconds_fp32, step_seconds_fp64;
@@ -187,6 +202,51 @@ int cmcg_solve_host(cmcg_handle* h, const double* f_host, const double* g_host, 
                     double* u_host, cmcg_stats* stats);
 
 const char* cmcg_status_string(int status);
+
+/* ---- multi-solve engine (batched solves and serving) -------------------------------- */
+/* Many solves advance together, one CG iteration per cmcg_engine_tick.  Each admitted solve
+ * keeps its own handle (its workspace holds the resident CG state).  Per tick, the FP32
+ * leapfrog step loops of all solves in their inner iterations run in one batched persistent
+ * kernel per period (forward, then adjoint; uneven grids and step counts step together and
+ * idle when done); the rest of each iteration is per-solve kernels.  The tick is captured as
+ * a CUDA graph and replayed while the set of active solves and their phases stay the same.
+ * Solves finish independently; a finished solve's result is read with cmcg_engine_result,
+ * which frees its slot.  Requirements: every handle uses the engine's stream, precision
+ * CMCG_FP32 or CMCG_MIXED and CMCG_FLAG_INEXACT_RIESZ (else CMCG_ERR_UNSUPPORTED).  The
+ * batched kernel is a cooperative launch whose grid barrier waits are bounded; a wait that
+ * runs out returns CMCG_ERR_DEVICE_TIMEOUT from cmcg_engine_tick. */
+typedef struct cmcg_engine cmcg_engine;
+#define CMCG_ENGINE_NO_GRAPH 1 /* run ticks as plain launches instead of CUDA graphs */
+
+/* Device workspace bytes for an engine of max_slots slots (0 if max_slots is not 1..4096). */
+size_t cmcg_engine_workspace_size(int max_slots);
+/* workspace: device, 256-byte aligned, caller-owned; stream: cudaStream_t shared with the
+ * handles (CUDA graphs need a created stream: on the legacy default stream, NULL, ticks run as
+ * plain launches); flags: CMCG_ENGINE_* bits. */
+int cmcg_engine_create(int max_slots, void* workspace, size_t ws_bytes, void* stream, int flags,
+                       cmcg_engine** out);
+int cmcg_engine_destroy(cmcg_engine* e);
+/* Admit a solve: f, g sources as in cmcg_solve (device, nullable, read now); tol as in
+ * cmcg_solve; u: device complex double[N_p] written when the solve finishes.  Returns the slot
+ * (>= 0), or CMCG_ERR_WORKSPACE when no slot is free, CMCG_ERR_INVALID_ARG when h is already
+ * in a slot. */
+int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const double* g, double tol, double* u);
+/* One iteration of every active solve.  finished[0..max_finished) receives the slots that
+ * finished in this tick, *n_finished their number. */
+int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_finished);
+/* Status and statistics of a finished slot (CMCG_OK, CMCG_NOT_CONVERGED or an error); frees
+ * the slot.  CMCG_ERR_INVALID_ARG if the slot has not finished. */
+int cmcg_engine_result(cmcg_engine* e, int slot, cmcg_stats* stats);
+/* Number of solves in progress. */
+int cmcg_engine_active(const cmcg_engine* e);
+/* Ticks run and CUDA graphs built so far. */
+int cmcg_engine_info(const cmcg_engine* e, long long* ticks, long long* graph_builds);
+/* Name of the CUDA error behind the engine's last CMCG_ERR_CUDA ("cudaSuccess" if none). */
+const char* cmcg_engine_cuda_error(const cmcg_engine* e);
+/* Failure-path self-test: launches a one-block grid barrier that expects one block more than
+ * exists, so its bounded wait must run out after spin_limit polls (1..2^24).  Returns
+ * CMCG_ERR_DEVICE_TIMEOUT when the time-out path works, CMCG_OK if it (wrongly) did not fire. */
+int cmcg_engine_barrier_selftest(cmcg_engine* e, long long spin_limit);
 
 /* Allocation-free FP64 wave period (the paper has no counterpart; this entry point exists for
  * callers that cannot allocate device memory, such as a plug-in inside a host application

@@ -26,9 +26,15 @@ FLAG_HOST_IO = 1
 FLAG_TIMING = 2
 FLAG_INEXACT_RIESZ = 4
 
+ERR_DEVICE_TIMEOUT = -7
+ENGINE_NO_GRAPH = 1
+
 EXPORTED = (
     "cmcg_workspace_size", "cmcg_create", "cmcg_destroy", "cmcg_get_info", "cmcg_wave_period",
     "cmcg_adjoint_period", "cmcg_riesz", "cmcg_solve", "cmcg_solve_host", "cmcg_status_string",
+    "cmcg_engine_workspace_size", "cmcg_engine_create", "cmcg_engine_destroy", "cmcg_engine_submit",
+    "cmcg_engine_tick", "cmcg_engine_result", "cmcg_engine_active", "cmcg_engine_info",
+    "cmcg_engine_barrier_selftest", "cmcg_engine_cuda_error",
 )
 
 
@@ -42,7 +48,8 @@ class BC(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("dt", C.c_double), ("max_iter", C.c_int), ("riesz_tol", C.c_double),
-                ("riesz_max_iter", C.c_int), ("inner_tol", C.c_double), ("flags", C.c_int)]
+                ("riesz_max_iter", C.c_int), ("inner_tol", C.c_double), ("flags", C.c_int),
+                ("runup_periods", C.c_int), ("tile", C.c_int * 4)]
 
 
 class Stats(C.Structure):
@@ -51,7 +58,7 @@ class Stats(C.Structure):
                 ("omega_tilde", C.c_double), ("omega_hat", C.c_double), ("rel_residual", C.c_double),
                 ("J0", C.c_double), ("J_final", C.c_double), ("lambda_re", C.c_double),
                 ("lambda_im", C.c_double), ("point_updates", C.c_longlong), ("seconds", C.c_double),
-                ("kernel_launches", C.c_longlong), ("step_seconds_fp32", C.c_double),
+                ("kernel_launches", C.c_longlong), ("runup_periods", C.c_int), ("step_seconds_fp32", C.c_double),
                 ("step_seconds_fp64", C.c_double), ("step_launches_fp32", C.c_longlong),
                 ("step_launches_fp64", C.c_longlong)]
 
@@ -97,6 +104,26 @@ def load(path: str = LIB_PATH):
     lib.cmcg_solve_host.restype = I
     lib.cmcg_status_string.argtypes = [I]
     lib.cmcg_status_string.restype = C.c_char_p
+    lib.cmcg_engine_workspace_size.argtypes = [I]
+    lib.cmcg_engine_workspace_size.restype = S
+    lib.cmcg_engine_create.argtypes = [I, P, S, P, I, C.POINTER(P)]
+    lib.cmcg_engine_create.restype = I
+    lib.cmcg_engine_destroy.argtypes = [P]
+    lib.cmcg_engine_destroy.restype = I
+    lib.cmcg_engine_submit.argtypes = [P, P, P, P, D, P]
+    lib.cmcg_engine_submit.restype = I
+    lib.cmcg_engine_tick.argtypes = [P, C.POINTER(I), I, C.POINTER(I)]
+    lib.cmcg_engine_tick.restype = I
+    lib.cmcg_engine_result.argtypes = [P, I, C.POINTER(Stats)]
+    lib.cmcg_engine_result.restype = I
+    lib.cmcg_engine_active.argtypes = [P]
+    lib.cmcg_engine_active.restype = I
+    lib.cmcg_engine_info.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    lib.cmcg_engine_info.restype = I
+    lib.cmcg_engine_barrier_selftest.argtypes = [P, C.c_longlong]
+    lib.cmcg_engine_barrier_selftest.restype = I
+    lib.cmcg_engine_cuda_error.argtypes = [P]
+    lib.cmcg_engine_cuda_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -128,10 +155,14 @@ def make_grid(n, h, order=2) -> Grid:
     return g
 
 
-def make_options(precision=FP64, dt=0.0, max_iter=0, riesz_tol=0.0, riesz_max_iter=0, inner_tol=0.0, flags=0):
+def make_options(precision=FP64, dt=0.0, max_iter=0, riesz_tol=0.0, riesz_max_iter=0, inner_tol=0.0, flags=0,
+                 runup_periods=0, tile=None):
     o = Options()
     o.precision, o.dt, o.max_iter = int(precision), float(dt), int(max_iter)
     o.riesz_tol, o.riesz_max_iter, o.inner_tol, o.flags = float(riesz_tol), int(riesz_max_iter), float(inner_tol), int(flags)
+    o.runup_periods = int(runup_periods)
+    for k, v in enumerate(tile or ()):
+        o.tile[k] = int(v)
     return o
 
 
@@ -208,7 +239,8 @@ class Solver:
     """A handle plus its caller-owned workspace (torch uint8 tensor on the device)."""
 
     def __init__(self, n, h, c, omega, faces, mask=None, order=2, precision=FP64, dt=0.0, max_iter=0,
-                 riesz_tol=0.0, riesz_max_iter=0, inner_tol=0.0, flags=0, device="cuda", stream=None):
+                 riesz_tol=0.0, riesz_max_iter=0, inner_tol=0.0, flags=0, device="cuda", stream=None,
+                 runup_periods=0, tile=None):
         import torch
 
         load()
@@ -217,7 +249,12 @@ class Solver:
         self.n = tuple(int(m) for m in n)
         self.shape = tuple(m + 1 for m in reversed(self.n))
         self.grid = make_grid(self.n, h, order)
-        self.opts = make_options(precision, dt, max_iter, riesz_tol, riesz_max_iter, inner_tol, flags)
+        if tile is None:
+            from . import autotune
+
+            tile = autotune.lookup(len(self.n), max(self.n), precision)
+        self.opts = make_options(precision, dt, max_iter, riesz_tol, riesz_max_iter, inner_tol, flags, runup_periods,
+                                 tile)
         nbytes = cmcg_workspace_size(self.grid, self.opts)
         if nbytes == 0:
             raise CMCGError(ERR_INVALID_ARG, "cmcg_workspace_size")
@@ -229,8 +266,21 @@ class Solver:
         self.mask = None if mask is None else self._dev(mask, torch.uint8)
         self.bc.dirichlet_mask = _ptr(self.mask)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._after_caller()
         self.handle = cmcg_create(self.grid, self.c, omega, self.bc, self.opts, self.workspace, self.stream.cuda_stream)
         self.info = cmcg_get_info(self.handle)
+
+    def _after_caller(self):
+        # inputs produced on the caller's stream must be complete before this solver's stream
+        # reads them (torch's side streams do not synchronise with the default stream)
+        cur = self.torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+
+    def _before_caller(self):
+        cur = self.torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
 
     def _dev(self, a, dtype):
         torch = self.torch
@@ -256,21 +306,27 @@ class Solver:
         u0, v0 = self._dev(u0, torch.float64), self._dev(v0, torch.float64)
         f, g = self._dev(f, torch.complex128), self._dev(g, torch.complex128)
         uT, vT = torch.empty_like(u0), torch.empty_like(v0)
+        self._after_caller()
         cmcg_wave_period(self.handle, u0, v0, f, g, uT, vT)
+        self._before_caller()
         return uT.reshape(self.shape), vT.reshape(self.shape)
 
     def adjoint_period(self, a, b):
         torch = self.torch
         a, b = self._dev(a, torch.float64), self._dev(b, torch.float64)
         q0, q1 = torch.empty_like(a), torch.empty_like(b)
+        self._after_caller()
         cmcg_adjoint_period(self.handle, a, b, q0, q1)
+        self._before_caller()
         return q0.reshape(self.shape), q1.reshape(self.shape)
 
     def riesz(self, rhs):
         torch = self.torch
         rhs = self._dev(rhs, torch.float64)
         s = torch.empty_like(rhs)
+        self._after_caller()
         code = cmcg_riesz(self.handle, rhs, s)
+        self._before_caller()
         return s.reshape(self.shape), code
 
     def solve(self, f=None, g=None, tol=1e-6):
@@ -278,7 +334,98 @@ class Solver:
         f, g = self._dev(f, torch.complex128), self._dev(g, torch.complex128)
         u = torch.empty(int(np.prod(self.shape)), dtype=torch.complex128, device=self.device)
         st = Stats()
+        self._after_caller()
         code = cmcg_solve(self.handle, f, g, tol, u, st)
+        self._before_caller()
         out = st.as_dict()
         out["status"] = code
         return u.reshape(self.shape), out
+
+
+# ---- multi-solve engine ----------------------------------------------------------------------
+class Engine:
+    """Batched / served solves: a cmcg_engine plus its device workspace.  Solvers submitted to it
+    must share its stream and use precision FP32 or MIXED with FLAG_INEXACT_RIESZ.  Without a
+    stream argument the engine creates its own (CUDA graphs need a created stream); pass
+    engine.stream to the solvers."""
+
+    def __init__(self, max_slots, stream=None, flags=0, device="cuda"):
+        import torch
+
+        lib = load()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        nbytes = int(lib.cmcg_engine_workspace_size(int(max_slots)))
+        if nbytes == 0:
+            raise CMCGError(ERR_INVALID_ARG, "cmcg_engine_workspace_size")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.handle = C.c_void_p()
+        _check(lib.cmcg_engine_create(int(max_slots), self.workspace.data_ptr(), nbytes, self.stream.cuda_stream,
+                                      int(flags), C.byref(self.handle)), "cmcg_engine_create")
+        self.max_slots = int(max_slots)
+        self._pending = {}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().cmcg_engine_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, solver, f=None, g=None, tol=1e-6):
+        """Admit a solve; returns its slot.  The result tensor is returned by result()."""
+        torch = self.torch
+        f, g = solver._dev(f, torch.complex128), solver._dev(g, torch.complex128)
+        u = torch.empty(int(np.prod(solver.shape)), dtype=torch.complex128, device=self.device)
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+        slot = load().cmcg_engine_submit(self.handle, solver.handle, _ptr(f), _ptr(g), float(tol), _ptr(u))
+        if slot < 0:
+            raise CMCGError(slot, "cmcg_engine_submit")
+        self._pending[slot] = (solver, u, f, g)
+        return slot
+
+    def tick(self):
+        """One CG iteration of every active solve; returns the slots that finished."""
+        buf = (C.c_int * self.max_slots)()
+        n = C.c_int(0)
+        code = load().cmcg_engine_tick(self.handle, buf, self.max_slots, C.byref(n))
+        if code != OK:
+            raise CMCGError(code, "cmcg_engine_tick [" + load().cmcg_engine_cuda_error(self.handle).decode() + "]")
+        return [buf[i] for i in range(n.value)]
+
+    def result(self, slot):
+        st = Stats()
+        code = load().cmcg_engine_result(self.handle, int(slot), C.byref(st))
+        solver, u, _, _ = self._pending.pop(slot)
+        cur = self.torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+        out = st.as_dict()
+        out["status"] = code
+        return u.reshape(solver.shape), out
+
+    def active(self):
+        return int(load().cmcg_engine_active(self.handle))
+
+    def info(self):
+        t, gb = C.c_longlong(0), C.c_longlong(0)
+        load().cmcg_engine_info(self.handle, C.byref(t), C.byref(gb))
+        return {"ticks": t.value, "graph_builds": gb.value}
+
+    def barrier_selftest(self, spin_limit=100000):
+        return int(load().cmcg_engine_barrier_selftest(self.handle, int(spin_limit)))
+
+    def run_all(self):
+        """Tick until every admitted solve has finished; returns {slot: (u, stats)}."""
+        out = {}
+        while self.active() > 0:
+            for s in self.tick():
+                out[s] = self.result(s)
+        return out

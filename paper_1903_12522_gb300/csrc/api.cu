@@ -13,6 +13,7 @@
 #include "cmcg.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "solver.h"
 
 using namespace cmcg;
 
@@ -24,10 +25,6 @@ long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
-constexpr int kMaxLevels = 16;
-constexpr int kZcStep3D = 16;  // z-planes per thread in the leapfrog step (3D)
-constexpr int kZcEnds = 8;     // z-planes per thread in the period endpoint kernels
-constexpr double kPi = 3.14159265358979323846;
 
 struct Carver {
     char* base;
@@ -43,54 +40,9 @@ struct Carver {
 
 }  // namespace
 
-struct cmcg_handle {
-    Geom g{};
-    int order = 2;
-    cmcg_options opt{};
-    cudaStream_t st = nullptr;
-    double omega = 0, T = 0, dt = 0, wt = 0, wh = 0, volume = 0;
-    int N = 0;
-    bool has_dir = false;
-    double sumM = 0, sumB = 0, sumW = 0;
-    // coefficients
-    double *kap64 = nullptr, *mass = nullptr, *minv = nullptr, *S = nullptr;
-    float* kap32 = nullptr;
-    unsigned char* mask = nullptr;
-    // wave buffers (sized for double; FP32 stepping uses the first half) + FP64 temp
-    void *ya = nullptr, *yb = nullptr;
-    double* tmp = nullptr;
-    // CG state
-    double *w0, *w1, *r0, *r1, *rh0, *rh1, *d0, *d1, *gh0, *gh1, *gt0, *gt1, *z0, *z1;
-    double *wo0 = nullptr, *wo1 = nullptr;  // CMCG_MIXED outer iterate
-    // Riesz PCG
-    double *pr, *pp, *pAp, *pzd;
-    MGLevel lv[kMaxLevels];
-    int nlev = 0;
-    int blk_level = -1;       // first level run inside one thread block (-1: none)
-    BlockLevels blk{};
-    int riesz_guess = 0;      // PCG iterations of the previous Riesz solve
-    // host staging
-    double* stage = nullptr;
-    // reductions
-    double* partials = nullptr;
-    unsigned* tickets = nullptr;
-    double* sc = nullptr;
-    double* hsc = nullptr;  // pinned host mirror of sc
-    // counters of the current call
-    long long riesz_iters = 0;
-    long long periods = 0;
-    // CMCG_FLAG_TIMING: event pairs around the step loops of the periods since the last sync
-    bool timing = false;
-    cudaEvent_t ev[8] = {};
-    int ev_used = 0;
-    bool ev_fp32[4] = {};
-    int ev_steps[4] = {};
-    double step_s[2] = {0, 0};     // [fp64, fp32]
-    long long step_n[2] = {0, 0};
-    Red red() const { return Red{partials, tickets, sc}; }
-};
 
-namespace {
+namespace cmcg {
+namespace detail {
 
 bool valid_grid(const cmcg_grid* gr) {
     if (!gr) return false;
@@ -236,66 +188,230 @@ void timing_end(cmcg_handle* H, int p) {
 }
 
 // ---- period drivers ------------------------------------------------------------------------
-// Forward period from (w0, w1).  mode 0: z = E (Pi(w) - w) into (out0, out1) and J into
-// sc[SC_J]; mode 1: (y(T), y_t(T)) into (out0, out1).
+// A period is begin (start kernel), N-1 leapfrog steps, end (end kernel).  The pieces are
+// separate so that the multi-solve engine can run the step loops of many solves in one
+// batched kernel.
+template <typename T>
+PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool src) {
+    const Geom& g = H->g;
+    const int zce = g.dim == 3 ? kZcEnds : 1;
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    PeriodBuffers b;
+    b.cur = H->yb;
+    b.prev = H->ya;
+    // T-precision copy of w0 for the endpoint stencils (FP32: in the temp buffer, which the
+    // forward period does not otherwise use)
+    b.w0t = w0;
+    if (std::is_same<T, float>::value) {
+        float* w0f = (float*)H->tmp;
+        launch_to_float(g.np, w0, w0f, H->st);
+        b.w0t = w0f;
+    }
+    launch_start<T>(g, H->order, (const T*)b.w0t, w1, (T*)b.prev, (T*)b.cur, kap, src ? H->S : nullptr, H->dt,
+                    zce, H->st);
+    return b;
+}
+
+// z-planes per thread of the one-step kernels
+int step_zc(const cmcg_handle* H) {
+    if (H->g.dim != 3) return 1;
+    return H->opt.tile[0] > 0 ? H->opt.tile[0] : kZcStep3D;
+}
+
+// FP32 3D 7-point homogeneous steps run in pairs through the two-step kernel, whose outputs go
+// to the spare halves of the (double-sized) wave buffers.
+template <typename T>
+bool use_pairs(const cmcg_handle* H, bool src) {
+    return std::is_same<T, float>::value && !src && step2_supported(H->g, H->order);
+}
+
+// `count` homogeneous steps from b (in pairs where possible, else one by one).
+template <typename T>
+void plain_steps(cmcg_handle* H, PeriodBuffers& b, int count) {
+    const Geom& g = H->g;
+    const int zc = step_zc(H);
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    if (use_pairs<T>(H, false) && count >= 2) {
+        float* spare[2] = {(float*)H->ya + g.np, (float*)H->yb + g.np};
+        // the spare halves are whichever two of the four float fields cur/prev are not
+        float* fields[4] = {(float*)H->ya, (float*)H->yb, spare[0], spare[1]};
+        int k = 0;
+        for (float* f : fields)
+            if (f != (float*)b.cur && f != (float*)b.prev && k < 2) spare[k++] = f;
+        const int tp = timing_begin(H, true, count / 2);
+        while (count >= 2) {
+            launch_step2(g, (const float*)b.prev, (const float*)b.cur, (const float*)kap, spare[0], spare[1],
+                         H->opt.tile[1] > 0 ? H->opt.tile[1] : kZcStep2, H->opt.tile[2] > 0 ? H->opt.tile[2] : 16,
+                         H->st);
+            float* old_prev = (float*)b.prev;
+            float* old_cur = (float*)b.cur;
+            b.prev = spare[0];
+            b.cur = spare[1];
+            spare[0] = old_prev;
+            spare[1] = old_cur;
+            count -= 2;
+        }
+        timing_end(H, tp);
+    }
+    if (count <= 0) return;
+    const int tp = use_pairs<T>(H, false) ? -1 : timing_begin(H, std::is_same<T, float>::value, count);
+    for (int n = 0; n < count; ++n) {
+        launch_step<T>(g, H->order, (const T*)b.cur, (T*)b.prev, kap, nullptr, 0.0, 0.0, 0, zc, H->st);
+        std::swap(b.cur, b.prev);
+    }
+    timing_end(H, tp);
+}
+
+template <typename T>
+void fwd_steps(cmcg_handle* H, PeriodBuffers& b, bool src) {
+    const Geom& g = H->g;
+    const int zc = step_zc(H);
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    if (!src) {
+        plain_steps<T>(H, b, H->N - 1);
+        return;
+    }
+    const double* S = H->S;
+    const int tp = timing_begin(H, std::is_same<T, float>::value, H->N - 1);
+    for (int n = 1; n < H->N; ++n) {
+        const double th = H->omega * n * H->dt;
+        launch_step<T>(g, H->order, (const T*)b.cur, (T*)b.prev, kap, S, cos(th), sin(th), kStepSrc, zc, H->st);
+        std::swap(b.cur, b.prev);
+    }
+    timing_end(H, tp);
+}
+
+// mode 0: z = E (Pi(w) - w) into (out0, out1) and J into sc[SC_J]; mode 1: (y(T), y_t(T)).
+template <typename T>
+void fwd_end(cmcg_handle* H, const PeriodBuffers& b, const double* w1, bool src, int mode, double* out0,
+             double* out1) {
+    const Geom& g = H->g;
+    const int zce = g.dim == 3 ? kZcEnds : 1;
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    const double thN = H->omega * H->N * H->dt;
+    launch_end<T>(g, H->order, mode, (const T*)b.cur, (const T*)b.prev, (const T*)b.w0t, w1, kap, H->mass,
+                  src ? H->S : nullptr, cos(thN), sin(thN), out0, out1, H->red(), H->dt, zce, H->st);
+    H->periods += 1;
+}
+
 template <typename T>
 void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src, int mode, double* out0,
                     double* out1) {
+    PeriodBuffers b = fwd_begin<T>(H, w0, w1, src);
+    fwd_steps<T>(H, b, src);
+    fwd_end<T>(H, b, w1, src, mode, out0, out1);
+}
+
+// Adjoint (transposed) period of the cotangents (a, b).
+template <typename T>
+PeriodBuffers adj_begin(cmcg_handle* H, const double* a, const double* bb) {
+    const Geom& g = H->g;
+    const int zce = g.dim == 3 ? kZcEnds : 1;
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    PeriodBuffers b;
+    b.cur = H->ya;
+    b.prev = H->yb;
+    b.w0t = nullptr;
+    T* t = (T*)H->tmp;
+    launch_adj_prep<T>(g, bb, H->mass, kap, t, zce, H->st);
+    launch_adj_start<T>(g, H->order, a, t, H->mass, kap, (T*)b.cur, (T*)b.prev, H->dt, zce, H->st);
+    return b;
+}
+
+// Step flags of the k-th of the N-1 adjoint steps.
+int adj_step_flags(int k, int N) {
+    int flags = 0;
+    if (k == 0) flags |= kStepPrevScaled;
+    if (k == N - 2) flags |= kStepNoDiv;
+    return flags;
+}
+
+template <typename T>
+void adj_steps(cmcg_handle* H, PeriodBuffers& b) {
+    const Geom& g = H->g;
+    const int zc = step_zc(H);
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    const int n = H->N - 1;  // steps k = 0 .. N-2; the first and the last have their own variants
+    auto single = [&](int k) {
+        launch_step<T>(g, H->order, (const T*)b.cur, (T*)b.prev, kap, nullptr, 0.0, 0.0, adj_step_flags(k, H->N), zc,
+                       H->st);
+        std::swap(b.cur, b.prev);
+    };
+    if (use_pairs<T>(H, false)) {
+        single(0);
+        if (n >= 3) plain_steps<T>(H, b, n - 2);
+        if (n >= 2) single(n - 1);
+        return;
+    }
+    const int tp = timing_begin(H, std::is_same<T, float>::value, n);
+    for (int k = 0; k < n; ++k) single(k);
+    timing_end(H, tp);
+}
+
+// mode 1: q = P^T (a, b) into (o0, o1).  mode 0: ghat = P^T z - z into (o0, o1),
+// g~1 = ghat1 / M into gt1, and the reductions ghat . d -> sc[SC_GD], sum ghat0 -> sc[SC_GSUM].
+template <typename T>
+void adj_end(cmcg_handle* H, const PeriodBuffers& b, const double* a, const double* bb, int mode, const double* d0,
+             const double* d1, double* o0, double* o1, double* gt1) {
+    const Geom& g = H->g;
+    const int zce = g.dim == 3 ? kZcEnds : 1;
+    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
+    launch_adj_final<T>(g, H->order, mode, (const T*)b.cur, (const T*)b.prev, H->mass, kap, H->minv, a, bb, d0, d1,
+                        o0, o1, gt1, H->red(), H->dt, zce, H->st);
+    H->periods += 1;
+}
+
+template <typename T>
+void adjoint_period(cmcg_handle* H, const double* a, const double* bb, int mode, const double* d0, const double* d1,
+                    double* o0, double* o1, double* gt1) {
+    PeriodBuffers b = adj_begin<T>(H, a, bb);
+    adj_steps<T>(H, b);
+    adj_end<T>(H, b, a, bb, mode, d0, d1, o0, o1, gt1);
+}
+
+// ---- initial run-up (Sec. 4.3) ---------------------------------------------------------------
+int runup_count(const cmcg_handle* H) {
+    if (H->opt.runup_periods > 0) return H->opt.runup_periods;
+    if (H->opt.runup_periods == 0) return 0;
+    double d2 = (double)H->g.nx * H->g.nx + (double)H->g.ny * H->g.ny + (double)H->g.nz * H->g.nz;
+    const double diam = H->g.h * sqrt(d2);
+    return std::max(1, (int)ceil(diam / (H->T * H->cmin)));
+}
+
+// theta_tr(t) = (2 - sin(pi t / (2 t_tr))) sin(pi t / (2 t_tr)) for t <= t_tr, 1 after.
+double ramp(double t, double ttr) {
+    if (t >= ttr) return 1.0;
+    const double s = sin(0.5 * kPi * t / ttr);
+    return (2.0 - s) * s;
+}
+
+// Integrate the wave equation from rest for `periods` periods with the ramped sources and
+// return (y, y_t) at t = periods T in (w0, w1).
+template <typename T>
+void runup(cmcg_handle* H, int periods, double* w0, double* w1) {
     const Geom& g = H->g;
     const int zc = g.dim == 3 ? kZcStep3D : 1;
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     T* cur = (T*)H->yb;
     T* prev = (T*)H->ya;
-    const double* S = src ? H->S : nullptr;
-    // T-precision copy of w0 for the endpoint stencils (FP32: second half of the ya buffer)
-    const T* w0t = (const T*)w0;
-    if (std::is_same<T, float>::value) {
-        float* w0f = (float*)H->ya + g.np;
-        launch_to_float(g.np, w0, w0f, H->st);
-        w0t = (const T*)w0f;
-    }
-    launch_start<T>(g, H->order, w0t, w1, prev, cur, kap, S, H->dt, zce, H->st);
-    const int tp = timing_begin(H, std::is_same<T, float>::value, H->N - 1);
-    for (int n = 1; n < H->N; ++n) {
-        const double th = H->omega * n * H->dt;
-        launch_step<T>(g, H->order, cur, prev, kap, S, cos(th), sin(th), src ? kStepSrc : 0, zc, H->st);
+    // y^0 = 0 and y^1 = 0: at rest, and the ramp vanishes at t = 0
+    cudaMemsetAsync(cur, 0, sizeof(T) * g.np, H->st);
+    cudaMemsetAsync(prev, 0, sizeof(T) * g.np, H->st);
+    const long long total = (long long)periods * H->N;
+    const double ttr = periods * H->T;
+    for (long long n = 1; n < total; ++n) {
+        const double t = n * H->dt;
+        const double th = ramp(t, ttr);
+        launch_step<T>(g, H->order, cur, prev, kap, H->S, th * cos(H->omega * t), th * sin(H->omega * t), kStepSrc,
+                       zc, H->st);
         std::swap(cur, prev);
     }
-    timing_end(H, tp);
-    const double thN = H->omega * H->N * H->dt;
-    launch_end<T>(g, H->order, mode, cur, prev, w0t, w1, kap, H->mass, S, cos(thN), sin(thN), out0, out1,
-                  H->red(), H->dt, zce, H->st);
-    H->periods += 1;
-}
-
-// Adjoint (transposed) period of the cotangents (a, b).  mode 1: q = P^T (a, b) into
-// (o0, o1).  mode 0: ghat = P^T z - z into (o0, o1), g~1 = ghat1 / M into gt1, and the
-// reductions ghat . d -> sc[SC_GD], sum ghat0 -> sc[SC_GSUM].
-template <typename T>
-void adjoint_period(cmcg_handle* H, const double* a, const double* b, int mode, const double* d0, const double* d1,
-                    double* o0, double* o1, double* gt1) {
-    const Geom& g = H->g;
-    const int zc = g.dim == 3 ? kZcStep3D : 1;
-    const int zce = g.dim == 3 ? kZcEnds : 1;
-    const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
-    T* cur = (T*)H->ya;
-    T* prev = (T*)H->yb;
-    T* t = (T*)H->tmp;
-    launch_adj_prep<T>(g, b, H->mass, kap, t, zce, H->st);
-    launch_adj_start<T>(g, H->order, a, t, H->mass, kap, cur, prev, H->dt, zce, H->st);
-    const int tp = timing_begin(H, std::is_same<T, float>::value, H->N - 1);
-    for (int k = 0; k < H->N - 1; ++k) {
-        int flags = 0;
-        if (k == 0) flags |= kStepPrevScaled;
-        if (k == H->N - 2) flags |= kStepNoDiv;
-        launch_step<T>(g, H->order, cur, prev, kap, nullptr, 0.0, 0.0, flags, zc, H->st);
-        std::swap(cur, prev);
-    }
-    timing_end(H, tp);
-    launch_adj_final<T>(g, H->order, mode, cur, prev, H->mass, kap, H->minv, a, b, d0, d1, o0, o1, gt1, H->red(),
-                        H->dt, zce, H->st);
-    H->periods += 1;
+    const double tN = total * H->dt;
+    launch_end<T>(g, H->order, 1, cur, prev, (const T*)nullptr, nullptr, kap, H->mass, H->S,
+                  ramp(tN, ttr) * cos(H->omega * tN), ramp(tN, ttr) * sin(H->omega * tN), w0, w1, H->red(), H->dt,
+                  zce, H->st);
+    H->periods += periods;
 }
 
 // ---- Riesz map: FP64 flexible PCG with a FP32 multigrid V-cycle --------------------------
@@ -397,7 +513,7 @@ int riesz_solve(cmcg_handle* H, const double* rhs, double* x, int* iters_out) {
 // z -> (z0, z1); J -> sc[SC_J].
 template <typename T>
 int gradient(cmcg_handle* H, const double* w0, const double* w1, bool src, const double* dd0, const double* dd1,
-             bool riesz = true) {
+             bool riesz) {
     forward_period<T>(H, w0, w1, src, 0, H->z0, H->z1);
     adjoint_period<T>(H, H->z0, H->z1, 0, dd0, dd1, H->gh0, H->gh1, H->gt1);
     if (!riesz) return CMCG_OK;
@@ -455,6 +571,43 @@ int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_o
     return rel <= tol ? CMCG_OK : CMCG_NOT_CONVERGED;
 }
 
+// gamma = ||g~||_E^2 of the gradient currently in (gh, gt) (exact Riesz) or z = B ghat.
+int gradient_norm(cmcg_handle* H, double* gamma) {
+    const long long n = H->g.np;
+    Red red = H->red();
+    if (inexact(H)) {
+        cudaMemcpyAsync(H->rh0, H->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+        cudaMemcpyAsync(H->rh1, H->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+        apply_B(H, true);
+        launch_scalar_residual(n, H->r0, H->r1, H->rh0, H->rh1, red, SC_R7, H->st);
+    } else {
+        launch_scalar_residual(n, H->gt0, H->gt1, H->gh0, H->gh1, red, SC_R7, H->st);
+    }
+    const int rc = sync_read(H);
+    if (rc != CMCG_OK) return rc;
+    *gamma = H->hsc[SC_R7];
+    return (*gamma == *gamma && *gamma >= 0) ? CMCG_OK : CMCG_ERR_DIVERGED;
+}
+
+// With a run-up: the zero-guess gradient norm (the tolerance reference), then the run-up
+// state into (w0, w1).  Without: (w0, w1) = 0 and gamma_zero = -1.
+template <typename T>
+int initial_guess(cmcg_handle* H, double* w0, double* w1, double* gamma_zero, cmcg_stats* stats) {
+    const long long n = H->g.np;
+    launch_fill(w0, n, 0.0, H->st);
+    launch_fill(w1, n, 0.0, H->st);
+    *gamma_zero = -1.0;
+    const int ell = runup_count(H);
+    stats->runup_periods = ell;
+    if (ell <= 0) return CMCG_OK;
+    int rc = gradient<T>(H, w0, w1, true, w0, w1, !inexact(H));
+    if (rc < 0) return rc;
+    rc = gradient_norm(H, gamma_zero);
+    if (rc != CMCG_OK) return rc;
+    runup<T>(H, ell, w0, w1);
+    return cuda_status();
+}
+
 // CG loop of Steps (4)-(5) on the current gradient (gh, gt) with homogeneous periods in
 // precision T; iterate accumulated into (w0, w1) (v -= alpha d).
 template <typename T>
@@ -471,7 +624,7 @@ int cg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_ou
     if (rel > tol) {
         for (it = 1; it <= max_iter; ++it) {
             // 5.1: homogeneous forward + adjoint period from d; 5.2: Riesz
-            rc = gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1);
+            rc = gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1, true);
             if (rc < 0) return rc;
             // 5.3-5.6
             launch_cg_update(n, H->w0, H->w1, H->r0, H->r1, H->rh0, H->rh1, H->d0, H->d1, H->gt0, H->gt1, H->gh0,
@@ -495,19 +648,33 @@ int cg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_ou
 template <typename T>
 int solve_plain(cmcg_handle* H, double tol, cmcg_stats* stats) {
     const long long n = H->g.np;
-    // (1) v = 0; (2)-(3) gradient with the sources and its Riesz representer
-    launch_fill(H->w0, n, 0.0, H->st);
-    launch_fill(H->w1, n, 0.0, H->st);
-    int rc = gradient<T>(H, H->w0, H->w1, true, H->w0, H->w1, !inexact(H));
-    if (rc < 0) return rc;
-    rc = sync_read(H);
+    // (1) v = 0 or the run-up state; (2)-(3) gradient with the sources and its Riesz map
+    double gamma_zero = -1.0;
+    int rc = initial_guess<T>(H, H->w0, H->w1, &gamma_zero, stats);
     if (rc != CMCG_OK) return rc;
+    rc = gradient<T>(H, H->w0, H->w1, true, H->w0, H->w1, !inexact(H));
+    if (rc < 0) return rc;
+    double scale = 1.0;  // rel w.r.t. this start -> rel w.r.t. the zero guess
+    if (gamma_zero > 0) {
+        double g_init = 0.0;
+        rc = gradient_norm(H, &g_init);
+        if (rc != CMCG_OK) return rc;
+        scale = sqrt(g_init / gamma_zero);
+    } else {
+        rc = sync_read(H);
+        if (rc != CMCG_OK) return rc;
+    }
     stats->J0 = H->hsc[SC_J];
     int iters = 0;
     double rel = 1.0;
-    rc = cg_loop<T>(H, tol, H->opt.max_iter, &iters, &rel);
+    if (scale <= tol) {
+        stats->iterations = 0;
+        stats->rel_residual = scale;
+        return CMCG_OK;
+    }
+    rc = cg_loop<T>(H, tol / scale, H->opt.max_iter, &iters, &rel);
     stats->iterations = iters;
-    stats->rel_residual = rel;
+    stats->rel_residual = rel * scale;
     return rc;
 }
 
@@ -516,9 +683,9 @@ int solve_plain(cmcg_handle* H, double tol, cmcg_stats* stats) {
 int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
     const long long n = H->g.np;
     Red red = H->red();
-    launch_fill(H->wo0, n, 0.0, H->st);
-    launch_fill(H->wo1, n, 0.0, H->st);
     double gamma_ref = -1.0;
+    int rc0 = initial_guess<float>(H, H->wo0, H->wo1, &gamma_ref, stats);
+    if (rc0 != CMCG_OK) return rc0;
     int total = 0, outer = 0;
     double rel = 1.0;
     int rc = CMCG_OK;
@@ -539,7 +706,7 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
         const double gam = H->hsc[SC_R7];
         if (!(gam == gam) || gam < 0) return CMCG_ERR_DIVERGED;
         if (outer == 0) {
-            gamma_ref = gam;
+            if (gamma_ref <= 0) gamma_ref = gam;
             stats->J0 = H->hsc[SC_J];
         }
         rel = gamma_ref > 0 ? sqrt(gam / gamma_ref) : 0.0;
@@ -564,6 +731,32 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
     stats->rel_residual = rel;
     if (cuda_status() != CMCG_OK) return CMCG_ERR_CUDA;
     return rel <= tol ? CMCG_OK : CMCG_NOT_CONVERGED;
+}
+
+// Step (6): U = v0 + i v1 / omega_hat from (w0, w1), then the compatibility-condition shift
+//   lambda = (1.F + wt^2 1.M u + i wh 1.B u) / (wt^2 sum M + i wh sum B)
+// when there is no Dirichlet node.
+int recover(cmcg_handle* h, double* u, cmcg_stats* st) {
+    const long long n = h->g.np;
+    launch_recover(h->g, h->w0, h->w1, h->wh, h->S, h->kap64, h->mass, u, h->red(), h->st);
+    if (sync_read(h) != CMCG_OK) return CMCG_ERR_CUDA;
+    double lre = 0.0, lim = 0.0;
+    if (!h->has_dir) {
+        const double* r = h->hsc + SC_R0;
+        const double wt2 = h->wt * h->wt;
+        const double nre = r[0] + wt2 * r[2] - h->wh * r[5];
+        const double nim = r[1] + wt2 * r[3] + h->wh * r[4];
+        const double dre = wt2 * h->sumM, dim = h->wh * h->sumB;
+        const double den = dre * dre + dim * dim;
+        lre = (nre * dre + nim * dim) / den;
+        lim = (nim * dre - nre * dim) / den;
+        launch_shift(n, u, h->kap64, lre, lim, h->st);
+    }
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    if (cuda_status() != CMCG_OK) return CMCG_ERR_CUDA;
+    st->lambda_re = lre;
+    st->lambda_im = lim;
+    return CMCG_OK;
 }
 
 // Steps (1)-(6) with the source S already in the workspace; U into u (device).
@@ -592,25 +785,7 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
         st->J_final = h->hsc[SC_J];
     }
     // (6) recovery and the compatibility-condition shift
-    launch_recover(h->g, h->w0, h->w1, h->wh, h->S, h->kap64, h->mass, u, h->red(), h->st);
-    if (sync_read(h) != CMCG_OK) return CMCG_ERR_CUDA;
-    double lre = 0.0, lim = 0.0;
-    if (!h->has_dir) {
-        const double* r = h->hsc + SC_R0;
-        const double wt2 = h->wt * h->wt;
-        // lambda = (1.F + wt^2 1.M u + i wh 1.B u) / (wt^2 sum M + i wh sum B)
-        const double nre = r[0] + wt2 * r[2] - h->wh * r[5];
-        const double nim = r[1] + wt2 * r[3] + h->wh * r[4];
-        const double dre = wt2 * h->sumM, dim = h->wh * h->sumB;
-        const double den = dre * dre + dim * dim;
-        lre = (nre * dre + nim * dim) / den;
-        lim = (nim * dre - nre * dim) / den;
-        launch_shift(n, u, h->kap64, lre, lim, h->st);
-    }
-    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
-    if (cuda_status() != CMCG_OK) return CMCG_ERR_CUDA;
-    st->lambda_re = lre;
-    st->lambda_im = lim;
+    if (recover(h, u, st) != CMCG_OK) return CMCG_ERR_CUDA;
     st->steps_per_period = h->N;
     st->dt = h->dt;
     st->omega_tilde = h->wt;
@@ -628,7 +803,24 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
 }
 
 
-}  // namespace
+template PeriodBuffers fwd_begin<float>(cmcg_handle*, const double*, const double*, bool);
+template PeriodBuffers fwd_begin<double>(cmcg_handle*, const double*, const double*, bool);
+template void fwd_end<float>(cmcg_handle*, const PeriodBuffers&, const double*, bool, int, double*, double*);
+template void fwd_end<double>(cmcg_handle*, const PeriodBuffers&, const double*, bool, int, double*, double*);
+template PeriodBuffers adj_begin<float>(cmcg_handle*, const double*, const double*);
+template PeriodBuffers adj_begin<double>(cmcg_handle*, const double*, const double*);
+template void adj_end<float>(cmcg_handle*, const PeriodBuffers&, const double*, const double*, int, const double*,
+                             const double*, double*, double*, double*);
+template void adj_end<double>(cmcg_handle*, const PeriodBuffers&, const double*, const double*, int, const double*,
+                              const double*, double*, double*, double*);
+template int gradient<double>(cmcg_handle*, const double*, const double*, bool, const double*, const double*, bool);
+template int gradient<float>(cmcg_handle*, const double*, const double*, bool, const double*, const double*, bool);
+template void forward_period<double>(cmcg_handle*, const double*, const double*, bool, int, double*, double*);
+
+}  // namespace detail
+}  // namespace cmcg
+
+using namespace cmcg::detail;
 
 // ---- period on caller-provided scratch (used by the allocation-free entry point) --------
 namespace cmcg {
@@ -771,7 +963,8 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     };
     cudaMemsetAsync(H->tickets, 0, sizeof(unsigned) * kNumTickets, H->st);
     cudaMemsetAsync(H->sc, 0, sizeof(double) * SC_COUNT, H->st);
-    // pass 1 (dt = 1): validity, sums, c_max
+    cudaMemsetAsync(H->sc + 6, 0xFF, sizeof(double), H->st);
+    // pass 1 (dt = 1): validity, sums, c_max, c_min
     launch_setup_coeffs(H->g, c, bc->dirichlet_mask, dir, 1.0, H->kap64, H->kap32, H->mass, H->mask, H->red(), H->st);
     if (sync_read(H) != CMCG_OK) return fail(CMCG_ERR_CUDA);
     if (H->hsc[3] != 0.0) return fail(CMCG_ERR_INVALID_ARG);
@@ -783,8 +976,14 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     memcpy(&bits, &H->hsc[5], sizeof(bits));
     double cmax;
     memcpy(&cmax, &bits, sizeof(cmax));
+    memcpy(&bits, &H->hsc[6], sizeof(bits));
+    memcpy(&H->cmin, &bits, sizeof(double));
     if (H->has_dir && H->order == 4) return fail(CMCG_ERR_UNSUPPORTED);
     if (H->has_dir && H->sumW <= 0) return fail(CMCG_ERR_INVALID_ARG);
+    if (o.runup_periods < -1 || o.runup_periods > 100000) return fail(CMCG_ERR_INVALID_ARG);
+    if (o.tile[0] < 0 || o.tile[0] > 512 || o.tile[1] < 0 || o.tile[1] > 512 || o.tile[2] < 0 || o.tile[2] > 16 ||
+        o.tile[3] != 0)
+        return fail(CMCG_ERR_INVALID_ARG);
     // time step: N = ceil(T / dt_target - 1e-9), dt = T / N
     const double dt_target = o.dt > 0 ? o.dt : 0.5 * grid->h / (sqrt((double)grid->dim) * cmax);
     H->N = (int)ceil(H->T / dt_target - 1e-9);
@@ -927,6 +1126,7 @@ const char* cmcg_status_string(int s) {
         case CMCG_ERR_UNSUPPORTED: return "unsupported combination";
         case CMCG_ERR_CUDA: return "CUDA error";
         case CMCG_ERR_DIVERGED: return "diverged (non-finite or non-positive CG scalar)";
+        case CMCG_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
         default: return "unknown status";
     }
 }

@@ -1,0 +1,503 @@
+// Multi-solve engine: many CMCG solves (different grids, frequencies, sources) advance
+// together, one CG iteration per tick.
+//
+// Each admitted solve sits in a slot with its own handle (workspace, resident CG state).  A
+// tick enqueues, for every active slot, its next unit of work:
+//   - OUTER (CMCG_MIXED): W += w; FP64 gradient of J at W with the sources; z = B rhat; w = 0;
+//     d = z  (the defect-correction residual, Sec. 2.3 steps (2)-(4) in FP64);
+//   - INIT  (CMCG_FP32): w = 0; FP32 gradient with the sources; z = B rhat; d = z;
+//   - INNER: one flexible-CG iteration with FP32 periods (Steps 5.1-5.7).
+// The FP32 leapfrog step loops of all INNER slots run in ONE batched persistent kernel per
+// period (forward, then adjoint); everything else is per-slot launches.  The tick is captured
+// as a CUDA graph and replayed while the set of (slot, unit) pairs stays the same.  After each
+// tick the host reads every slot's convergence word and moves slots between units; a finished
+// slot gets its recovery (Step (6)) and is released.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "cmcg.h"
+#include "solver.h"
+
+using namespace cmcg;
+using namespace cmcg::detail;
+
+namespace {
+
+enum Unit { U_FREE = 0, U_INIT32, U_OUTER, U_INNER, U_DONE };
+
+struct EngineSlot {
+    cmcg_handle* h = nullptr;
+    double* u = nullptr;
+    double tol = 0;
+    int unit = U_FREE;
+    int status = CMCG_OK;
+    int iters = 0, inner_iters = 0, outer = 0;
+    long long periods = 0, riesz = 0;  // counted per tick (graph replays skip the launch-time counters)
+    double gamma_ref = -1, rel = 1, inner_tol = 1e-3;
+    long long launches0 = 0;
+    std::chrono::steady_clock::time_point t0;
+    cmcg_stats st{};
+};
+
+}  // namespace
+
+struct cmcg_engine {
+    cudaStream_t st = nullptr;
+    int max_slots = 0;
+    std::vector<EngineSlot> slots;
+    // device
+    BatchItem* items_dev = nullptr;  // [2 * max_slots]: forward items, then adjoint items
+    unsigned* bar = nullptr;         // barrier counter + generation
+    int* err = nullptr;              // barrier time-out flag
+    int* err_host = nullptr;         // pinned
+    int grid = 0;
+    bool use_graph = true;
+    // graph cache
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> signature;
+    long long graph_launches = 0;
+    long long ticks = 0, graph_builds = 0;
+    cudaError_t last_error = cudaSuccess;  // the CUDA error behind the last CMCG_ERR_CUDA
+};
+
+namespace {
+
+size_t engine_layout(cmcg_engine* e, int max_slots, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = (off + 255) & ~(size_t)255;
+        char* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    char* items = take(sizeof(BatchItem) * 2 * (size_t)max_slots);
+    char* bar = take(sizeof(unsigned) * 4);
+    char* err = take(sizeof(int) * 4);
+    if (e) {
+        e->items_dev = (BatchItem*)items;
+        e->bar = (unsigned*)bar;
+        e->err = (int*)err;
+    }
+    return off + 256;
+}
+
+BatchItem make_item(cmcg_handle* h, const PeriodBuffers& b, bool adjoint) {
+    BatchItem it{};
+    it.g = h->g;
+    it.kap = h->kap32;
+    it.buf0 = (float*)b.cur;
+    it.buf1 = (float*)b.prev;
+    it.order = h->order;
+    it.nsteps = h->N - 1;
+    it.adjoint = adjoint ? 1 : 0;
+    it.zc = h->g.dim == 3 ? kZcStep3D : 1;
+    const long long plane = (long long)h->g.sx * h->g.sy;
+    it.blocks_xy = (int)((plane + 255) / 256);
+    it.blocks = it.blocks_xy * ((h->g.sz + it.zc - 1) / it.zc);
+    return it;
+}
+
+PeriodBuffers after_steps(PeriodBuffers b, int nsteps) {
+    if (nsteps & 1) std::swap(b.cur, b.prev);
+    return b;
+}
+
+// The per-slot prologue of a unit that ends with "z = B rhat, d = z" (OUTER, INIT32).
+void reset_direction(cmcg_handle* h) {
+    const long long n = h->g.np;
+    cudaMemcpyAsync(h->rh0, h->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
+    cudaMemcpyAsync(h->rh1, h->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
+    apply_B(h, true);
+    cudaMemcpyAsync(h->d0, h->r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
+    cudaMemcpyAsync(h->d1, h->r1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
+}
+
+// Enqueue one tick on the engine's stream (also used while capturing).
+cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
+    cudaMemsetAsync(e->err, 0, sizeof(int), e->st);
+    std::vector<int> inner;
+    for (int s : act) {
+        EngineSlot& sl = e->slots[s];
+        cmcg_handle* h = sl.h;
+        const long long n = h->g.np;
+        if (sl.unit == U_OUTER) {
+            launch_axpy(n, 1.0, h->w0, h->wo0, h->st);
+            launch_axpy(n, 1.0, h->w1, h->wo1, h->st);
+            gradient<double>(h, h->wo0, h->wo1, true, h->wo0, h->wo1, false);
+            launch_fill(h->w0, n, 0.0, h->st);
+            launch_fill(h->w1, n, 0.0, h->st);
+            reset_direction(h);
+        } else if (sl.unit == U_INIT32) {
+            launch_fill(h->w0, n, 0.0, h->st);
+            launch_fill(h->w1, n, 0.0, h->st);
+            gradient<float>(h, h->w0, h->w1, true, h->w0, h->w1, false);
+            reset_direction(h);
+        } else if (sl.unit == U_INNER) {
+            inner.push_back(s);
+        }
+    }
+    if (!inner.empty()) {
+        const int m = (int)inner.size();
+        std::vector<PeriodBuffers> fb(m), ab(m);
+        // forward periods from d: start kernels, one batched step loop, end kernels
+        int total = 0, maxs = 0;
+        std::vector<BatchItem> items(2 * (size_t)m);
+        for (int i = 0; i < m; ++i) {
+            cmcg_handle* h = e->slots[inner[i]].h;
+            fb[i] = fwd_begin<float>(h, h->d0, h->d1, false);
+            items[i] = make_item(h, fb[i], false);
+            items[i].offset = total;
+            total += items[i].blocks;
+            maxs = std::max(maxs, items[i].nsteps);
+        }
+        cudaError_t ce = launch_batch_steps(e->items_dev, m, total, maxs, e->bar, e->err, e->grid, e->st);
+        if (ce != cudaSuccess) return ce;
+        int total_a = 0, maxa = 0;
+        for (int i = 0; i < m; ++i) {
+            cmcg_handle* h = e->slots[inner[i]].h;
+            fwd_end<float>(h, after_steps(fb[i], h->N - 1), h->d1, false, 0, h->z0, h->z1);
+            ab[i] = adj_begin<float>(h, h->z0, h->z1);
+            items[m + i] = make_item(h, ab[i], true);
+            items[m + i].offset = total_a;
+            total_a += items[m + i].blocks;
+            maxa = std::max(maxa, items[m + i].nsteps);
+        }
+        ce = launch_batch_steps(e->items_dev + e->max_slots, m, total_a, maxa, e->bar, e->err, e->grid, e->st);
+        if (ce != cudaSuccess) return ce;
+        for (int i = 0; i < m; ++i) {
+            cmcg_handle* h = e->slots[inner[i]].h;
+            const long long n = h->g.np;
+            adj_end<float>(h, after_steps(ab[i], h->N - 1), h->z0, h->z1, 0, h->d0, h->d1, h->gh0, h->gh1, h->gt1);
+            launch_fcg_update(n, h->w0, h->w1, h->rh0, h->rh1, h->d0, h->d1, h->gh0, h->gh1, h->red(), h->st);
+            apply_B(h, false);
+            launch_cg_direction(n, h->r0, h->r1, h->d0, h->d1, h->red(), h->st);
+        }
+        // the descriptors are uploaded before the tick (upload_items)
+    }
+    for (int s : act) {
+        cmcg_handle* h = e->slots[s].h;
+        cudaMemcpyAsync(h->hsc, h->sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, e->st);
+    }
+    cudaMemcpyAsync(e->err_host, e->err, sizeof(int), cudaMemcpyDeviceToHost, e->st);
+    return cudaGetLastError();
+}
+
+// Batch descriptors of the INNER slots (forward and adjoint): the buffer roles at step 0 are
+// fixed per handle (fwd: cur = yb, prev = ya; adjoint: cur = ya, prev = yb), so they can be
+// uploaded before the tick and stay valid across graph replays.
+void upload_items(cmcg_engine* e, const std::vector<int>& act) {
+    std::vector<BatchItem> items(2 * (size_t)e->max_slots);
+    int m = 0, tf = 0, ta = 0;
+    for (int s : act) {
+        EngineSlot& sl = e->slots[s];
+        if (sl.unit != U_INNER) continue;
+        cmcg_handle* h = sl.h;
+        PeriodBuffers f{h->yb, h->ya, nullptr}, a{h->ya, h->yb, nullptr};
+        items[m] = make_item(h, f, false);
+        items[m].offset = tf;
+        tf += items[m].blocks;
+        items[e->max_slots + m] = make_item(h, a, true);
+        items[e->max_slots + m].offset = ta;
+        ta += items[e->max_slots + m].blocks;
+        ++m;
+    }
+    cudaMemcpyAsync(e->items_dev, items.data(), sizeof(BatchItem) * 2 * (size_t)e->max_slots, cudaMemcpyHostToDevice,
+                    e->st);
+    cudaStreamSynchronize(e->st);
+}
+
+int finish_slot(cmcg_engine* e, int s) {
+    EngineSlot& sl = e->slots[s];
+    cmcg_handle* h = sl.h;
+    const long long n = h->g.np;
+    if (h->opt.precision == CMCG_MIXED) {
+        cudaMemcpyAsync(h->w0, h->wo0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
+        cudaMemcpyAsync(h->w1, h->wo1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
+    }
+    if (recover(h, sl.u, &sl.st) != CMCG_OK) return CMCG_ERR_CUDA;
+    sl.st.iterations = sl.iters;
+    sl.st.outer_iterations = sl.outer;
+    sl.st.rel_residual = sl.rel;
+    sl.st.steps_per_period = h->N;
+    sl.st.dt = h->dt;
+    sl.st.omega_tilde = h->wt;
+    sl.st.omega_hat = h->wh;
+    sl.st.periods = (int)sl.periods;
+    sl.st.riesz_iterations = (int)sl.riesz;
+    sl.st.point_updates = sl.periods * (long long)h->N * n;
+    sl.st.kernel_launches = launch_count() - sl.launches0;
+    sl.st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - sl.t0).count();
+    sl.unit = U_DONE;
+    return CMCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cmcg_engine_workspace_size(int max_slots) {
+    if (max_slots <= 0 || max_slots > 4096) return 0;
+    return engine_layout(nullptr, max_slots, nullptr);
+}
+
+int cmcg_engine_create(int max_slots, void* workspace, size_t ws_bytes, void* stream, int flags,
+                       cmcg_engine** out) {
+    if (!out || max_slots <= 0 || max_slots > 4096 || !workspace) return CMCG_ERR_INVALID_ARG;
+    if (((uintptr_t)workspace & 255u) != 0 || (flags & ~CMCG_ENGINE_NO_GRAPH)) return CMCG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (ws_bytes < cmcg_engine_workspace_size(max_slots)) return CMCG_ERR_WORKSPACE;
+    cmcg_engine* e = new cmcg_engine();
+    e->st = (cudaStream_t)stream;
+    e->max_slots = max_slots;
+    e->slots.resize(max_slots);
+    // stream capture needs a created stream: on the legacy default stream run plain launches
+    e->use_graph = (flags & CMCG_ENGINE_NO_GRAPH) == 0 && stream != nullptr;
+    engine_layout(e, max_slots, (char*)workspace);
+    if (cudaMallocHost((void**)&e->err_host, sizeof(int)) != cudaSuccess) {
+        delete e;
+        return CMCG_ERR_CUDA;
+    }
+    cudaMemsetAsync(e->bar, 0, sizeof(unsigned) * 4, e->st);
+    cudaMemsetAsync(e->err, 0, sizeof(int) * 4, e->st);
+    e->grid = batch_steps_max_blocks();
+    if (cudaStreamSynchronize(e->st) != cudaSuccess || e->grid <= 0) {
+        cudaFreeHost(e->err_host);
+        delete e;
+        return CMCG_ERR_CUDA;
+    }
+    *out = e;
+    return CMCG_OK;
+}
+
+int cmcg_engine_destroy(cmcg_engine* e) {
+    if (!e) return CMCG_ERR_INVALID_ARG;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    cudaFreeHost(e->err_host);
+    delete e;
+    return CMCG_OK;
+}
+
+int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const double* g, double tol, double* u) {
+    if (!e || !h || !u || !(tol > 0)) return CMCG_ERR_INVALID_ARG;
+    if (h->st != e->st || h->opt.precision == CMCG_FP64 || !(h->opt.flags & CMCG_FLAG_INEXACT_RIESZ))
+        return CMCG_ERR_UNSUPPORTED;
+    int s = -1;
+    for (int i = 0; i < e->max_slots; ++i) {
+        if (e->slots[i].h == h && e->slots[i].unit != U_FREE) return CMCG_ERR_INVALID_ARG;  // handle busy
+        if (s < 0 && e->slots[i].unit == U_FREE) s = i;
+    }
+    if (s < 0) return CMCG_ERR_WORKSPACE;  // no free slot
+    EngineSlot& sl = e->slots[s];
+    sl = EngineSlot();
+    sl.h = h;
+    sl.u = u;
+    sl.tol = tol;
+    sl.t0 = std::chrono::steady_clock::now();
+    sl.launches0 = launch_count();
+    h->riesz_iters = 0;
+    h->periods = 0;
+    if (f || g)
+        launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
+    else
+        launch_fill(h->S, 2 * h->g.np, 0.0, h->st);
+    if (h->opt.precision == CMCG_MIXED) {
+        launch_fill(h->wo0, h->g.np, 0.0, h->st);
+        launch_fill(h->wo1, h->g.np, 0.0, h->st);
+        launch_fill(h->w0, h->g.np, 0.0, h->st);
+        launch_fill(h->w1, h->g.np, 0.0, h->st);
+        sl.unit = U_OUTER;
+    } else {
+        sl.unit = U_INIT32;
+    }
+    if (cudaGetLastError() != cudaSuccess) return CMCG_ERR_CUDA;
+    return s;
+}
+
+int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_finished) {
+    if (!e || !n_finished || (max_finished > 0 && !finished)) return CMCG_ERR_INVALID_ARG;
+    *n_finished = 0;
+    std::vector<int> act;
+    for (int i = 0; i < e->max_slots; ++i) {
+        const int u = e->slots[i].unit;
+        if (u == U_INIT32 || u == U_OUTER || u == U_INNER) act.push_back(i);
+    }
+    if (act.empty()) return CMCG_OK;
+    // configuration signature: (slot, unit, handle) of every active slot
+    std::vector<long long> sig;
+    for (int s : act) {
+        sig.push_back(s);
+        sig.push_back(e->slots[s].unit);
+        sig.push_back((long long)(uintptr_t)e->slots[s].h);
+    }
+    const bool same = e->exec != nullptr && sig == e->signature;
+    if (!same) upload_items(e, act);
+    if (e->use_graph) {
+        if (!same) {
+            if (e->exec) {
+                cudaGraphExecDestroy(e->exec);
+                e->exec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce0 = cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal);
+            if (ce0 != cudaSuccess) {
+                e->last_error = ce0;
+                return CMCG_ERR_CUDA;
+            }
+            const long long before = launch_count();
+            const cudaError_t ce = enqueue_tick(e, act);
+            const cudaError_t ce2 = cudaStreamEndCapture(e->st, &graph);
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(e->st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g2 = nullptr;
+                cudaStreamEndCapture(e->st, &g2);  // never leave the stream capturing
+                if (g2) cudaGraphDestroy(g2);
+            }
+            if (ce != cudaSuccess || ce2 != cudaSuccess || !graph) {
+                e->last_error = ce != cudaSuccess ? ce : (ce2 != cudaSuccess ? ce2 : cudaErrorUnknown);
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return CMCG_ERR_CUDA;
+            }
+            const cudaError_t ce3 = cudaGraphInstantiate(&e->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce3 != cudaSuccess) {
+                e->last_error = ce3;
+                e->exec = nullptr;
+                return CMCG_ERR_CUDA;
+            }
+            e->signature = sig;
+            e->graph_launches = launch_count() - before;  // kernels one replay runs
+            e->graph_builds += 1;
+        } else {
+            note_launch(e->graph_launches);
+        }
+        const cudaError_t ce = cudaGraphLaunch(e->exec, e->st);
+        if (ce != cudaSuccess) {
+            e->last_error = ce;
+            return CMCG_ERR_CUDA;
+        }
+    } else {
+        const cudaError_t ce = enqueue_tick(e, act);
+        if (ce != cudaSuccess) {
+            e->last_error = ce;
+            return CMCG_ERR_CUDA;
+        }
+    }
+    const cudaError_t cs = cudaStreamSynchronize(e->st);
+    if (cs != cudaSuccess) {
+        e->last_error = cs;
+        return CMCG_ERR_CUDA;
+    }
+    e->ticks += 1;
+    const bool timeout = *e->err_host != 0;
+    for (int s : act) {
+        EngineSlot& sl = e->slots[s];
+        cmcg_handle* h = sl.h;
+        const double* sc = h->hsc;
+        bool done = false;
+        sl.periods += 2;  // every unit runs one forward and one adjoint period
+        sl.riesz += 1;    // and one approximate Riesz map
+        if (timeout && sl.unit == U_INNER) {
+            sl.status = CMCG_ERR_DEVICE_TIMEOUT;
+            done = true;
+        } else if (sc[SC_STATUS] != 0.0) {
+            sl.status = CMCG_ERR_DIVERGED;
+            done = true;
+        } else if (sl.unit == U_OUTER) {
+            const double gam = sc[SC_GAMMA0];
+            if (sl.outer == 0) {
+                sl.gamma_ref = gam;
+                sl.st.J0 = sc[SC_J];
+            }
+            sl.outer += 1;
+            sl.rel = sl.gamma_ref > 0 ? sqrt(std::max(gam, 0.0) / sl.gamma_ref) : 0.0;
+            if (sl.rel <= sl.tol) {
+                sl.status = CMCG_OK;
+                done = true;
+            } else if (sl.iters >= h->opt.max_iter || sl.outer > 50) {
+                sl.status = CMCG_NOT_CONVERGED;
+                done = true;
+            } else {
+                sl.inner_tol = std::min(0.5, std::max(h->opt.inner_tol, 0.5 * sl.tol / sl.rel));
+                sl.inner_iters = 0;
+                sl.unit = U_INNER;
+            }
+        } else if (sl.unit == U_INIT32) {
+            sl.st.J0 = sc[SC_J];
+            sl.rel = sc[SC_REL];
+            if (sl.rel <= sl.tol) {
+                sl.status = CMCG_OK;
+                done = true;
+            } else {
+                sl.unit = U_INNER;
+            }
+        } else {  // U_INNER
+            sl.iters += 1;
+            sl.inner_iters += 1;
+            const double r = sc[SC_REL];
+            if (h->opt.precision == CMCG_MIXED) {
+                if (r <= sl.inner_tol || sl.iters >= h->opt.max_iter) sl.unit = U_OUTER;
+            } else {
+                sl.rel = r;
+                if (r <= sl.tol) {
+                    sl.status = CMCG_OK;
+                    done = true;
+                } else if (sl.iters >= h->opt.max_iter) {
+                    sl.status = CMCG_NOT_CONVERGED;
+                    done = true;
+                }
+            }
+        }
+        if (done) {
+            if (sl.status >= 0 && finish_slot(e, s) != CMCG_OK) sl.status = CMCG_ERR_CUDA;
+            sl.unit = U_DONE;
+            if (*n_finished < max_finished) finished[*n_finished] = s;
+            *n_finished += 1;
+        }
+    }
+    return timeout ? CMCG_ERR_DEVICE_TIMEOUT : CMCG_OK;
+}
+
+int cmcg_engine_result(cmcg_engine* e, int slot, cmcg_stats* stats) {
+    if (!e || slot < 0 || slot >= e->max_slots || e->slots[slot].unit != U_DONE) return CMCG_ERR_INVALID_ARG;
+    EngineSlot& sl = e->slots[slot];
+    if (stats) *stats = sl.st;
+    const int status = sl.status;
+    sl = EngineSlot();
+    return status;
+}
+
+int cmcg_engine_active(const cmcg_engine* e) {
+    if (!e) return CMCG_ERR_INVALID_ARG;
+    int n = 0;
+    for (const EngineSlot& sl : e->slots) n += (sl.unit == U_INIT32 || sl.unit == U_OUTER || sl.unit == U_INNER) ? 1 : 0;
+    return n;
+}
+
+int cmcg_engine_info(const cmcg_engine* e, long long* ticks, long long* graph_builds) {
+    if (!e) return CMCG_ERR_INVALID_ARG;
+    if (ticks) *ticks = e->ticks;
+    if (graph_builds) *graph_builds = e->graph_builds;
+    return CMCG_OK;
+}
+
+const char* cmcg_engine_cuda_error(const cmcg_engine* e) {
+    if (!e) return "invalid engine";
+    return cudaGetErrorName(e->last_error);
+}
+
+int cmcg_engine_barrier_selftest(cmcg_engine* e, long long spin_limit) {
+    if (!e || spin_limit <= 0 || spin_limit > (1ll << 24)) return CMCG_ERR_INVALID_ARG;
+    cudaMemsetAsync(e->bar + 2, 0, sizeof(unsigned) * 2, e->st);
+    cudaMemsetAsync(e->err + 1, 0, sizeof(int), e->st);
+    if (launch_barrier_selftest(e->bar + 2, e->err + 1, spin_limit, e->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    int flag = 0;
+    cudaMemcpyAsync(&flag, e->err + 1, sizeof(int), cudaMemcpyDeviceToHost, e->st);
+    if (cudaStreamSynchronize(e->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return flag ? CMCG_ERR_DEVICE_TIMEOUT : CMCG_OK;
+}
+
+}  // extern "C"

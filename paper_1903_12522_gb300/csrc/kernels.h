@@ -42,6 +42,25 @@ template <typename T>
 void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass, const T* kap,
                       const double* minv, const double* z0, const double* z1, const double* d0, const double* d1,
                       double* o0, double* o1, double* gt1, Red red, double dt, int zc, cudaStream_t st);
+// Two leapfrog steps per launch (3D 7-point, FP32, homogeneous): (A = y^{n-1}, B = y^n) ->
+// (C = y^{n+1}, D = y^{n+2}); the four buffers must be distinct.
+bool step2_supported(const Geom& g, int order);
+void launch_step2(const Geom& g, const float* A, const float* B, const float* kap, float* C, float* D, int zc,
+                  int ty_max, cudaStream_t st);
+
+// Batched persistent step loop (wave.cu): one cooperative launch runs the FP32 step loops of
+// many solves.  offset = prefix sum of blocks over the preceding items.
+struct BatchItem {
+    Geom g;
+    const float* kap;
+    float* buf0;  // y^n at step 0
+    float* buf1;  // y^{n-1} at step 0
+    int order, nsteps, adjoint, zc, blocks_xy, blocks, offset;
+};
+int batch_steps_max_blocks();
+cudaError_t launch_batch_steps(const BatchItem* items, int nitems, int total_blocks, int max_steps, unsigned* bar,
+                               int* err, int grid, cudaStream_t st);
+cudaError_t launch_barrier_selftest(unsigned* bar, int* err, long long spin_limit, cudaStream_t st);
 void launch_make_source(const Geom& g, const double* f, const double* gb, const double* kap64, double* S, int zc,
                         bool accumulate, cudaStream_t st);
 long long plane_blocks(const Geom& g, int zc);

@@ -22,14 +22,14 @@ inline unsigned vec_blocks(long long n) {
 // ---- setup -------------------------------------------------------------------------------
 // kappa = c^2 dt^2 / h^2, M = W / c^2, zero on Dirichlet nodes.  Reduces (sum M, sum B,
 // sum W) over active nodes, the number of invalid c and the number of Dirichlet nodes into
-// sc[0..5), and max c into sc[5] (as the bit pattern of a positive double, which orders like
-// an unsigned integer).
+// sc[0..5), max c into sc[5] and min c into sc[6] (as bit patterns of positive doubles, which
+// order like unsigned integers; sc[6] must start as all ones).
 __global__ void __launch_bounds__(kT) k_setup(const double* __restrict__ c, const unsigned char* __restrict__ umask,
                                               unsigned face_dir, double dt, double* __restrict__ kap64,
                                               float* __restrict__ kap32, double* __restrict__ mass,
                                               unsigned char* __restrict__ mask, Red red, Geom g) {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    unsigned long long cmax_bits = 0ull;
+    unsigned long long cmax_bits = 0ull, cmin_bits = ~0ull;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
         const unsigned t = (unsigned)j / (unsigned)g.sx;
@@ -67,14 +67,20 @@ __global__ void __launch_bounds__(kT) k_setup(const double* __restrict__ c, cons
         if (cj > 0.0 && isfinite(cj)) {
             const unsigned long long bits = (unsigned long long)__double_as_longlong(cj);
             cmax_bits = bits > cmax_bits ? bits : cmax_bits;
+            cmin_bits = bits < cmin_bits ? bits : cmin_bits;
         }
     }
     // max c: order-independent atomic on the bit pattern of positive doubles
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long other = __shfl_down_sync(0xffffffffu, cmax_bits, o);
         cmax_bits = other > cmax_bits ? other : cmax_bits;
+        other = __shfl_down_sync(0xffffffffu, cmin_bits, o);
+        cmin_bits = other < cmin_bits ? other : cmin_bits;
     }
-    if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)&red.sc[5], cmax_bits);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax((unsigned long long*)&red.sc[5], cmax_bits);
+        atomicMin((unsigned long long*)&red.sc[6], cmin_bits);
+    }
     if (grid_sum<5>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
         for (int k = 0; k < 5; ++k) red.sc[k] = acc[k];
     }

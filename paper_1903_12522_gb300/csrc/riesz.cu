@@ -136,8 +136,36 @@ __device__ __forceinline__ void fine_range(int J, int nf, int nc, int& lo, int& 
     hi = hi > nf ? nf : hi;
 }
 
+__device__ __forceinline__ bool nested(const Geom& gf, const Geom& gc) {
+    return gf.nx == 2 * gc.nx && gf.ny == 2 * gc.ny && (gf.dim == 2 || gf.nz == 2 * gc.nz);
+}
+
+// nested 2:1 case: weights 1 at 2J and 1/2 at 2J +- 1 per axis
+__device__ __forceinline__ float restrict_nested(const Geom& gf, const float* rf, int jx, int jy, int jz) {
+    const int cx = 2 * jx, cy = 2 * jy, cz = 2 * jz;
+    float acc = 0.f;
+    const int zlo = gf.dim == 3 ? -1 : 0, zhi = gf.dim == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        const int fz = cz + dz;
+        if (fz < 0 || fz > gf.nz) continue;
+        const float wz = dz == 0 ? 1.f : 0.5f;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int fy = cy + dy;
+            if (fy < 0 || fy > gf.ny) continue;
+            const float wy = dy == 0 ? 1.f : 0.5f;
+            const float* row = rf + node(gf, 0, fy, fz);
+            float racc = row[cx];
+            if (cx > 0) racc += 0.5f * row[cx - 1];
+            if (cx < gf.nx) racc += 0.5f * row[cx + 1];
+            acc += wy * wz * racc;
+        }
+    }
+    return acc;
+}
+
 __device__ __forceinline__ float restrict_node(const Geom& gf, const Geom& gc, const float* rf, int jx, int jy,
                                                int jz) {
+    if (nested(gf, gc)) return restrict_nested(gf, rf, jx, jy, jz);
     int xlo, xhi, ylo, yhi, zlo = 0, zhi = 0;
     fine_range(jx, gf.nx, gc.nx, xlo, xhi);
     fine_range(jy, gf.ny, gc.ny, ylo, yhi);
@@ -159,14 +187,24 @@ __device__ __forceinline__ float restrict_node(const Geom& gf, const Geom& gc, c
     return acc;
 }
 
+__device__ __forceinline__ Interp1 interp1_fast(int i, int nf, int nc) {
+    if (nf == 2 * nc) {
+        Interp1 r;
+        r.j0 = i >> 1;
+        r.t = (i & 1) ? 0.5f : 0.f;
+        return r;
+    }
+    return interp1(i, nf, nc);
+}
+
 __device__ __forceinline__ float prolong_node(const Geom& gc, const float* xc, const Geom& gf, int ix, int iy, int iz) {
-    const Interp1 px = interp1(ix, gf.nx, gc.nx), py = interp1(iy, gf.ny, gc.ny);
+    const Interp1 px = interp1_fast(ix, gf.nx, gc.nx), py = interp1_fast(iy, gf.ny, gc.ny);
     const int x1 = px.t > 0.f ? px.j0 + 1 : px.j0, y1 = py.t > 0.f ? py.j0 + 1 : py.j0;
     const float ax = 1.f - px.t, ay = 1.f - py.t;
     float v = ay * (ax * xc[node(gc, px.j0, py.j0, 0)] + px.t * xc[node(gc, x1, py.j0, 0)]) +
               py.t * (ax * xc[node(gc, px.j0, y1, 0)] + px.t * xc[node(gc, x1, y1, 0)]);
     if (gf.dim == 3) {
-        const Interp1 pz = interp1(iz, gf.nz, gc.nz);
+        const Interp1 pz = interp1_fast(iz, gf.nz, gc.nz);
         const int z1 = pz.t > 0.f ? pz.j0 + 1 : pz.j0;
         const long long offz0 = (long long)pz.j0 * gc.sx * gc.sy, offz1 = (long long)z1 * gc.sx * gc.sy;
         const float* c0 = xc + offz0;

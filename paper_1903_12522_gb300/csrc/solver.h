@@ -1,0 +1,105 @@
+// Internal: the solver handle and the host-side pieces shared by the single-solve entry
+// points (api.cu) and the multi-solve engine (engine.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "cmcg.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cmcg {
+constexpr int kMaxLevels = 16;
+constexpr int kZcStep3D = 16;  // z-planes per thread in the leapfrog step (3D)
+constexpr int kZcEnds = 8;     // z-planes per thread in the period endpoint kernels
+constexpr int kZcStep2 = 24;   // z-planes per block in the two-step kernel
+constexpr double kPi = 3.14159265358979323846;
+}  // namespace cmcg
+
+using namespace cmcg;  // internal header: the handle's members use the library's types
+
+struct cmcg_handle {
+    Geom g{};
+    int order = 2;
+    cmcg_options opt{};
+    cudaStream_t st = nullptr;
+    double omega = 0, T = 0, dt = 0, wt = 0, wh = 0, volume = 0;
+    int N = 0;
+    bool has_dir = false;
+    double sumM = 0, sumB = 0, sumW = 0, cmin = 1;
+    // coefficients
+    double *kap64 = nullptr, *mass = nullptr, *minv = nullptr, *S = nullptr;
+    float* kap32 = nullptr;
+    unsigned char* mask = nullptr;
+    // wave buffers (sized for double; FP32 stepping uses the first half) + FP64 temp
+    void *ya = nullptr, *yb = nullptr;
+    double* tmp = nullptr;
+    // CG state
+    double *w0, *w1, *r0, *r1, *rh0, *rh1, *d0, *d1, *gh0, *gh1, *gt0, *gt1, *z0, *z1;
+    double *wo0 = nullptr, *wo1 = nullptr;  // CMCG_MIXED outer iterate
+    // Riesz PCG
+    double *pr, *pp, *pAp, *pzd;
+    MGLevel lv[kMaxLevels];
+    int nlev = 0;
+    int blk_level = -1;       // first level run inside one thread block (-1: none)
+    BlockLevels blk{};
+    int riesz_guess = 0;      // PCG iterations of the previous Riesz solve
+    // host staging
+    double* stage = nullptr;
+    // reductions
+    double* partials = nullptr;
+    unsigned* tickets = nullptr;
+    double* sc = nullptr;
+    double* hsc = nullptr;  // pinned host mirror of sc
+    // counters of the current call
+    long long riesz_iters = 0;
+    long long periods = 0;
+    // CMCG_FLAG_TIMING: event pairs around the step loops of the periods since the last sync
+    bool timing = false;
+    cudaEvent_t ev[8] = {};
+    int ev_used = 0;
+    bool ev_fp32[4] = {};
+    int ev_steps[4] = {};
+    double step_s[2] = {0, 0};     // [fp64, fp32]
+    long long step_n[2] = {0, 0};
+    Red red() const { return Red{partials, tickets, sc}; }
+};
+
+namespace cmcg {
+namespace detail {
+
+// The two leapfrog buffers of a period in flight: cur holds y^n, prev y^{n-1}; w0t is the
+// stepping-precision copy of the initial displacement (forward periods).
+struct PeriodBuffers {
+    void* cur;
+    void* prev;
+    const void* w0t;
+};
+
+int cuda_status();
+int sync_read(cmcg_handle* H);
+bool inexact(const cmcg_handle* H);
+void apply_B(cmcg_handle* H, bool first);
+int adj_step_flags(int k, int N);
+template <typename T>
+PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool src);
+template <typename T>
+void fwd_end(cmcg_handle* H, const PeriodBuffers& b, const double* w1, bool src, int mode, double* out0,
+             double* out1);
+template <typename T>
+PeriodBuffers adj_begin(cmcg_handle* H, const double* a, const double* bb);
+template <typename T>
+void adj_end(cmcg_handle* H, const PeriodBuffers& b, const double* a, const double* bb, int mode, const double* d0,
+             const double* d1, double* o0, double* o1, double* gt1);
+template <typename T>
+int gradient(cmcg_handle* H, const double* w0, const double* w1, bool src, const double* dd0, const double* dd1,
+             bool riesz);
+template <typename T>
+void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src, int mode, double* out0,
+                    double* out1);
+// Step (6): U from (w0, w1) into u and the compatibility-condition shift; fills st's
+// lambda fields.  Synchronises the stream.
+int recover(cmcg_handle* h, double* u, cmcg_stats* st);
+
+}  // namespace detail
+}  // namespace cmcg

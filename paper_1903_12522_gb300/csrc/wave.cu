@@ -357,6 +357,284 @@ __global__ void __launch_bounds__(kThreads) k_make_source(const double* __restri
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Two leapfrog steps per sweep (temporal blocking), 3D 7-point, FP32, homogeneous steps.
+// A block owns an interior tile TX x TY of every plane in its z-chunk and marches z.  It keeps
+// in shared memory a 3-plane ring of y^n over the tile plus a 2-node halo (mirror-filled at
+// the faces) and a 3-plane ring of y^{n+1} over the tile plus a 1-node halo (computed
+// redundantly at the halo, with the mirrored node's coefficients, so that it equals the
+// mirror value there).  Per plane k: load y^n(k+1); y^{n+1}(k) on the 1-halo region;
+// y^{n+2}(k-1) on the interior.  y^{n-1}, kappa are read at the points they are needed.
+// Outputs go to two other buffers (y^{n+1} -> C, y^{n+2} -> D): other blocks still read the
+// inputs' halos.  Each output equals two applications of the one-step update.
+constexpr int kTbThreads = 256;
+constexpr int kTbMaxW = 68, kTbMaxH = 20;                       // interior tile <= 64 x 16
+constexpr int kTbR2 = (kTbMaxW * kTbMaxH + kTbThreads - 1) / kTbThreads;                  // points per thread
+constexpr int kTbR1 = ((kTbMaxW - 2) * (kTbMaxH - 2) + kTbThreads - 1) / kTbThreads;
+constexpr int kTbR0 = ((kTbMaxW - 4) * (kTbMaxH - 4) + kTbThreads - 1) / kTbThreads;
+
+__device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
+__device__ __forceinline__ int ring(int p) { return ((p % 3) + 3) % 3; }
+
+__global__ void __launch_bounds__(kTbThreads) k_step3d7_x2(const float* __restrict__ A, const float* __restrict__ B,
+                                                           const float* __restrict__ kap, float* __restrict__ Cout,
+                                                           float* __restrict__ Dout, Geom g, int TX, int TY, int zc) {
+    extern __shared__ float sm[];
+    const int W2 = TX + 4, H2 = TY + 4, W1 = TX + 2, H1 = TY + 2;
+    float* Y = sm;                  // 3 x W2 x H2
+    float* L = sm + 3 * W2 * H2;    // 3 x W1 x H1
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.sz);
+    const long long sxy = (long long)g.sx * g.sy;
+    const int tid = threadIdx.x;
+    // per-thread point lists (same every plane)
+    int p2_off[kTbR2], p2_phys[kTbR2];
+    int p1_loc[kTbR1], p1_phys[kTbR1], p1_nb[kTbR1];
+    int p0_loc[kTbR0], p0_phys[kTbR0], p0_nb[kTbR0], p0_l1[kTbR0];
+#pragma unroll
+    for (int r = 0; r < kTbR2; ++r) {
+        const int i = tid + r * kTbThreads;
+        p2_off[r] = -1;
+        if (i < W2 * H2) {
+            const int lx = i % W2, ly = i / W2;
+            const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
+            if (gx <= g.nx + 2 && gy <= g.ny + 2) {
+                p2_off[r] = i;
+                p2_phys[r] = mirror(gx, g.nx) + g.sx * mirror(gy, g.ny);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kTbR1; ++r) {
+        const int i = tid + r * kTbThreads;
+        p1_loc[r] = -1;
+        if (i < W1 * H1) {
+            const int lx = i % W1, ly = i / W1;
+            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            if (gx <= g.nx + 1 && gy <= g.ny + 1) {
+                const int px = mirror(gx, g.nx), py = mirror(gy, g.ny);
+                p1_loc[r] = (lx + 1) + W2 * (ly + 1);  // position in the Y plane
+                p1_phys[r] = px + g.sx * py;
+                p1_nb[r] = ((px == 0) & (int)(g.abc & 1u)) + ((px == g.nx) & (int)((g.abc >> 1) & 1u)) +
+                           ((py == 0) & (int)((g.abc >> 2) & 1u)) + ((py == g.ny) & (int)((g.abc >> 3) & 1u));
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kTbR0; ++r) {
+        const int i = tid + r * kTbThreads;
+        p0_loc[r] = -1;
+        if (i < TX * TY) {
+            const int lx = i % TX, ly = i / TX;
+            const int gx = x0 + lx, gy = y0 + ly;
+            if (gx <= g.nx && gy <= g.ny) {
+                p0_loc[r] = (lx + 2) + W2 * (ly + 2);
+                p0_l1[r] = (lx + 1) + W1 * (ly + 1);
+                p0_phys[r] = gx + g.sx * gy;
+                p0_nb[r] = ((gx == 0) & (int)(g.abc & 1u)) + ((gx == g.nx) & (int)((g.abc >> 1) & 1u)) +
+                           ((gy == 0) & (int)((g.abc >> 2) & 1u)) + ((gy == g.ny) & (int)((g.abc >> 3) & 1u));
+            }
+        }
+    }
+    const int zabc0 = (int)((g.abc >> 4) & 1u), zabc1 = (int)((g.abc >> 5) & 1u);
+    auto load_plane = [&](int p) {  // y^n at virtual plane p into the ring
+        float* dst = Y + ring(p) * W2 * H2;
+        const long long base = (long long)mirror(p, g.nz) * sxy;
+#pragma unroll
+        for (int r = 0; r < kTbR2; ++r)
+            if (p2_off[r] >= 0) dst[p2_off[r]] = B[base + p2_phys[r]];
+    };
+    load_plane(z0 - 2);
+    load_plane(z0 - 1);
+    for (int k = z0 - 1; k <= z1; ++k) {
+        load_plane(k + 1);
+        __syncthreads();
+        if (k >= 0 && k <= g.nz) {
+            // y^{n+1} at plane k over the 1-halo region
+            const float* Ym = Y + ring(k - 1) * W2 * H2;
+            const float* Yc = Y + ring(k) * W2 * H2;
+            const float* Yp = Y + ring(k + 1) * W2 * H2;
+            float* Lk = L + ring(k) * W1 * H1;
+            const long long base = (long long)k * sxy;
+            const int nbz = ((k == 0) & zabc0) + ((k == g.nz) & zabc1);
+            const bool write_c = k >= z0 && k < z1;
+#pragma unroll
+            for (int r = 0; r < kTbR1; ++r) {
+                const int c = p1_loc[r];
+                if (c < 0) continue;
+                const float yc = Yc[c];
+                const float lap = 6.f * yc - ((Yc[c - 1] + Yc[c + 1]) + (Yc[c - W2] + Yc[c + W2]) + (Ym[c] + Yp[c]));
+                const long long j = base + p1_phys[r];
+                const float kk = kap[j];
+                const float yp = A[j];
+                const float rhs = 2.f * yc - kk * lap;
+                const int nb = p1_nb[r] + nbz;
+                float out;
+                if (nb == 0) {
+                    out = rhs - yp;
+                } else {
+                    const float beta = (float)nb * sqrtf(kk);
+                    out = (rhs - (1.f - beta) * yp) / (1.f + beta);
+                }
+                const int lx = (c % W2) - 1, ly = (c / W2) - 1;  // position in the L plane
+                Lk[lx + W1 * ly] = out;
+                if (write_c && lx >= 1 && ly >= 1 && lx <= TX && ly <= TY) {
+                    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+                    if (gx <= g.nx && gy <= g.ny) Cout[base + gx + (long long)g.sx * gy] = out;
+                }
+            }
+        }
+        __syncthreads();
+        const int q = k - 1;
+        if (q >= z0 && q < z1) {
+            // y^{n+2} at plane q over the interior
+            const float* Lm = L + ring(mirror(q - 1, g.nz)) * W1 * H1;
+            const float* Lc = L + ring(q) * W1 * H1;
+            const float* Lp = L + ring(mirror(q + 1, g.nz)) * W1 * H1;
+            const float* Yq = Y + ring(q) * W2 * H2;
+            const long long base = (long long)q * sxy;
+            const int nbz = ((q == 0) & zabc0) + ((q == g.nz) & zabc1);
+#pragma unroll
+            for (int r = 0; r < kTbR0; ++r) {
+                if (p0_loc[r] < 0) continue;
+                const int c = p0_l1[r];
+                const float lc = Lc[c];
+                const float lap = 6.f * lc - ((Lc[c - 1] + Lc[c + 1]) + (Lc[c - W1] + Lc[c + W1]) + (Lm[c] + Lp[c]));
+                const long long j = base + p0_phys[r];
+                const float kk = kap[j];
+                const float yp = Yq[p0_loc[r]];
+                const float rhs = 2.f * lc - kk * lap;
+                const int nb = p0_nb[r] + nbz;
+                float out;
+                if (nb == 0) {
+                    out = rhs - yp;
+                } else {
+                    const float beta = (float)nb * sqrtf(kk);
+                    out = (rhs - (1.f - beta) * yp) / (1.f + beta);
+                }
+                Dout[j] = out;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched persistent step loop: one cooperative launch advances the step loops of many solves
+// (uneven grids and step counts) together.  Per step, the blocks stride over the work items of
+// every solve that still has steps left (a work item is one block of the solve's own launch
+// grid: 256 plane nodes x zc planes), then meet at a grid barrier.  Solve i uses buf0 as y^n
+// at its step 0 and the two buffers alternate; adjoint loops use the PREV_SCALED / NO_DIV
+// variants on their first / last step.  Every barrier wait is bounded: on time-out the kernel
+// sets *err and all blocks return.
+constexpr long long kBarrierSpinLimit = 1ll << 24;
+
+__device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, long long spin_limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > spin_limit || *(volatile int*)err) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// The step of one work item (block-sized piece of one solve's grid).
+template <int ORDER, int FLAGS>
+__device__ __forceinline__ void step_item(const float* __restrict__ cur, float* __restrict__ prev,
+                                          const float* __restrict__ kap, const Geom& g, int zc, int bx, int bz) {
+    const long long plane = (long long)g.sx * g.sy;
+    const long long p = (long long)bx * kThreads + threadIdx.x;
+    if (p >= plane) return;
+    const int iy = (int)(p / g.sx);
+    const int ix = (int)(p - (long long)iy * g.sx);
+    const int z0 = bz * zc, z1 = min(z0 + zc, g.sz);
+    Ld<float> f{cur};
+    for (int iz = z0; iz < z1; ++iz) {
+        const long long j = node(g, ix, iy, iz);
+        const float L = lap_t<ORDER, float>(g, f, j, ix, iy, iz);
+        const float k = kap[j];
+        const float yp = prev[j];
+        const float rhs = 2.f * cur[j] - k * L;
+        const int nb = num_abc(g, ix, iy, iz);
+        float out;
+        if (nb == 0) {
+            out = rhs - yp;
+        } else {
+            const float beta = (float)nb * sqrtf(k);
+            const float v = rhs - ((FLAGS & kStepPrevScaled) ? yp : (1.f - beta) * yp);
+            out = (FLAGS & kStepNoDiv) ? v : v / (1.f + beta);
+        }
+        prev[j] = out;
+    }
+}
+
+template <int ORDER>
+__device__ __forceinline__ void step_item_flags(const float* cur, float* prev, const float* kap, const Geom& g, int zc,
+                                                int bx, int bz, int flags) {
+    switch (flags) {
+        case 0: step_item<ORDER, 0>(cur, prev, kap, g, zc, bx, bz); break;
+        case kStepPrevScaled: step_item<ORDER, kStepPrevScaled>(cur, prev, kap, g, zc, bx, bz); break;
+        case kStepNoDiv: step_item<ORDER, kStepNoDiv>(cur, prev, kap, g, zc, bx, bz); break;
+        default: step_item<ORDER, kStepPrevScaled | kStepNoDiv>(cur, prev, kap, g, zc, bx, bz); break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_batch_steps(const BatchItem* __restrict__ items, int nitems,
+                                                          int total_blocks, int max_steps, unsigned* bar, int* err,
+                                                          long long spin_limit) {
+    for (int s = 0; s < max_steps; ++s) {
+        for (int w = blockIdx.x; w < total_blocks; w += gridDim.x) {
+            int lo = 0, hi = nitems - 1;  // last item with offset <= w
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (items[mid].offset <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            const BatchItem& it = items[lo];
+            if (s >= it.nsteps) continue;
+            const int lb = w - it.offset;
+            const int bz = lb / it.blocks_xy, bx = lb - bz * it.blocks_xy;
+            const float* cur = (s & 1) ? it.buf1 : it.buf0;
+            float* prev = (s & 1) ? it.buf0 : it.buf1;
+            int flags = 0;
+            if (it.adjoint) {
+                if (s == 0) flags |= kStepPrevScaled;
+                if (s == it.nsteps - 1) flags |= kStepNoDiv;
+            }
+            if (it.order == 2) step_item_flags<2>(cur, prev, it.kap, it.g, it.zc, bx, bz, flags);
+            else step_item_flags<4>(cur, prev, it.kap, it.g, it.zc, bx, bz, flags);
+        }
+        if (s + 1 < max_steps && !grid_barrier(bar, err, gridDim.x, spin_limit)) return;
+    }
+}
+
+// A barrier that can never complete (one more arrival expected than blocks exist): used only
+// by the self-test of the time-out path.
+__global__ void k_barrier_selftest(unsigned* bar, int* err, long long spin_limit) {
+    grid_barrier(bar, err, gridDim.x + 1, spin_limit);
+}
+
 inline dim3 plane_grid(const Geom& g, int zc) {
     const long long plane = (long long)g.sx * g.sy;
     return dim3((unsigned)((plane + kThreads - 1) / kThreads), (unsigned)((g.sz + zc - 1) / zc), 1);
@@ -496,5 +774,67 @@ long long plane_blocks(const Geom& g, int zc) {
 CMCG_INST(float)
 CMCG_INST(double)
 #undef CMCG_INST
+
+}  // namespace cmcg
+
+namespace cmcg {
+
+int batch_steps_max_blocks() {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_steps, kThreads, 0);
+    return per_sm * sms;
+}
+
+cudaError_t launch_batch_steps(const BatchItem* items, int nitems, int total_blocks, int max_steps, unsigned* bar,
+                               int* err, int grid, cudaStream_t st) {
+    note_launch(1);
+    long long spin = kBarrierSpinLimit;
+    void* args[] = {(void*)&items, (void*)&nitems, (void*)&total_blocks, (void*)&max_steps, (void*)&bar, (void*)&err,
+                    (void*)&spin};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)k_batch_steps, args);
+}
+
+cudaError_t launch_barrier_selftest(unsigned* bar, int* err, long long spin_limit, cudaStream_t st) {
+    note_launch(1);
+    k_barrier_selftest<<<1, kThreads, 0, st>>>(bar, err, spin_limit);
+    return cudaGetLastError();
+}
+
+}  // namespace cmcg
+
+namespace cmcg {
+
+// Tile of the two-step kernel for a grid: interior <= 64 x ty_max (ty_max <= 16), balanced
+// over the grid.
+void tb_tile(const Geom& g, int ty_max, int* TX, int* TY) {
+    const int tx = (g.sx + 63) / 64, ty = (g.sy + ty_max - 1) / ty_max;
+    *TX = (g.sx + tx - 1) / tx;
+    *TY = (g.sy + ty - 1) / ty;
+}
+
+bool step2_supported(const Geom& g, int order) {
+    return g.dim == 3 && order == 2 && g.nx >= 2 && g.ny >= 2 && g.nz >= 2;
+}
+
+void launch_step2(const Geom& g, const float* A, const float* B, const float* kap, float* C, float* D, int zc,
+                  int ty_max, cudaStream_t st) {
+    note_launch(1);
+    int TX, TY;
+    tb_tile(g, ty_max < 1 ? 1 : (ty_max > 16 ? 16 : ty_max), &TX, &TY);
+    const size_t smem = sizeof(float) * (3 * (size_t)(TX + 4) * (TY + 4) + 3 * (size_t)(TX + 2) * (TY + 2));
+    const dim3 grid((unsigned)((g.sx + TX - 1) / TX), (unsigned)((g.sy + TY - 1) / TY), (unsigned)((g.sz + zc - 1) / zc));
+    k_step3d7_x2<<<grid, kTbThreads, smem, st>>>(A, B, kap, C, D, g, TX, TY, zc);
+}
 
 }  // namespace cmcg

@@ -1,0 +1,246 @@
+"""Batched and served Helmholtz solves on the multi-solve engine (cmcg_engine_*).
+
+  python -m paper_1903_12522_gb300.serve batch [--count 64] [--max-n 1024]
+  python -m paper_1903_12522_gb300.serve serve [--requests 40] [--rate 50] [--budget-gb 120]
+
+batch: the uneven 2D batch -- instances seeded 1000+i, n ~ U{96..1024}, 8-20 points per
+  wavelength, smooth random c(x) in [1, 2], one Gaussian source each -- admitted together and
+  stepped by one persistent kernel per period; reports solves/s and grid-point updates/s.
+serve: Poisson arrivals (seeded) of a 70 % 2D (n ~ U{128..512}) / 30 % 3D (n ~ U{64..256})
+  request mix, 10-16 points per wavelength, smooth random c, one random source, tol 1e-6.
+  A request is admitted when its workspace (cmcg_workspace_size) fits the memory budget and a
+  slot is free; solves that arrive while others run join the next tick (continuous batching)
+  and leave when they finish.  Reports p50/p99 latency (arrival to result) and solves/s.
+
+Inputs are synthetic and seeded; the 3D smooth random fields are generated on the GPU (torch
+FFT) because host generation is slower than the arrival rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+if os.path.dirname(HERE) not in sys.path:
+    sys.path.insert(0, os.path.dirname(HERE))
+
+from paper_1903_12522_gb300 import cmcg  # noqa: E402
+from paper_1903_12522_gb300 import workloads as wl  # noqa: E402
+
+
+# ---- request recipe ----------------------------------------------------------------------
+def smooth_field_torch(shape, seed, device, corr_len=0.1, lo=1.0, hi=2.0):
+    """Smooth Gaussian random field on the device: white noise, Gaussian filter, affine map."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    noise = torch.randn(shape, generator=gen, device=device, dtype=torch.float64)
+    n = max(shape) - 1
+    sig = corr_len * n
+    spec = torch.fft.fftn(noise)
+    filt = torch.ones(shape, device=device, dtype=torch.float64)
+    for ax, m in enumerate(shape):
+        fr = torch.fft.fftfreq(m, device=device, dtype=torch.float64)
+        gk = torch.exp(-2.0 * (math.pi * sig * fr) ** 2)
+        sh = [1] * len(shape)
+        sh[ax] = m
+        filt = filt * gk.reshape(sh)
+    field = torch.fft.ifftn(spec * filt).real
+    fmin, fmax = field.min(), field.max()
+    return lo + (hi - lo) * (field - fmin) / (fmax - fmin)
+
+
+def gaussian_source_torch(n, h, center, sigma, device):
+    import torch
+
+    d = len(n)
+    r2 = 0.0
+    for a in range(d):
+        x = torch.arange(n[a] + 1, device=device, dtype=torch.float64) * h
+        sh = [1] * d
+        sh[d - 1 - a] = n[a] + 1
+        r2 = r2 + ((x - center[a]) ** 2).reshape(sh)
+    return torch.exp(-r2 / (2.0 * sigma * sigma)).to(torch.complex128)
+
+
+class Request:
+    def __init__(self, rid, arrival, dim, n, ppw, src, seed):
+        self.rid, self.arrival, self.dim, self.n, self.ppw, self.src, self.seed = rid, arrival, dim, n, ppw, src, seed
+        self.h = 1.0 / n
+        self.omega = 2.0 * math.pi * 1.0 / (ppw * self.h)  # c_min = 1
+        self.dt_target = 0.9 * self.h / (math.sqrt(dim) * 2.0)  # c_max = 2
+        self.admitted = None
+        self.finished = None
+        self.stats = None
+
+    def grid(self):
+        return (self.n,) * self.dim
+
+    def build(self, device):
+        shape = (self.n + 1,) * self.dim
+        c = smooth_field_torch(shape, self.seed, device)
+        f = gaussian_source_torch(self.grid(), self.h, self.src, 0.4 * self.ppw * self.h, device)
+        return c, f
+
+
+def poisson_requests(count, rate, seed=5, two_d=(128, 512), three_d=(64, 256), frac_2d=0.7, ppw=(10.0, 16.0)):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate)
+        dim = 2 if rng.random() < frac_2d else 3
+        lo, hi = two_d if dim == 2 else three_d
+        n = int(rng.integers(lo, hi + 1))
+        p = float(rng.uniform(*ppw))
+        src = tuple(rng.uniform(0.2, 0.8, size=dim))
+        out.append(Request(i, t, dim, n, p, src, seed * 100000 + i))
+    return out
+
+
+# ---- engine driver -------------------------------------------------------------------------
+def make_solver(req, c, precision, stream):
+    faces = (cmcg.BC_ABC,) * 6
+    return cmcg.Solver(req.grid(), req.h, c, req.omega, faces, precision=precision, dt=req.dt_target,
+                       flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream)
+
+
+def workspace_bytes(req, precision):
+    return cmcg.cmcg_workspace_size(cmcg.make_grid(req.grid(), req.h),
+                                    cmcg.make_options(precision, flags=cmcg.FLAG_INEXACT_RIESZ))
+
+
+def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, device="cuda", log=None,
+          keep_results=False, stream=None):
+    """Run the request stream in real time; returns per-request records and totals."""
+    import torch
+
+    eng = cmcg.Engine(max_slots=max_slots, stream=stream)
+    stream = eng.stream
+    queue = list(requests)
+    waiting = []
+    running = {}
+    used = 0
+    done = []
+    t0 = time.perf_counter()
+    updates = 0
+    while queue or waiting or running:
+        now = time.perf_counter() - t0
+        while queue and queue[0].arrival <= now:
+            waiting.append(queue.pop(0))
+        # admission: first fit in arrival order by workspace bytes and free slots
+        for req in list(waiting):
+            if len(running) >= max_slots:
+                break
+            nb = workspace_bytes(req, precision)
+            if used + nb > budget_bytes:
+                continue
+            c, f = req.build(device)
+            s = make_solver(req, c, precision, stream)
+            slot = eng.submit(s, f, None, tol)
+            req.admitted = time.perf_counter() - t0
+            running[slot] = (req, s, nb)
+            used += nb
+            waiting.remove(req)
+        if not running:
+            if queue:
+                time.sleep(max(0.0, min(queue[0].arrival - (time.perf_counter() - t0), 0.05)))
+            continue
+        for slot in eng.tick():
+            req, s, nb = running.pop(slot)
+            u, st = eng.result(slot)
+            req.finished = time.perf_counter() - t0
+            req.stats = st
+            if keep_results:
+                req.result = u.clone()
+            updates += st["point_updates"]
+            used -= nb
+            s.close()
+            done.append(req)
+            if log:
+                log(req)
+    wall = time.perf_counter() - t0
+    info = eng.info()
+    eng.close()
+    lat = np.array([r.finished - r.arrival for r in done])
+    return {
+        "requests": len(done),
+        "wall_s": wall,
+        "solves_per_s": len(done) / wall,
+        "updates_per_s": updates / wall,
+        "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                       "mean": 1e3 * float(lat.mean())},
+        "queue_ms_mean": 1e3 * float(np.mean([r.admitted - r.arrival for r in done])),
+        "status_ok": int(sum(1 for r in done if r.stats["status"] == cmcg.OK)),
+        "ticks": info["ticks"],
+        "graph_builds": info["graph_builds"],
+    }
+
+
+def batch(count=64, max_n=None, precision=cmcg.MIXED, tol=1e-6, device="cuda"):
+    """The uneven 2D batch solved together; returns totals."""
+    import torch
+
+    eng = cmcg.Engine(max_slots=count)
+    stream = eng.stream
+    ws = []
+    for i in range(count):
+        w = wl.random_2d_instance(i)
+        if max_n is not None and w.n[0] > max_n:
+            w = wl.random_2d_instance(i, n=max_n)
+        ws.append(w)
+    solvers = [cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, precision=precision, dt=w.dt_target,
+                           flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream) for w in ws]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, w in zip(solvers, ws):
+        eng.submit(s, w.f, None, tol)
+    res = eng.run_all()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    info = eng.info()
+    eng.close()
+    sts = [st for _, st in res.values()]
+    return {
+        "instances": count,
+        "nodes_total": int(sum(w.num_nodes for w in ws)),
+        "wall_s": wall,
+        "solves_per_s": count / wall,
+        "updates_per_s": sum(st["point_updates"] for st in sts) / wall,
+        "iterations": {"min": min(st["iterations"] for st in sts), "max": max(st["iterations"] for st in sts)},
+        "status_ok": sum(1 for st in sts if st["status"] == cmcg.OK),
+        "ticks": info["ticks"],
+        "graph_builds": info["graph_builds"],
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("mode", choices=["batch", "serve"])
+    ap.add_argument("--count", type=int, default=64)
+    ap.add_argument("--max-n", type=int, default=None)
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
+    ap.add_argument("--max-3d", type=int, default=256)
+    a = ap.parse_args()
+    prec = cmcg.MIXED if a.precision == "mixed" else cmcg.FP32
+    if a.mode == "batch":
+        out = batch(a.count, a.max_n, prec, a.tol)
+    else:
+        reqs = poisson_requests(a.requests, a.rate, three_d=(64, a.max_3d))
+        out = serve(reqs, int(a.budget_gb * 1e9), precision=prec, tol=a.tol)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+"""The multi-solve engine (batched solves, serving): results against the oracle's direct
+solve, a solve alone vs in a mix of other solves (bitwise), graphs vs plain launches,
+admission errors, and the bounded grid-barrier time-out path."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import direct  # noqa: E402
+from oracle.grid import Discretization  # noqa: E402
+from paper_1903_12522_gb300 import cmcg  # noqa: E402
+from paper_1903_12522_gb300 import workloads as wl  # noqa: E402
+
+ABC, NEU = wl.ABC, wl.NEUMANN
+
+
+def small_random(i, n):
+    return wl.random_2d_instance(i, n=n)
+
+
+def odd_2d():
+    n = (37, 29)
+    h = 1.0 / 37
+    rng = np.random.Generator(np.random.PCG64(13))
+    c = 1.0 + rng.random((30, 38))
+    g = (rng.standard_normal((30, 38)) + 1j * rng.standard_normal((30, 38))).astype(np.complex128)
+    return wl.Workload(name="odd2d", n=n, h=h, c=c, omega=11.0, faces=(ABC,) * 4 + (NEU, NEU),
+                       dt_target=0.4 * h / 2.0, mask=wl.sphere_mask(n, h, (0.5, 0.4), 0.12), g=g)
+
+
+def mix():
+    return [wl.gaussian_2d(n=40), odd_2d(), wl.sphere_3d(n=16), small_random(3, 45), small_random(7, 60)]
+
+
+def solver(w, precision, stream):
+    return cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, order=w.order, precision=precision,
+                       dt=w.dt_target, flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream)
+
+
+def wrel(dz, a, b):
+    return math.sqrt(float(np.sum(dz.W * np.abs(a - b) ** 2) / np.sum(dz.W * np.abs(b) ** 2)))
+
+
+STREAM = None
+
+
+def engine_stream():
+    global STREAM
+    if STREAM is None:
+        STREAM = torch.cuda.Stream()
+    return STREAM
+
+
+def run_engine(ws, precision, tol, flags=0):
+    stream = engine_stream()
+    eng = cmcg.Engine(max_slots=len(ws), stream=stream, flags=flags)
+    solvers = [solver(w, precision, stream) for w in ws]
+    slots = [eng.submit(s, w.f, w.g, tol) for s, w in zip(solvers, ws)]
+    res = eng.run_all()
+    out = [res[sl] for sl in slots]
+    info = eng.info()
+    eng.close()
+    return out, info
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(cmcg.MIXED, 1e-9, 1e-6), (cmcg.FP32, 1e-6, 1e-4)])
+def test_batch_matches_direct(precision, tol, bound):
+    ws = mix()
+    out, info = run_engine(ws, precision, tol)
+    assert info["graph_builds"] >= 1 and info["ticks"] >= 1
+    for w, (u, st) in zip(ws, out):
+        assert st["status"] == cmcg.OK, (w.name, st)
+        dz = Discretization(w.n, w.h, w.c, w.omega, w.faces, w.dt_target, order=w.order, mask=w.mask)
+        U = direct.solve(dz, dz.load(w.f, w.g))
+        assert wrel(dz, u.cpu().numpy(), U) <= bound, (w.name, st)
+        assert st["point_updates"] == st["periods"] * dz.N * dz.size
+
+
+@pytest.mark.parametrize("precision", [cmcg.MIXED, cmcg.FP32])
+def test_alone_equals_in_the_mix(precision):
+    ws = mix()
+    tol = 1e-8 if precision == cmcg.MIXED else 1e-6
+    mixed, _ = run_engine(ws, precision, tol)
+    for k in (0, 2):
+        alone, _ = run_engine([ws[k]], precision, tol)
+        assert torch.equal(alone[0][0], mixed[k][0]), ws[k].name
+        assert alone[0][1]["iterations"] == mixed[k][1]["iterations"]
+
+
+def test_graph_and_plain_launches_agree():
+    ws = mix()[:3]
+    a, _ = run_engine(ws, cmcg.MIXED, 1e-8)
+    b, info = run_engine(ws, cmcg.MIXED, 1e-8, flags=cmcg.ENGINE_NO_GRAPH)
+    assert info["graph_builds"] == 0
+    for (ua, _), (ub, _) in zip(a, b):
+        assert torch.equal(ua, ub)
+
+
+def test_admission_errors():
+    stream = engine_stream()
+    eng = cmcg.Engine(max_slots=1, stream=stream)
+    w = wl.gaussian_2d(n=24)
+    s64 = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, precision=cmcg.FP64, dt=w.dt_target, stream=stream)
+    with pytest.raises(cmcg.CMCGError) as e:
+        eng.submit(s64, w.f, None, 1e-6)
+    assert e.value.code == cmcg.ERR_UNSUPPORTED
+    s1 = solver(w, cmcg.FP32, stream)
+    s2 = solver(w, cmcg.FP32, stream)
+    eng.submit(s1, w.f, None, 1e-6)
+    with pytest.raises(cmcg.CMCGError) as e:
+        eng.submit(s1, w.f, None, 1e-6)
+    assert e.value.code == cmcg.ERR_INVALID_ARG
+    with pytest.raises(cmcg.CMCGError) as e:
+        eng.submit(s2, w.f, None, 1e-6)
+    assert e.value.code == cmcg.ERR_WORKSPACE
+    eng.run_all()
+    eng.close()
+
+
+def test_barrier_timeout_is_reported_and_engine_recovers():
+    stream = engine_stream()
+    eng = cmcg.Engine(max_slots=2, stream=stream)
+    assert eng.barrier_selftest(spin_limit=20000) == cmcg.ERR_DEVICE_TIMEOUT
+    w = wl.gaussian_2d(n=24)
+    s = solver(w, cmcg.MIXED, stream)
+    eng.submit(s, w.f, None, 1e-8)
+    res = eng.run_all()
+    (u, st), = res.values()
+    assert st["status"] == cmcg.OK
+    eng.close()
+
+
+def test_serving_loop_results_match_alone():
+    from paper_1903_12522_gb300 import serve
+
+    reqs = serve.poisson_requests(8, rate=400.0, seed=9, two_d=(24, 48), three_d=(10, 16))
+    out = serve.serve(reqs, budget_bytes=int(4e9), max_slots=4, tol=1e-7, keep_results=True, stream=engine_stream())
+    assert out["requests"] == 8 and out["status_ok"] == 8
+    assert out["latency_ms"]["p50"] <= out["latency_ms"]["p99"]
+    # a request solved alone gives the same field as inside the served mix
+    stream = engine_stream()
+    for r in reqs[:3]:
+        c, f = r.build("cuda")
+        eng = cmcg.Engine(max_slots=1, stream=stream)
+        s = serve.make_solver(r, c, cmcg.MIXED, stream)
+        slot = eng.submit(s, f, None, 1e-7)
+        (u, st), = eng.run_all().values()
+        eng.close()
+        assert torch.equal(u.reshape(-1), r.result.reshape(-1)), r.rid
+
+
+def test_default_stream_runs_without_graphs():
+    ws = mix()[:2]
+    stream = torch.cuda.current_stream()
+    eng = cmcg.Engine(max_slots=2, stream=stream)
+    solvers = [solver(w, cmcg.MIXED, stream) for w in ws]
+    for s, w in zip(solvers, ws):
+        eng.submit(s, w.f, w.g, 1e-8)
+    res = eng.run_all()
+    assert eng.info()["graph_builds"] == 0
+    assert all(st["status"] == cmcg.OK for _, st in res.values())
+    eng.close()
