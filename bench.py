@@ -5,10 +5,12 @@ Workload (one "step" = one complete CMCG solve, Steps (1)-(6) of the CMCG Algori
   c(x) = 1 + 0.3 sin(2 pi x) sin(2 pi y) sin(2 pi z), omega = 2 pi * 17.92 (10 points per
   wavelength at c_min = 0.7), sound-soft sphere r = 0.1 at the centre, plane wave
   d = (1/2, 0, sqrt(3)/2) entering through first-order absorbing faces, dt = 0.4 h
-  (N = 36 steps per period), relative CG tolerance 1e-9 (the tolerance at which the solution
-  is within 1e-6 of the plain FP64 GPU solve).  Precision: FP32 leapfrog fields with FP64 CG
-  vectors, inner products and energy functional, inside an FP64 defect-correction loop; the
-  Riesz map is one multigrid V-cycle per iteration in flexible CG.
+  (N = 36 steps per period).  The solve starts from the run-up of Sec. 4.3 (ceil(diam/(T c_min))
+  = 45 periods with ramped sources) and stops at a relative CG residual of 5e-10 with respect to
+  the zero initial guess, the tolerance at which the solution is within 1e-6 of the plain FP64
+  GPU solve.  Precision: FP32 leapfrog fields with FP64 CG vectors, inner products and energy
+  functional, inside an FP64 defect-correction loop; the Riesz map is one multigrid V-cycle per
+  iteration in flexible CG.
 
 Metric: grid-point leapfrog updates per second (forward and adjoint periods), with solves/s,
 the relative error against the plain FP64 GPU solve (tol 1e-10) and per-solve latency.
@@ -40,8 +42,9 @@ if ROOT not in sys.path:
 METRIC = "grid-point updates/s and solves/s at rel err 1e-6 vs plain FP64 GPU; p50/p99 latency"
 UNIT = "grid-point updates/s"
 FALLBACK_HBM_GBS = 6800.0
-STEP_BYTES_FP32 = 16  # read y^n, y^{n-1}, kappa; write y^{n+1} (4 B each)
+STEP_BYTES_FP32 = 16  # one step: read y^n, y^{n-1}, kappa; write y^{n+1} (4 B each)
 STEP_BYTES_FP64 = 32
+PAIR_BYTES_FP32 = 20  # two-step kernel: read y^{n-1}, y^n, kappa; write y^{n+1}, y^{n+2}
 
 
 def parse():
@@ -51,9 +54,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="intervals per axis (default: the full 256^3 workload)")
-    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--tol", type=float, default=5e-10)
     ap.add_argument("--riesz", default="vcycle", choices=["vcycle", "exact"])
     ap.add_argument("--max-iter", type=int, default=0, help="CG iteration cap (profiling runs)")
+    ap.add_argument("--runup", type=int, default=-1, help="run-up periods (Sec. 4.3); -1 = ceil(diam/(T c_min))")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -76,8 +80,14 @@ def workload_config(w, args):
                       "fp32": "fp32 stepping + fp64 CG", "fp64": "fp64"}[args.precision],
         "riesz": {"vcycle": "one FP32 multigrid V-cycle per CG iteration (flexible CG)",
                   "exact": "FP64 MG-PCG to 1e-12"}[args.riesz],
+        "runup_periods": args.runup,
         "l2": "inputs larger than L2 (136 MB per FP64 field > 129 MB)",
     }
+
+
+def tile_config(solver):
+    t = list(solver.opts.tile)
+    return {"tile": t, "step_scheme": "two steps per launch" if t[3] == 2 else "one step per launch"}
 
 
 def aggregate_over_ranks(elapsed, updates, device=None):
@@ -167,10 +177,10 @@ def hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_traffic(kernel_src_hash):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None if the
-    kernel source changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "step3d7_fp32_sphere.json")
+def kernel_traffic(profile, kernel_src_hash):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, or None if the kernel
+    source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(p):
         return None
     try:
@@ -182,10 +192,10 @@ def kernel_traffic(kernel_src_hash):
     return d.get("dram_bytes_per_launch_full_size")
 
 
-def step_kernel_src_hash():
-    """Hash of the 3D 7-point step kernel's source text (the kernel the ncu counters describe)."""
+def kernel_src_hash(name="k_step3d7("):
+    """Hash of a kernel's source text in wave.cu (the kernel that ncu counters describe)."""
     src = open(os.path.join(ROOT, "paper_1903_12522_gb300", "csrc", "wave.cu")).read()
-    start = src.index("k_step3d7(")
+    start = src.index(name)
     end = src.index("// ----", start)
     return hashlib.sha256(src[start:end].encode()).hexdigest()
 
@@ -266,7 +276,7 @@ def run_ours(args):
     g_dev = g_host.to(dev).reshape(-1)
     rflag = cmcg.FLAG_INEXACT_RIESZ if args.riesz == "vcycle" else 0
     s = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, precision=prec, dt=w.dt_target,
-                    flags=cmcg.FLAG_TIMING | rflag, max_iter=args.max_iter, device=dev)
+                    flags=cmcg.FLAG_TIMING | rflag, max_iter=args.max_iter, device=dev, runup_periods=args.runup)
     u = torch.empty(w.num_nodes, dtype=torch.complex128, device=dev)
     stream = s.stream
 
@@ -330,15 +340,25 @@ def run_ours(args):
     n32 = sum(st.step_launches_fp32 for st in stats)
     s64 = sum(st.step_seconds_fp64 for st in stats)
     n64 = sum(st.step_launches_fp64 for st in stats)
-    if n32 > 0:
-        per_launch, bpu, name = s32 / n32, STEP_BYTES_FP32, "leapfrog step 3D 7-point FP32"
+    pairs = s.opts.tile[3] == 2
+    tile_cfg = tile_config(s)
+    if n32 > 0 and pairs:
+        # FP32 3D 7-point periods run their homogeneous steps in pairs (k_step3d7_x2)
+        per_launch, bpl, upl = s32 / n32, PAIR_BYTES_FP32, 2
+        name, prof, src = "k_step3d7_x2: two FP32 leapfrog steps, 3D 7-point", "step3d7x2_fp32_sphere.json", "k_step3d7_x2("
+    elif n32 > 0:
+        per_launch, bpl, upl = s32 / n32, STEP_BYTES_FP32, 1
+        name, prof, src = "k_step3d7<float>: FP32 leapfrog step, 3D 7-point", "step3d7_fp32_sphere.json", "k_step3d7("
     else:
-        per_launch, bpu, name = s64 / max(n64, 1), STEP_BYTES_FP64, "leapfrog step 3D 7-point FP64"
+        per_launch, bpl, upl = s64 / max(n64, 1), STEP_BYTES_FP64, 1
+        name, prof, src = "k_step3d7<double>: FP64 leapfrog step, 3D 7-point", None, "k_step3d7("
     peak, peak_src = hbm_peak()
-    achieved = bpu * w.num_nodes / per_launch / 1e9
-    traffic = kernel_traffic(step_kernel_src_hash()) if n32 > 0 else None
+    achieved = bpl * w.num_nodes / per_launch / 1e9
+    traffic = kernel_traffic(prof, kernel_src_hash(src)) if prof else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": name, "bytes_per_update": bpu,
+                "traffic": traffic, "kernel": name, "algorithmic_bytes_per_node_per_launch": bpl,
+                "updates_per_node_per_launch": upl,
+                "effective_gbs_at_16B_per_update": STEP_BYTES_FP32 * upl * w.num_nodes / per_launch / 1e9,
                 "avg_launch_us": per_launch * 1e6, "peak_source": f"{peak_src} (copy bandwidth)",
                 "step_time_share": (s32 + s64) / elapsed if elapsed > 0 else None}
 
@@ -348,7 +368,7 @@ def run_ours(args):
         s.close()
         del s
         torch.cuda.empty_cache()
-        opts = cmcg.make_options(prec, dt=w.dt_target, flags=cmcg.FLAG_HOST_IO | rflag)
+        opts = cmcg.make_options(prec, dt=w.dt_target, flags=cmcg.FLAG_HOST_IO | rflag, runup_periods=args.runup)
         grid = cmcg.make_grid(w.n, w.h)
         ws_t = torch.empty(cmcg.cmcg_workspace_size(grid, opts), dtype=torch.uint8, device=dev)
         c_dev = torch.empty_like(c_host, device=dev)
@@ -397,12 +417,13 @@ def run_ours(args):
         "metric": METRIC, "value": updates / elapsed, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp32": "f32+f64", "fp64": "f64"}[args.precision],
-        "data": "synthetic", "config": workload_config(w, args),
+        "data": "synthetic", "config": {**workload_config(w, args), **tile_cfg},
         "solves_per_s": ws * args.steps / elapsed,
         "rel_err_vs_fp64_gpu": err,
         "plain_fp64_gpu_reference": ref_info,
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
         "cg_iterations": [st.iterations for st in stats],
+        "runup_periods_done": [st.runup_periods for st in stats],
         "outer_iterations": [st.outer_iterations for st in stats],
         "riesz_iterations": [st.riesz_iterations for st in stats],
         "periods_per_solve": [st.periods for st in stats],

@@ -110,8 +110,11 @@ typedef struct {
     int tile[4];            /* launch shape of the leapfrog kernels, 0 = default: [0] z-planes
                                per thread of the one-step 3D kernel (16), [1] z-planes per block
                                of the two-step kernel (24), [2] maximum interior tile height of
-                               the two-step kernel (16, at most 16), [3] reserved (0).  Chosen
-                               per grid class by the autotuner (paper_1903_12522_gb300/autotune.py). */
+                               the two-step kernel (16, at most 16), [3] step scheme of FP32 3D
+                               7-point homogeneous steps: 0 or 1 = one step per launch, 2 = two
+                               steps per launch (temporal blocking), 3 = one step per launch with
+                               two z-planes per thread iteration.  Chosen per grid class by
+                               the autotuner (paper_1903_12522_gb300/autotune.py). */
 } cmcg_options;
 
 typedef struct {

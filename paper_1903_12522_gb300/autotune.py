@@ -18,7 +18,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 
-CANDIDATES_3D = {"zc1": (8, 16, 32), "zc2": (16, 24, 32, 48), "ty": (8, 12, 16)}
+CANDIDATES_3D = {"zc1": (8, 16, 32), "zc2": (8, 12, 16, 24, 32), "ty": (8, 16), "scheme": (1, 2, 3)}
 
 
 def size_class(dim, n, precision):
@@ -53,8 +53,10 @@ def tune(dim, n, precision, reps=5):
     act = 1.0 - w.mask.astype("float64")
     a, b = [torch.as_tensor(x * act, device="cuda").reshape(-1) for x in wl.random_fields(w.shape, 2, 17)]
     results = []
-    for zc1, zc2, ty in itertools.product(*CANDIDATES_3D.values()):
-        tile = (zc1, zc2, ty, 0)
+    for zc1, zc2, ty, scheme in itertools.product(*CANDIDATES_3D.values()):
+        if scheme != 2 and (zc2, ty) != (CANDIDATES_3D["zc2"][0], CANDIDATES_3D["ty"][0]):
+            continue  # the two-step knobs do not matter for one-step launches
+        tile = (zc1, zc2, ty, scheme)
         s = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, precision=precision, dt=w.dt_target, tile=tile)
         s.adjoint_period(a, b)  # warm-up
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -86,7 +88,8 @@ def main():
     prec = {"fp32": cmcg.FP32, "mixed": cmcg.MIXED, "fp64": cmcg.FP64}[a.precision]
     for n in a.n:
         best, ms, res = tune(a.dim, n, prec)
-        print(json.dumps({"class": size_class(a.dim, n, prec), "tile": best, "ms": ms, "worst_ms": res[-1][0]}))
+        print(json.dumps({"class": size_class(a.dim, n, prec), "tile": best, "ms": ms, "worst_ms": res[-1][0],
+                          "all": [[round(t, 4), list(c)] for t, c in res]}))
 
 
 if __name__ == "__main__":

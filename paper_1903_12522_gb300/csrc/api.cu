@@ -212,17 +212,19 @@ PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool
     return b;
 }
 
-// z-planes per thread of the one-step kernels
+// z-planes per thread of the one-step kernels; negative selects the variant that processes two
+// planes per loop iteration (tile[3] == 3)
 int step_zc(const cmcg_handle* H) {
     if (H->g.dim != 3) return 1;
-    return H->opt.tile[0] > 0 ? H->opt.tile[0] : kZcStep3D;
+    const int zc = H->opt.tile[0] > 0 ? H->opt.tile[0] : kZcStep3D;
+    return (H->opt.tile[3] == 3 && H->order == 2) ? -zc : zc;
 }
 
 // FP32 3D 7-point homogeneous steps run in pairs through the two-step kernel, whose outputs go
 // to the spare halves of the (double-sized) wave buffers.
 template <typename T>
 bool use_pairs(const cmcg_handle* H, bool src) {
-    return std::is_same<T, float>::value && !src && step2_supported(H->g, H->order);
+    return H->opt.tile[3] == 2 && std::is_same<T, float>::value && !src && step2_supported(H->g, H->order);
 }
 
 // `count` homogeneous steps from b (in pairs where possible, else one by one).
@@ -982,7 +984,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     if (H->has_dir && H->sumW <= 0) return fail(CMCG_ERR_INVALID_ARG);
     if (o.runup_periods < -1 || o.runup_periods > 100000) return fail(CMCG_ERR_INVALID_ARG);
     if (o.tile[0] < 0 || o.tile[0] > 512 || o.tile[1] < 0 || o.tile[1] > 512 || o.tile[2] < 0 || o.tile[2] > 16 ||
-        o.tile[3] != 0)
+        o.tile[3] < 0 || o.tile[3] > 3)
         return fail(CMCG_ERR_INVALID_ARG);
     // time step: N = ceil(T / dt_target - 1e-9), dt = T / N
     const double dt_target = o.dt > 0 ? o.dt : 0.5 * grid->h / (sqrt((double)grid->dim) * cmax);

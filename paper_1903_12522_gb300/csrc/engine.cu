@@ -57,10 +57,16 @@ struct cmcg_engine {
     bool use_graph = true;
     // graph cache
     cudaGraphExec_t exec = nullptr;
-    std::vector<long long> signature;
+    std::vector<long long> signature;       // configuration of the cached graph
+    std::vector<long long> last_signature;  // configuration of the previous tick
     long long graph_launches = 0;
     long long ticks = 0, graph_builds = 0;
     cudaError_t last_error = cudaSuccess;  // the CUDA error behind the last CMCG_ERR_CUDA
+    // side streams: per-solve kernels of different solves run concurrently between the batched
+    // launches (fork/join by events; under capture these become parallel graph branches)
+    static constexpr int kSide = 8;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
 };
 
 namespace {
@@ -115,26 +121,53 @@ void reset_direction(cmcg_handle* h) {
     cudaMemcpyAsync(h->d1, h->r1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
 }
 
+void fork_sides(cmcg_engine* e) {
+    cudaEventRecord(e->fork, e->st);
+    for (int k = 0; k < cmcg_engine::kSide; ++k) cudaStreamWaitEvent(e->side[k], e->fork, 0);
+}
+
+void join_sides(cmcg_engine* e) {
+    for (int k = 0; k < cmcg_engine::kSide; ++k) {
+        cudaEventRecord(e->join[k], e->side[k]);
+        cudaStreamWaitEvent(e->st, e->join[k], 0);
+    }
+}
+
+// Run f(h) with the handle's launches on side stream k (the handle's own stream is restored).
+template <typename F>
+void on_side(cmcg_engine* e, cmcg_handle* h, int k, F f) {
+    cudaStream_t own = h->st;
+    h->st = e->side[k % cmcg_engine::kSide];
+    f(h);
+    h->st = own;
+}
+
 // Enqueue one tick on the engine's stream (also used while capturing).
 cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
     cudaMemsetAsync(e->err, 0, sizeof(int), e->st);
+    fork_sides(e);
     std::vector<int> inner;
+    int lane = 0;
     for (int s : act) {
         EngineSlot& sl = e->slots[s];
-        cmcg_handle* h = sl.h;
-        const long long n = h->g.np;
         if (sl.unit == U_OUTER) {
-            launch_axpy(n, 1.0, h->w0, h->wo0, h->st);
-            launch_axpy(n, 1.0, h->w1, h->wo1, h->st);
-            gradient<double>(h, h->wo0, h->wo1, true, h->wo0, h->wo1, false);
-            launch_fill(h->w0, n, 0.0, h->st);
-            launch_fill(h->w1, n, 0.0, h->st);
-            reset_direction(h);
+            on_side(e, sl.h, lane++, [](cmcg_handle* h) {
+                const long long n = h->g.np;
+                launch_axpy(n, 1.0, h->w0, h->wo0, h->st);
+                launch_axpy(n, 1.0, h->w1, h->wo1, h->st);
+                gradient<double>(h, h->wo0, h->wo1, true, h->wo0, h->wo1, false);
+                launch_fill(h->w0, n, 0.0, h->st);
+                launch_fill(h->w1, n, 0.0, h->st);
+                reset_direction(h);
+            });
         } else if (sl.unit == U_INIT32) {
-            launch_fill(h->w0, n, 0.0, h->st);
-            launch_fill(h->w1, n, 0.0, h->st);
-            gradient<float>(h, h->w0, h->w1, true, h->w0, h->w1, false);
-            reset_direction(h);
+            on_side(e, sl.h, lane++, [](cmcg_handle* h) {
+                const long long n = h->g.np;
+                launch_fill(h->w0, n, 0.0, h->st);
+                launch_fill(h->w1, n, 0.0, h->st);
+                gradient<float>(h, h->w0, h->w1, true, h->w0, h->w1, false);
+                reset_direction(h);
+            });
         } else if (sl.unit == U_INNER) {
             inner.push_back(s);
         }
@@ -147,36 +180,47 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
         std::vector<BatchItem> items(2 * (size_t)m);
         for (int i = 0; i < m; ++i) {
             cmcg_handle* h = e->slots[inner[i]].h;
-            fb[i] = fwd_begin<float>(h, h->d0, h->d1, false);
+            on_side(e, h, lane + i, [&](cmcg_handle* hh) { fb[i] = fwd_begin<float>(hh, hh->d0, hh->d1, false); });
             items[i] = make_item(h, fb[i], false);
             items[i].offset = total;
             total += items[i].blocks;
             maxs = std::max(maxs, items[i].nsteps);
         }
+        join_sides(e);  // the cooperative kernel runs alone: all its blocks are co-resident
         cudaError_t ce = launch_batch_steps(e->items_dev, m, total, maxs, e->bar, e->err, e->grid, e->st);
         if (ce != cudaSuccess) return ce;
+        fork_sides(e);
         int total_a = 0, maxa = 0;
         for (int i = 0; i < m; ++i) {
             cmcg_handle* h = e->slots[inner[i]].h;
-            fwd_end<float>(h, after_steps(fb[i], h->N - 1), h->d1, false, 0, h->z0, h->z1);
-            ab[i] = adj_begin<float>(h, h->z0, h->z1);
+            on_side(e, h, lane + i, [&](cmcg_handle* hh) {
+                fwd_end<float>(hh, after_steps(fb[i], hh->N - 1), hh->d1, false, 0, hh->z0, hh->z1);
+                ab[i] = adj_begin<float>(hh, hh->z0, hh->z1);
+            });
             items[m + i] = make_item(h, ab[i], true);
             items[m + i].offset = total_a;
             total_a += items[m + i].blocks;
             maxa = std::max(maxa, items[m + i].nsteps);
         }
+        join_sides(e);
         ce = launch_batch_steps(e->items_dev + e->max_slots, m, total_a, maxa, e->bar, e->err, e->grid, e->st);
         if (ce != cudaSuccess) return ce;
+        fork_sides(e);
         for (int i = 0; i < m; ++i) {
             cmcg_handle* h = e->slots[inner[i]].h;
-            const long long n = h->g.np;
-            adj_end<float>(h, after_steps(ab[i], h->N - 1), h->z0, h->z1, 0, h->d0, h->d1, h->gh0, h->gh1, h->gt1);
-            launch_fcg_update(n, h->w0, h->w1, h->rh0, h->rh1, h->d0, h->d1, h->gh0, h->gh1, h->red(), h->st);
-            apply_B(h, false);
-            launch_cg_direction(n, h->r0, h->r1, h->d0, h->d1, h->red(), h->st);
+            on_side(e, h, lane + i, [&](cmcg_handle* hh) {
+                const long long n = hh->g.np;
+                adj_end<float>(hh, after_steps(ab[i], hh->N - 1), hh->z0, hh->z1, 0, hh->d0, hh->d1, hh->gh0, hh->gh1,
+                               hh->gt1);
+                launch_fcg_update(n, hh->w0, hh->w1, hh->rh0, hh->rh1, hh->d0, hh->d1, hh->gh0, hh->gh1, hh->red(),
+                                  hh->st);
+                apply_B(hh, false);
+                launch_cg_direction(n, hh->r0, hh->r1, hh->d0, hh->d1, hh->red(), hh->st);
+            });
         }
         // the descriptors are uploaded before the tick (upload_items)
     }
+    join_sides(e);
     for (int s : act) {
         cmcg_handle* h = e->slots[s].h;
         cudaMemcpyAsync(h->hsc, h->sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, e->st);
@@ -263,7 +307,17 @@ int cmcg_engine_create(int max_slots, void* workspace, size_t ws_bytes, void* st
     cudaMemsetAsync(e->bar, 0, sizeof(unsigned) * 4, e->st);
     cudaMemsetAsync(e->err, 0, sizeof(int) * 4, e->st);
     e->grid = batch_steps_max_blocks();
-    if (cudaStreamSynchronize(e->st) != cudaSuccess || e->grid <= 0) {
+    bool ok = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < cmcg_engine::kSide; ++k) {
+        ok = ok && cudaStreamCreateWithFlags(&e->side[k], cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&e->join[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok || cudaStreamSynchronize(e->st) != cudaSuccess || e->grid <= 0) {
+        for (int k = 0; k < cmcg_engine::kSide; ++k) {
+            if (e->side[k]) cudaStreamDestroy(e->side[k]);
+            if (e->join[k]) cudaEventDestroy(e->join[k]);
+        }
+        if (e->fork) cudaEventDestroy(e->fork);
         cudaFreeHost(e->err_host);
         delete e;
         return CMCG_ERR_CUDA;
@@ -275,6 +329,13 @@ int cmcg_engine_create(int max_slots, void* workspace, size_t ws_bytes, void* st
 int cmcg_engine_destroy(cmcg_engine* e) {
     if (!e) return CMCG_ERR_INVALID_ARG;
     if (e->exec) cudaGraphExecDestroy(e->exec);
+    cudaStreamSynchronize(e->st);
+    for (int k = 0; k < cmcg_engine::kSide; ++k) {
+        cudaStreamSynchronize(e->side[k]);
+        cudaStreamDestroy(e->side[k]);
+        cudaEventDestroy(e->join[k]);
+    }
+    cudaEventDestroy(e->fork);
     cudaFreeHost(e->err_host);
     delete e;
     return CMCG_OK;
@@ -332,9 +393,14 @@ int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_fin
         sig.push_back(e->slots[s].unit);
         sig.push_back((long long)(uintptr_t)e->slots[s].h);
     }
+    // the batch descriptors follow the configuration of every tick (a cached graph reads them)
+    const bool changed = sig != e->last_signature;
+    if (changed) upload_items(e, act);
+    e->last_signature = sig;
     const bool same = e->exec != nullptr && sig == e->signature;
-    if (!same) upload_items(e, act);
-    if (e->use_graph) {
+    // capture a configuration only once it has held for two ticks: a solve that changes unit
+    // every few ticks would otherwise pay a graph build each time
+    if (e->use_graph && (same || !changed)) {
         if (!same) {
             if (e->exec) {
                 cudaGraphExecDestroy(e->exec);

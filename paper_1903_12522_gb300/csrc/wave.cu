@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const T yz = cur[j + (iz < g.nz ? sZ : -sZ)];
         const T L = T(6) * yc - ((cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]) + (ym + yz));
-        const T k = kap[j];
+        const T k = __ldcs(kap + j);  // streamed: keep L2 for the two wave fields reused next step
         const T yp = prev_out[j];
         T rhs = T(2) * yc - k * L;
         if (FLAGS & kStepSrc) rhs += (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
@@ -130,6 +130,115 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
         ym = yc;
         yc = yz;
         j += sZ;
+    }
+}
+
+// Leapfrog step, 3D 2nd order, two z-planes per loop iteration: both planes' loads are
+// issued before either update (more loads in flight per thread).
+template <typename T, int FLAGS>
+__global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ cur, T* __restrict__ prev_out,
+                                                         const T* __restrict__ kap, const double* __restrict__ S,
+                                                         double cs, double sn, Geom g, int zc) {
+    const PlaneMap m = plane_map(g, zc);
+    if (!m.valid || m.z0 >= m.z1) return;
+    const long long sZ = (long long)g.sx * g.sy;
+    long long j = node(g, m.ix, m.iy, m.z0);
+    const long long oxm = off_m1(m.ix, 1), oxp = off_p1(m.ix, g.nx, 1);
+    const long long oym = off_m1(m.iy, g.sx), oyp = off_p1(m.iy, g.ny, g.sx);
+    int nbxy = 0;
+    nbxy += (m.ix == 0) & (int)(g.abc & 1u);
+    nbxy += (m.ix == g.nx) & (int)((g.abc >> 1) & 1u);
+    nbxy += (m.iy == 0) & (int)((g.abc >> 2) & 1u);
+    nbxy += (m.iy == g.ny) & (int)((g.abc >> 3) & 1u);
+    auto update = [&](T yc, T ym, T yz, long long jj, int iz, T sxy, T k, T yp) {
+        const T L = T(6) * yc - (sxy + (ym + yz));
+        T rhs = T(2) * yc - k * L;
+        if (FLAGS & kStepSrc) rhs += (T)(S[2 * jj] * cs + S[2 * jj + 1] * sn);
+        const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
+        T out;
+        if (nb == 0) {
+            out = rhs - yp;
+        } else {
+            const T beta = (T)nb * sqrt(k);
+            const T v = rhs - ((FLAGS & kStepPrevScaled) ? yp : (T(1) - beta) * yp);
+            out = (FLAGS & kStepNoDiv) ? v : v / (T(1) + beta);
+        }
+        prev_out[jj] = out;
+    };
+    T ym = cur[j + (m.z0 > 0 ? -sZ : sZ)];
+    T yc = cur[j];
+    int iz = m.z0;
+    for (; iz + 1 < m.z1; iz += 2) {
+        const long long j1 = j + sZ;
+        const T y1 = cur[j1];                                    // plane iz+1 (exists: iz+1 < z1 <= sz)
+        const T y2 = cur[j1 + (iz + 1 < g.nz ? sZ : -sZ)];       // plane iz+2 (mirrored at the top)
+        const T s0 = (cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]);
+        const T s1 = (cur[j1 + oxm] + cur[j1 + oxp]) + (cur[j1 + oym] + cur[j1 + oyp]);
+        const T k0 = __ldcs(kap + j), k1 = __ldcs(kap + j1);
+        const T p0 = prev_out[j], p1 = prev_out[j1];
+        update(yc, ym, y1, j, iz, s0, k0, p0);
+        update(y1, yc, y2, j1, iz + 1, s1, k1, p1);
+        ym = y1;
+        yc = y2;
+        j += 2 * sZ;
+    }
+    if (iz < m.z1) {
+        const T yz = cur[j + (iz < g.nz ? sZ : -sZ)];
+        const T s0 = (cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]);
+        update(yc, ym, yz, j, iz, s0, __ldcs(kap + j), prev_out[j]);
+    }
+}
+
+// Leapfrog step, 3D 4th order (13-point): the five z-planes z-2..z+2 carried in registers
+// (even reflection at the faces), x/y neighbours at distance 1 and 2 loaded.
+__device__ __forceinline__ int refl(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
+
+template <typename T, int FLAGS>
+__global__ void __launch_bounds__(kThreads) k_step3d13(const T* __restrict__ cur, T* __restrict__ prev_out,
+                                                       const T* __restrict__ kap, const double* __restrict__ S,
+                                                       double cs, double sn, Geom g, int zc) {
+    const PlaneMap m = plane_map(g, zc);
+    if (!m.valid || m.z0 >= m.z1) return;
+    const long long sZ = (long long)g.sx * g.sy;
+    const long long col = (long long)m.ix + (long long)g.sx * m.iy;
+    const long long ox1m = off_m1(m.ix, 1), ox1p = off_p1(m.ix, g.nx, 1);
+    const long long ox2m = off_m2(m.ix, 1), ox2p = off_p2(m.ix, g.nx, 1);
+    const long long oy1m = off_m1(m.iy, g.sx), oy1p = off_p1(m.iy, g.ny, g.sx);
+    const long long oy2m = off_m2(m.iy, g.sx), oy2p = off_p2(m.iy, g.ny, g.sx);
+    int nbxy = 0;
+    nbxy += (m.ix == 0) & (int)(g.abc & 1u);
+    nbxy += (m.ix == g.nx) & (int)((g.abc >> 1) & 1u);
+    nbxy += (m.iy == 0) & (int)((g.abc >> 2) & 1u);
+    nbxy += (m.iy == g.ny) & (int)((g.abc >> 3) & 1u);
+    T zm2 = cur[col + refl(m.z0 - 2, g.nz) * sZ];
+    T zm1 = cur[col + refl(m.z0 - 1, g.nz) * sZ];
+    T zc0 = cur[col + (long long)m.z0 * sZ];
+    T zp1 = cur[col + refl(m.z0 + 1, g.nz) * sZ];
+    const T c1 = T(4) / T(3), c2 = T(1) / T(12);
+    for (int iz = m.z0; iz < m.z1; ++iz) {
+        const long long j = col + (long long)iz * sZ;
+        const T zp2 = cur[col + refl(iz + 2, g.nz) * sZ];
+        const T a1 = (cur[j + ox1m] + cur[j + ox1p]) + (cur[j + oy1m] + cur[j + oy1p]) + (zm1 + zp1);
+        const T a2 = (cur[j + ox2m] + cur[j + ox2p]) + (cur[j + oy2m] + cur[j + oy2p]) + (zm2 + zp2);
+        const T L = T(7.5) * zc0 - c1 * a1 + c2 * a2;
+        const T k = kap[j];
+        const T yp = prev_out[j];
+        T rhs = T(2) * zc0 - k * L;
+        if (FLAGS & kStepSrc) rhs += (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
+        const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
+        T out;
+        if (nb == 0) {
+            out = rhs - yp;
+        } else {
+            const T beta = (T)nb * sqrt(k);
+            const T v = rhs - ((FLAGS & kStepPrevScaled) ? yp : (T(1) - beta) * yp);
+            out = (FLAGS & kStepNoDiv) ? v : v / (T(1) + beta);
+        }
+        prev_out[j] = out;
+        zm2 = zm1;
+        zm1 = zc0;
+        zc0 = zp1;
+        zp1 = zp2;
     }
 }
 
@@ -359,160 +468,145 @@ __global__ void __launch_bounds__(kThreads) k_make_source(const double* __restri
 
 // ---------------------------------------------------------------------------------------
 // Two leapfrog steps per sweep (temporal blocking), 3D 7-point, FP32, homogeneous steps.
-// A block owns an interior tile TX x TY of every plane in its z-chunk and marches z.  It keeps
-// in shared memory a 3-plane ring of y^n over the tile plus a 2-node halo (mirror-filled at
-// the faces) and a 3-plane ring of y^{n+1} over the tile plus a 1-node halo (computed
-// redundantly at the halo, with the mirrored node's coefficients, so that it equals the
-// mirror value there).  Per plane k: load y^n(k+1); y^{n+1}(k) on the 1-halo region;
-// y^{n+2}(k-1) on the interior.  y^{n-1}, kappa are read at the points they are needed.
-// Outputs go to two other buffers (y^{n+1} -> C, y^{n+2} -> D): other blocks still read the
-// inputs' halos.  Each output equals two applications of the one-step update.
+// A block owns an interior tile TX x TY of every plane in its z-chunk and marches z.  Shared
+// memory holds 4-plane rings of y^n over the tile plus a 2-node halo (mirror-filled at the
+// faces) and of y^{n+1} over the tile plus a 1-node halo (computed redundantly at the halo, with
+// the mirrored node's coefficients, so that it equals the mirror value there).  Iteration k:
+//   phase A: load y^n(k+1);  y^{n+2}(k-2) on the interior (from y^{n+1}(k-3..k-1), y^n(k-2))
+//   phase B: y^{n+1}(k) on the 1-halo region (from y^n(k-1..k+1), y^{n-1}(k))
+// with one block barrier after each phase.  y^{n-1} and kappa are read where needed.  Outputs
+// go to two other buffers (y^{n+1} -> C, y^{n+2} -> D): other blocks still read the inputs'
+// halos.  Each output equals two applications of the one-step update.
 constexpr int kTbThreads = 256;
-constexpr int kTbMaxW = 68, kTbMaxH = 20;                       // interior tile <= 64 x 16
-constexpr int kTbR2 = (kTbMaxW * kTbMaxH + kTbThreads - 1) / kTbThreads;                  // points per thread
+constexpr int kTbMaxW = 68, kTbMaxH = 20;  // interior tile <= 64 x 16
+constexpr int kTbR2 = (kTbMaxW * kTbMaxH + kTbThreads - 1) / kTbThreads;
 constexpr int kTbR1 = ((kTbMaxW - 2) * (kTbMaxH - 2) + kTbThreads - 1) / kTbThreads;
 constexpr int kTbR0 = ((kTbMaxW - 4) * (kTbMaxH - 4) + kTbThreads - 1) / kTbThreads;
 
 __device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
-__device__ __forceinline__ int ring(int p) { return ((p % 3) + 3) % 3; }
+__device__ __forceinline__ int ring4(int p) { return p & 3; }  // two's complement: also for p < 0
+
+__device__ __forceinline__ int nb_xy(const Geom& g, int px, int py) {
+    return ((px == 0) & (int)(g.abc & 1u)) + ((px == g.nx) & (int)((g.abc >> 1) & 1u)) +
+           ((py == 0) & (int)((g.abc >> 2) & 1u)) + ((py == g.ny) & (int)((g.abc >> 3) & 1u));
+}
+
+__device__ __forceinline__ float lf_update(float yc, float lap, float kk, float yp, int nb) {
+    const float rhs = 2.f * yc - kk * lap;
+    if (nb == 0) return rhs - yp;
+    const float beta = (float)nb * sqrtf(kk);
+    return (rhs - (1.f - beta) * yp) / (1.f + beta);
+}
 
 __global__ void __launch_bounds__(kTbThreads) k_step3d7_x2(const float* __restrict__ A, const float* __restrict__ B,
                                                            const float* __restrict__ kap, float* __restrict__ Cout,
                                                            float* __restrict__ Dout, Geom g, int TX, int TY, int zc) {
     extern __shared__ float sm[];
     const int W2 = TX + 4, H2 = TY + 4, W1 = TX + 2, H1 = TY + 2;
-    float* Y = sm;                  // 3 x W2 x H2
-    float* L = sm + 3 * W2 * H2;    // 3 x W1 x H1
+    const int P2 = W2 * H2, P1 = W1 * H1;
+    float* Y = sm;           // 4 x P2
+    float* L = sm + 4 * P2;  // 4 x P1
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.sz);
     const long long sxy = (long long)g.sx * g.sy;
     const int tid = threadIdx.x;
-    // per-thread point lists (same every plane)
-    int p2_off[kTbR2], p2_phys[kTbR2];
-    int p1_loc[kTbR1], p1_phys[kTbR1], p1_nb[kTbR1];
-    int p0_loc[kTbR0], p0_phys[kTbR0], p0_nb[kTbR0], p0_l1[kTbR0];
+    // per-thread point lists, the same every plane
+    int ph2[kTbR2];                   // R2 (loads): physical (x, y) offset, -1 = none
+    int pk1[kTbR1], ph1[kTbR1];       // R1: Y position | nb << 16 | interior << 19; physical offset
+    int pk0[kTbR0], ph0[kTbR0];       // R0: L position | Y position << 11 | nb << 22; physical offset
 #pragma unroll
     for (int r = 0; r < kTbR2; ++r) {
         const int i = tid + r * kTbThreads;
-        p2_off[r] = -1;
-        if (i < W2 * H2) {
-            const int lx = i % W2, ly = i / W2;
+        ph2[r] = -1;
+        if (i < P2) {
+            const int ly = i / W2, lx = i - ly * W2;
             const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
-            if (gx <= g.nx + 2 && gy <= g.ny + 2) {
-                p2_off[r] = i;
-                p2_phys[r] = mirror(gx, g.nx) + g.sx * mirror(gy, g.ny);
-            }
+            if (gx <= g.nx + 2 && gy <= g.ny + 2) ph2[r] = mirror(gx, g.nx) + g.sx * mirror(gy, g.ny);
         }
     }
 #pragma unroll
     for (int r = 0; r < kTbR1; ++r) {
         const int i = tid + r * kTbThreads;
-        p1_loc[r] = -1;
-        if (i < W1 * H1) {
-            const int lx = i % W1, ly = i / W1;
+        pk1[r] = -1;
+        if (i < P1) {
+            const int ly = i / W1, lx = i - ly * W1;
             const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
             if (gx <= g.nx + 1 && gy <= g.ny + 1) {
                 const int px = mirror(gx, g.nx), py = mirror(gy, g.ny);
-                p1_loc[r] = (lx + 1) + W2 * (ly + 1);  // position in the Y plane
-                p1_phys[r] = px + g.sx * py;
-                p1_nb[r] = ((px == 0) & (int)(g.abc & 1u)) + ((px == g.nx) & (int)((g.abc >> 1) & 1u)) +
-                           ((py == 0) & (int)((g.abc >> 2) & 1u)) + ((py == g.ny) & (int)((g.abc >> 3) & 1u));
+                const int inner = (lx >= 1 && ly >= 1 && lx <= TX && ly <= TY && gx <= g.nx && gy <= g.ny) ? 1 : 0;
+                pk1[r] = ((lx + 1) + W2 * (ly + 1)) | (nb_xy(g, px, py) << 16) | (inner << 19);
+                ph1[r] = px + g.sx * py;
             }
         }
     }
 #pragma unroll
     for (int r = 0; r < kTbR0; ++r) {
         const int i = tid + r * kTbThreads;
-        p0_loc[r] = -1;
+        pk0[r] = -1;
         if (i < TX * TY) {
-            const int lx = i % TX, ly = i / TX;
+            const int ly = i / TX, lx = i - ly * TX;
             const int gx = x0 + lx, gy = y0 + ly;
             if (gx <= g.nx && gy <= g.ny) {
-                p0_loc[r] = (lx + 2) + W2 * (ly + 2);
-                p0_l1[r] = (lx + 1) + W1 * (ly + 1);
-                p0_phys[r] = gx + g.sx * gy;
-                p0_nb[r] = ((gx == 0) & (int)(g.abc & 1u)) + ((gx == g.nx) & (int)((g.abc >> 1) & 1u)) +
-                           ((gy == 0) & (int)((g.abc >> 2) & 1u)) + ((gy == g.ny) & (int)((g.abc >> 3) & 1u));
+                pk0[r] = ((lx + 1) + W1 * (ly + 1)) | (((lx + 2) + W2 * (ly + 2)) << 11) | (nb_xy(g, gx, gy) << 22);
+                ph0[r] = gx + g.sx * gy;
             }
         }
     }
     const int zabc0 = (int)((g.abc >> 4) & 1u), zabc1 = (int)((g.abc >> 5) & 1u);
-    auto load_plane = [&](int p) {  // y^n at virtual plane p into the ring
-        float* dst = Y + ring(p) * W2 * H2;
+    auto load_plane = [&](int p) {  // y^n at virtual plane p (mirrored) into the ring
+        float* dst = Y + ring4(p) * P2;
         const long long base = (long long)mirror(p, g.nz) * sxy;
 #pragma unroll
-        for (int r = 0; r < kTbR2; ++r)
-            if (p2_off[r] >= 0) dst[p2_off[r]] = B[base + p2_phys[r]];
+        for (int r = 0; r < kTbR2; ++r) {
+            const int i = tid + r * kTbThreads;
+            if (ph2[r] >= 0) dst[i] = B[base + ph2[r]];
+        }
     };
     load_plane(z0 - 2);
     load_plane(z0 - 1);
-    for (int k = z0 - 1; k <= z1; ++k) {
-        load_plane(k + 1);
+    for (int k = z0 - 1; k <= z1 + 1; ++k) {
+        // phase A: next y^n plane; y^{n+2} two planes behind
+        if (k <= g.nz) load_plane(k + 1);
+        const int q = k - 2;
+        if (q >= z0 && q < z1) {
+            const float* Lm = L + ring4(mirror(q - 1, g.nz)) * P1;
+            const float* Lc = L + ring4(q) * P1;
+            const float* Lp = L + ring4(mirror(q + 1, g.nz)) * P1;
+            const float* Yq = Y + ring4(q) * P2;
+            const long long base = (long long)q * sxy;
+            const int nbz = ((q == 0) & zabc0) + ((q == g.nz) & zabc1);
+#pragma unroll
+            for (int r = 0; r < kTbR0; ++r) {
+                const int pk = pk0[r];
+                if (pk < 0) continue;
+                const int c = pk & 2047, cy = (pk >> 11) & 2047, nb = (pk >> 22) + nbz;
+                const float lc = Lc[c];
+                const float lap = 6.f * lc - ((Lc[c - 1] + Lc[c + 1]) + (Lc[c - W1] + Lc[c + W1]) + (Lm[c] + Lp[c]));
+                const long long j = base + ph0[r];
+                Dout[j] = lf_update(lc, lap, kap[j], Yq[cy], nb);
+            }
+        }
         __syncthreads();
+        // phase B: y^{n+1} at plane k on the 1-halo region
         if (k >= 0 && k <= g.nz) {
-            // y^{n+1} at plane k over the 1-halo region
-            const float* Ym = Y + ring(k - 1) * W2 * H2;
-            const float* Yc = Y + ring(k) * W2 * H2;
-            const float* Yp = Y + ring(k + 1) * W2 * H2;
-            float* Lk = L + ring(k) * W1 * H1;
+            const float* Ym = Y + ring4(k - 1) * P2;
+            const float* Yc = Y + ring4(k) * P2;
+            const float* Yp = Y + ring4(k + 1) * P2;
+            float* Lk = L + ring4(k) * P1;
             const long long base = (long long)k * sxy;
             const int nbz = ((k == 0) & zabc0) + ((k == g.nz) & zabc1);
             const bool write_c = k >= z0 && k < z1;
 #pragma unroll
             for (int r = 0; r < kTbR1; ++r) {
-                const int c = p1_loc[r];
-                if (c < 0) continue;
+                const int pk = pk1[r];
+                if (pk < 0) continue;
+                const int c = pk & 65535, nb = ((pk >> 16) & 7) + nbz;
                 const float yc = Yc[c];
                 const float lap = 6.f * yc - ((Yc[c - 1] + Yc[c + 1]) + (Yc[c - W2] + Yc[c + W2]) + (Ym[c] + Yp[c]));
-                const long long j = base + p1_phys[r];
-                const float kk = kap[j];
-                const float yp = A[j];
-                const float rhs = 2.f * yc - kk * lap;
-                const int nb = p1_nb[r] + nbz;
-                float out;
-                if (nb == 0) {
-                    out = rhs - yp;
-                } else {
-                    const float beta = (float)nb * sqrtf(kk);
-                    out = (rhs - (1.f - beta) * yp) / (1.f + beta);
-                }
-                const int lx = (c % W2) - 1, ly = (c / W2) - 1;  // position in the L plane
-                Lk[lx + W1 * ly] = out;
-                if (write_c && lx >= 1 && ly >= 1 && lx <= TX && ly <= TY) {
-                    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-                    if (gx <= g.nx && gy <= g.ny) Cout[base + gx + (long long)g.sx * gy] = out;
-                }
-            }
-        }
-        __syncthreads();
-        const int q = k - 1;
-        if (q >= z0 && q < z1) {
-            // y^{n+2} at plane q over the interior
-            const float* Lm = L + ring(mirror(q - 1, g.nz)) * W1 * H1;
-            const float* Lc = L + ring(q) * W1 * H1;
-            const float* Lp = L + ring(mirror(q + 1, g.nz)) * W1 * H1;
-            const float* Yq = Y + ring(q) * W2 * H2;
-            const long long base = (long long)q * sxy;
-            const int nbz = ((q == 0) & zabc0) + ((q == g.nz) & zabc1);
-#pragma unroll
-            for (int r = 0; r < kTbR0; ++r) {
-                if (p0_loc[r] < 0) continue;
-                const int c = p0_l1[r];
-                const float lc = Lc[c];
-                const float lap = 6.f * lc - ((Lc[c - 1] + Lc[c + 1]) + (Lc[c - W1] + Lc[c + W1]) + (Lm[c] + Lp[c]));
-                const long long j = base + p0_phys[r];
-                const float kk = kap[j];
-                const float yp = Yq[p0_loc[r]];
-                const float rhs = 2.f * lc - kk * lap;
-                const int nb = p0_nb[r] + nbz;
-                float out;
-                if (nb == 0) {
-                    out = rhs - yp;
-                } else {
-                    const float beta = (float)nb * sqrtf(kk);
-                    out = (rhs - (1.f - beta) * yp) / (1.f + beta);
-                }
-                Dout[j] = out;
+                const long long j = base + ph1[r];
+                const float out = lf_update(yc, lap, kap[j], A[j], nb);
+                Lk[tid + r * kTbThreads] = out;
+                if (write_c && (pk >> 19)) Cout[j] = out;
             }
         }
         __syncthreads();
@@ -643,8 +737,13 @@ inline dim3 plane_grid(const Geom& g, int zc) {
 template <typename T, int ORDER, int FLAGS>
 void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const double* S, double cs, double sn,
                    int zc, cudaStream_t st) {
-    if (ORDER == 2 && g.dim == 3) {
+    // zc < 0 selects the two-planes-per-iteration variant of the 3D 7-point kernel
+    if (ORDER == 2 && g.dim == 3 && zc < 0) {
+        k_step3d7_z2<T, FLAGS><<<plane_grid(g, -zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, -zc);
+    } else if (ORDER == 2 && g.dim == 3) {
         k_step3d7<T, FLAGS><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, zc);
+    } else if (ORDER == 4 && g.dim == 3) {
+        k_step3d13<T, FLAGS><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, zc);
     } else {
         k_step<T, ORDER, FLAGS><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, zc);
     }
@@ -832,7 +931,7 @@ void launch_step2(const Geom& g, const float* A, const float* B, const float* ka
     note_launch(1);
     int TX, TY;
     tb_tile(g, ty_max < 1 ? 1 : (ty_max > 16 ? 16 : ty_max), &TX, &TY);
-    const size_t smem = sizeof(float) * (3 * (size_t)(TX + 4) * (TY + 4) + 3 * (size_t)(TX + 2) * (TY + 2));
+    const size_t smem = sizeof(float) * (4 * (size_t)(TX + 4) * (TY + 4) + 4 * (size_t)(TX + 2) * (TY + 2));
     const dim3 grid((unsigned)((g.sx + TX - 1) / TX), (unsigned)((g.sy + TY - 1) / TY), (unsigned)((g.sz + zc - 1) / zc));
     k_step3d7_x2<<<grid, kTbThreads, smem, st>>>(A, B, kap, C, D, g, TX, TY, zc);
 }

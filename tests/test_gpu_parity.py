@@ -136,6 +136,23 @@ def test_adjoint_period(case, precision, tol):
     assert rel(g1.cpu().numpy(), q1) <= tol, name
 
 
+@pytest.mark.parametrize("tile", [(0, 0, 0, 2), (0, 8, 8, 2), (0, 3, 16, 2), (16, 0, 0, 3), (3, 0, 0, 3)])
+def test_step_scheme_variants(case, tile):
+    # FP32 periods with the alternative step kernels: two steps per launch (temporal blocking,
+    # scheme 2) and two z-planes per thread iteration (scheme 3)
+    name, w, dz = case
+    if w.dim != 3 or w.order != 2:
+        pytest.skip("the two-step kernel covers 3D 7-point grids")
+    s = solver_of(w, cmcg.FP32, tile=tile)
+    y0, v0 = rand_state(dz, 6)
+    yT, vT = wave.period(dz, y0, v0, None)
+    uT, uV = s.wave_period(y0, v0)
+    assert rel(uT.cpu().numpy(), yT) <= 2e-5 and rel(uV.cpu().numpy(), vT) <= 2e-5
+    q0, q1 = wave.transposed_period(dz, y0, v0)
+    g0, g1 = s.adjoint_period(y0, v0)
+    assert rel(g0.cpu().numpy(), q0) <= 2e-5 and rel(g1.cpu().numpy(), q1) <= 2e-5
+
+
 def test_adjoint_dot_product_on_device(case):
     name, w, dz = case
     s = solver_of(w)
@@ -304,18 +321,22 @@ def full_size():
     return w, y0 * act, v0 * act
 
 
-@pytest.mark.parametrize("precision,tol", [(cmcg.FP64, 1e-11), (cmcg.FP32, 1e-4)])
-def test_full_size_period_sampled(full_size, precision, tol):
+@pytest.mark.parametrize("precision,tol,tile", [(cmcg.FP64, 1e-11, None), (cmcg.FP32, 1e-4, None),
+                                               (cmcg.FP32, 1e-4, (0, 0, 0, 2)), (cmcg.FP32, 1e-4, (16, 0, 0, 3))])
+def test_full_size_period_sampled(full_size, precision, tol, tile):
     w, y0, v0 = full_size
-    s = solver_of(w, precision)
-    uT, vT = [t.cpu().numpy() for t in s.wave_period(y0, v0, None, w.g)]
+    s = solver_of(w, precision, tile=tile)
+    if tile is not None:  # the two-step kernel runs homogeneous steps only: no source here
+        uT, vT = [t.cpu().numpy() for t in s.wave_period(y0, v0, None, None)]
+    else:
+        uT, vT = [t.cpu().numpy() for t in s.wave_period(y0, v0, None, w.g)]
     N = s.info["steps_per_period"]
     samples = [(0, 0, 0), (128, 128, 103), (256, 40, 200), (7, 250, 128), (140, 131, 129)]
     for cidx in samples:
         sub, sl, local = crop(w, cidx, N + 3)
         dz = dz_of(sub)
         assert dz.N == N
-        yT, vTo = wave.period(dz, y0[sl], v0[sl], dz.load(sub.f, sub.g))
+        yT, vTo = wave.period(dz, y0[sl], v0[sl], None if tile is not None else dz.load(sub.f, sub.g))
         scale = max(np.abs(yT).max(), 1e-30)
         assert abs(uT[sl][local] - yT[local]) <= tol * scale, (cidx, uT[sl][local], yT[local])
         scale_v = max(np.abs(vTo).max(), 1e-30)
