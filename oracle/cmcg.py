@@ -39,7 +39,7 @@ import numpy as np
 
 from .grid import Discretization
 from .riesz import RieszSolver
-from .wave import energy_operator, period, transposed_period
+from .wave import energy_operator, period, step, transposed_period
 
 
 def e_inner(dz: Discretization, a0, a1, b0, b1) -> float:
@@ -80,6 +80,38 @@ def remove_shift(dz: Discretization, u_cg, F_hat):
     den = wt2 * np.sum(dz.M * dz.act) + 1j * wh * np.sum(dz.B)
     lam = complex(num / den)
     return (u_cg - lam) * dz.act, lam
+
+
+def filtered(dz: Discretization, v0, v1, F_hat):
+    """Step (6) by the fundamental-frequency filter of Sec. 2.2 (Eq.
+    fundamental-frequency-solution): one forced period from (v0, v1), with the time integral
+    taken by the rectangle rule over t_n = n dt, n = 0..N-1, and i/omega_hat in place of i/omega
+    (both exact for the discrete time-harmonic solution):
+        y^ = (1/N) sum_n (y^n + (i / omega_hat) v^n) exp(i omega t_n).
+    The filter removes lambda and every T-periodic eigenmode.  A linear growth eta t of the
+    minimiser leaves a constant; by the proposition of Sec. 2.2 eta = 0 when there are
+    absorbing faces or Dirichlet nodes, and in the pure Neumann case the constant is fixed by
+    the compatibility condition (Eq. cc_neumann_eta, here in its discrete form).
+    Returns (u, shift)."""
+    y = np.asarray(v0, dtype=np.float64).reshape(dz.shape) * dz.act
+    v = np.asarray(v1, dtype=np.float64).reshape(dz.shape) * dz.act
+    acc = np.zeros(dz.shape, dtype=np.complex128)
+    for n in range(dz.N):
+        acc += (y + (1j / dz.omega_hat) * v) * np.exp(1j * dz.omega * n * dz.dt)
+        y, v, _ = step(dz, y, v, n, F_hat)
+    u = acc / dz.N * dz.act
+    if dz.has_dirichlet or float(np.sum(dz.B)) > 0.0:
+        return u, 0.0 + 0.0j
+    return remove_shift(dz, u, F_hat)
+
+
+def asymptotic(dz: Discretization, y, v, F_hat):
+    """The do-nothing approximation of Sec. 4.2 (Eq. AP_SOLUTION) from the state (y, v) of the
+    forced wave equation at t = l T, recovered as in step (6): y + (i / omega_hat) v, then the
+    compatibility-condition shift when there are no Dirichlet nodes (the constant mode is a
+    steady state of the homogeneous equation, so the long-time state can carry one too)."""
+    u = (np.asarray(y).reshape(dz.shape) + (1j / dz.omega_hat) * np.asarray(v).reshape(dz.shape)) * dz.act
+    return remove_shift(dz, u, F_hat)[0]
 
 
 def solve(dz: Discretization, F_hat, tol=1e-12, max_iter=10000, v_init=None, riesz=None) -> CMCGResult:

@@ -34,9 +34,12 @@ from .grid import Discretization
 
 def step(dz: Discretization, y, v, n: int, F_hat=None):
     """One velocity-Verlet leapfrog step from t_n to t_{n+1}.  Returns (y', v', v_half)."""
+    return kick_drift_kick(dz, y, v, dz.forcing(F_hat, n), dz.forcing(F_hat, n + 1))
+
+
+def kick_drift_kick(dz: Discretization, y, v, Fn, Fn1):
+    """The step with the loads F^n, F^{n+1} given as arrays.  Returns (y', v', v_half)."""
     dt = dz.dt
-    Fn = dz.forcing(F_hat, n)
-    Fn1 = dz.forcing(F_hat, n + 1)
     v_half = v + (dt / 2.0) * (Fn - dz.K(y) - dz.B * v) / dz.M
     y_new = (y + dt * v_half) * dz.act
     v_new = (dz.M * v_half + (dt / 2.0) * (Fn1 - dz.K(y_new))) / (dz.M + (dt / 2.0) * dz.B)
@@ -50,6 +53,36 @@ def period(dz: Discretization, y0, v0, F_hat=None):
     for n in range(dz.N):
         y, v, _ = step(dz, y, v, n, F_hat)
     return y, v
+
+
+def theta_tr(t: float, t_tr: float) -> float:
+    """Smooth switch-on of the sources for the initial run-up (Sec. 4.3, Eq. transientfunction):
+    with s = sin(pi t / (2 t_tr)), theta = (2 - s) s on [0, t_tr] and 1 afterwards.  It rises
+    from 0 at t = 0 to 1 at t = t_tr, where its slope vanishes."""
+    if t >= t_tr:
+        return 1.0
+    s = np.sin(0.5 * np.pi * t / t_tr)
+    return float((2.0 - s) * s)
+
+
+def long_time(dz: Discretization, F_hat, periods: int, smooth: bool = True, trajectory: bool = False):
+    """The forced wave equation (Eq. WE) integrated from rest, y(0) = y'(0) = 0, up to
+    t = periods * T: the time-dependent solution w(., t) whose state at t = l T the
+    do-nothing solver of Sec. 4.2 reads (Eq. AP_SOLUTION) and the initial run-up of Sec. 4.3
+    hands to CMCG.  With smooth=True the load is theta_tr(t) F(t), t_tr = periods * T.
+    Returns (y, v) at t = periods * T, and with trajectory=True also the list of every y^n."""
+    total = periods * dz.N
+    t_tr = total * dz.dt
+    y = np.zeros(dz.shape)
+    v = np.zeros(dz.shape)
+    ys = [y]
+    for n in range(total):
+        th0 = theta_tr(n * dz.dt, t_tr) if smooth else 1.0
+        th1 = theta_tr((n + 1) * dz.dt, t_tr) if smooth else 1.0
+        y, v, _ = kick_drift_kick(dz, y, v, th0 * dz.forcing(F_hat, n), th1 * dz.forcing(F_hat, n + 1))
+        if trajectory:
+            ys.append(y)
+    return (y, v, ys) if trajectory else (y, v)
 
 
 def transposed_period(dz: Discretization, a, b):

@@ -207,6 +207,50 @@ def random_2d_instance(i: int, n: Optional[int] = None) -> Workload:
                     faces=(ABC,) * 4 + (NEUMANN, NEUMANN), dt_target=0.9 * h / (math.sqrt(2.0) * 2.0), f=f)
 
 
+def square_obstacle_2d(n: int = 128, cavity: bool = False, wavelengths: float = 10.0) -> Workload:
+    """Plane-wave scattering off a sound-soft square obstacle (Sec. 4.2): the paper's domain of
+    10 x 10 wavelengths rescaled to the unit square, c = 1, omega = 2 pi * wavelengths, total
+    field with g_S = (d/dn - i k) u_in for u_in incident at 135 degrees, absorbing on all four
+    sides, dt = 0.4 h.  Convex case: the square |x - 1/2|, |y - 1/2| <= 0.15 (3 wavelengths).
+    Cavity case: the same square with its interior |.| < 0.12 removed (walls 0.03 thick) and a
+    mouth |y - 1/2| < 0.05 cut into its +x wall, which faces the incoming wave: a semi-open
+    cavity that traps waves."""
+    h = 1.0 / n
+    omega = 2.0 * math.pi * wavelengths
+    x, y = coords((n, n), h)
+    solid = (np.abs(x - 0.5) <= 0.15 + 1e-12) & (np.abs(y - 0.5) <= 0.15 + 1e-12)
+    if cavity:
+        hollow = (np.abs(x - 0.5) < 0.12 - 1e-12) & (np.abs(y - 0.5) < 0.12 - 1e-12)
+        mouth = (x > 0.5) & (np.abs(y - 0.5) < 0.05 - 1e-12)
+        solid = solid & ~hollow & ~mouth
+    faces = (ABC,) * 4 + (NEUMANN, NEUMANN)
+    theta = math.radians(135.0)
+    g = plane_wave_boundary_datum((n, n), h, omega, 1.0, (math.cos(theta), math.sin(theta)), faces)
+    return Workload(name=f"2d_{'cavity' if cavity else 'square'}_n{n}", n=(n, n), h=h,
+                    c=np.ones((n + 1, n + 1)), omega=omega, faces=faces, dt_target=0.4 * h,
+                    mask=solid.astype(np.uint8), g=g)
+
+
+def neumann_box_2d(n: int = 64, dt_frac: float = 0.5) -> Workload:
+    """The physically bounded domain of Sec. 3.4 lifted to the unit square: homogeneous Neumann
+    on all four sides, c = 1, k = omega = pi/4, and the source f = -u'' - k^2 u of the exact
+    solution u(x, y) = 16 x^2 (x - 1)^2 (constant in y, zero normal derivative on every side).
+    (4k)^2 = pi^2 is a Neumann eigenvalue: the wave equation has a mode of period T/4."""
+    h = 1.0 / n
+    k = math.pi / 4.0
+    x, y = coords((n, n), h)
+    u = 16.0 * x ** 2 * (x - 1.0) ** 2 + 0.0 * y
+    f = -(192.0 * x ** 2 - 192.0 * x + 32.0) - k * k * u + 0.0 * y
+    return Workload(name=f"2d_neumann_box_n{n}", n=(n, n), h=h, c=np.ones((n + 1, n + 1)), omega=k,
+                    faces=(NEUMANN,) * 6, dt_target=dt_frac * h, f=f.astype(np.complex128))
+
+
+def neumann_box_exact(n: int) -> np.ndarray:
+    """u(x, y) = 16 x^2 (x - 1)^2 on the nodes of neumann_box_2d(n)."""
+    x, y = coords((n, n), 1.0 / n)
+    return (16.0 * x ** 2 * (x - 1.0) ** 2 + 0.0 * y).astype(np.complex128)
+
+
 def manufactured_plane_wave_field(n, h, k_axis: float) -> np.ndarray:
     """u(x) = exp(i k x_1): a plane wave along x used by the manufactured-solution checks."""
     x = coords(n, h)[0]
