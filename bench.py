@@ -87,7 +87,9 @@ def workload_config(w, args):
 
 def tile_config(solver):
     t = list(solver.opts.tile)
-    return {"tile": t, "step_scheme": "two steps per launch" if t[3] == 2 else "one step per launch"}
+    scheme = {2: "two steps per launch", 3: "one step per launch, two z-planes per thread",
+              4: "one step per launch, operands staged by TMA bulk copies into a shared-memory ring"}
+    return {"tile": t, "step_scheme": scheme.get(t[3], "one step per launch")}
 
 
 def aggregate_over_ranks(elapsed, updates, device=None):
@@ -194,9 +196,11 @@ def kernel_traffic(profile, kernel_src_hash):
 
 def kernel_src_hash(name="k_step3d7("):
     """Hash of a kernel's source text in wave.cu (the kernel that ncu counters describe)."""
-    src = open(os.path.join(ROOT, "paper_1903_12522_gb300", "csrc", "wave.cu")).read()
+    fname = "step_bulk.cu" if "bulk" in name else "wave.cu"
+    src = open(os.path.join(ROOT, "paper_1903_12522_gb300", "csrc", fname)).read()
     start = src.index(name)
-    end = src.index("// ----", start)
+    ends = [src.find(m, start) for m in ("\ntemplate", "\n__global__", "\n// ----")]
+    end = min(e for e in ends if e >= 0)
     return hashlib.sha256(src[start:end].encode()).hexdigest()
 
 
@@ -346,6 +350,14 @@ def run_ours(args):
         # FP32 3D 7-point periods run their homogeneous steps in pairs (k_step3d7_x2)
         per_launch, bpl, upl = s32 / n32, PAIR_BYTES_FP32, 2
         name, prof, src = "k_step3d7_x2: two FP32 leapfrog steps, 3D 7-point", "step3d7x2_fp32_sphere.json", "k_step3d7_x2("
+    elif n32 > 0 and s.opts.tile[3] == 4:
+        per_launch, bpl, upl = s32 / n32, STEP_BYTES_FP32, 1
+        name, prof, src = ("k_step3d7_bulk<float>: FP32 leapfrog step, 3D 7-point, operands staged by bulk copies",
+                           "step3d7bulk_fp32_sphere.json", "k_step3d7_bulk(")
+    elif n32 > 0 and s.opts.tile[3] == 3:
+        per_launch, bpl, upl = s32 / n32, STEP_BYTES_FP32, 1
+        name, prof, src = ("k_step3d7_z2<float>: FP32 leapfrog step, 3D 7-point, two z-planes per thread",
+                           "step3d7z2_fp32_sphere.json", "k_step3d7_z2(")
     elif n32 > 0:
         per_launch, bpl, upl = s32 / n32, STEP_BYTES_FP32, 1
         name, prof, src = "k_step3d7<float>: FP32 leapfrog step, 3D 7-point", "step3d7_fp32_sphere.json", "k_step3d7("

@@ -67,6 +67,40 @@ extern "C" {
                                one multigrid V-cycle per CG iteration on the dual residual,
                                with flexible (Polak-Ribiere) CG; the fixed point is unchanged
                                (the gradient of J is still evaluated exactly) */
+#define CMCG_FLAG_FILTER 8  /* recover U with the fundamental-frequency filter of Sec. 2.2: one
+                               extra forced FP64 period from the converged (v0, v1) accumulates
+                               (1/N) sum_n (y^n + (i/wh) v^n) e^{i w t_n}, which removes the constant
+                               shift of Theorem 1 without the compatibility condition (stats
+                               lambda = 0).  In the pure Neumann case (no absorbing face, no
+                               Dirichlet node) the minimiser's linear growth eta t leaves a
+                               constant, removed with the discrete compatibility condition
+                               (Eq. cc_neumann_eta); stats lambda then holds that constant */
+#define CMCG_FLAG_NO_CG 16  /* "do-nothing" long-time solver of Sec. 4.2 (Eq. AP_SOLUTION), the
+                               comparator the paper uses to show why controllability is needed:
+                               integrate the forced wave equation from rest for runup_periods = l
+                               periods (or the automatic count for -1; 0 is CMCG_ERR_INVALID_ARG)
+                               with the sources ramped by theta_tr over [0, l T] (Sec. 4.3) and
+                               recover U from the state at t = l T as in step (6), without CG.
+                               Near trapped modes (nonconvex obstacles) U converges very slowly
+                               in l; stats J_final is the periodicity misfit of that state. */
+
+#define CMCG_FLAG_FIRST_ORDER 32 /* the first-order (mixed) formulation of Sec. 3 on a staggered
+                               grid: v = y_t on the nodes, p = grad y on the grid links
+                               (Eq. mixWE), staggered leapfrog, J^ of Eq. mix_cost_functional_J
+                               with its gradient from the backward first-order period
+                               (Eq. mixJ_deriative_2); the energy inner product is diagonal, so
+                               no Riesz solve runs.  U by Eq. mix_solution, or with
+                               CMCG_FLAG_FILTER by Eq. TH_FILTERED_MIXED_SOLUTION.  The discrete
+                               fixed point is the same U as the second-order scheme's.  Supports
+                               CMCG_FP64, CMCG_FP32 and CMCG_MIXED (FP64 defect correction around
+                               FP32 CG, as for the second-order scheme; with FP32 periods use
+                               CMCG_FLAG_FILTER: rounding excites the nearly periodic spurious
+                               modes of Sec. 3.3, which Eq. mix_solution keeps and the filter
+                               removes), order 2, no run-up;
+                               order 4, runup_periods != 0, CMCG_FLAG_INEXACT_RIESZ and
+                               CMCG_FLAG_NO_CG are CMCG_ERR_UNSUPPORTED.  cmcg_wave_period, cmcg_adjoint_period and
+                               cmcg_riesz return CMCG_ERR_UNSUPPORTED on such a handle; use
+                               cmcg_fo_period and cmcg_fo_adjoint_period. */
 
 /* ---- precision of the wave stepping ------------------------------------------------ */
 #define CMCG_FP64 0  /* every operation in FP64                                            */
@@ -206,6 +240,26 @@ int cmcg_solve_host(cmcg_handle* h, const double* f_host, const double* g_host, 
 
 const char* cmcg_status_string(int status);
 
+/* ---- first-order formulation -------------------------------------------------------- */
+/* First-order state (handles created with CMCG_FLAG_FIRST_ORDER): (dim + 1) * N_p doubles,
+ * laid out p_x | p_y | (p_z) | v; p_a[j] is the link from node j to node j + e_a (entries
+ * with j_a = n_a carry no link: ignored on input, 0 on output), v[j] the velocity at node j
+ * (ignored and returned 0 on Dirichlet nodes).  All pointers are device, caller-owned.
+ *
+ * One forward staggered-leapfrog period from s0 (Eq. mixWE) into sT; f, g (nullable) are the
+ * sources as in cmcg_wave_period.  CMCG_ERR_UNSUPPORTED for a second-order handle. */
+int cmcg_fo_period(cmcg_handle* h, const double* s0, const double* f, const double* g, double* sT);
+/* The plain (Euclidean) transpose of the homogeneous first-order period map applied to y:
+ * the backward first-order wave equation of Eq. mixJ_deriative_2 in its discrete form. */
+int cmcg_fo_adjoint_period(cmcg_handle* h, const double* y, double* out);
+
+/* Self-test of the bounded wait used by the bulk-copy step kernel (cmcg_options.tile[3] == 4):
+ * one CTA waits, with at most spin_limit polls, on an mbarrier phase that nothing completes.
+ * Returns CMCG_ERR_DEVICE_TIMEOUT (the expected outcome), CMCG_OK if the wait wrongly
+ * succeeded, CMCG_ERR_INVALID_ARG for spin_limit < 1, CMCG_ERR_CUDA on a CUDA error.  The
+ * context stays usable. */
+int cmcg_bulk_wait_selftest(int spin_limit, void* stream);
+
 /* ---- multi-solve engine (batched solves and serving) -------------------------------- */
 /* Many solves advance together, one CG iteration per cmcg_engine_tick.  Each admitted solve
  * keeps its own handle (its workspace holds the resident CG state).  Per tick, the FP32
@@ -215,7 +269,8 @@ const char* cmcg_status_string(int status);
  * a CUDA graph and replayed while the set of active solves and their phases stay the same.
  * Solves finish independently; a finished solve's result is read with cmcg_engine_result,
  * which frees its slot.  Requirements: every handle uses the engine's stream, precision
- * CMCG_FP32 or CMCG_MIXED and CMCG_FLAG_INEXACT_RIESZ (else CMCG_ERR_UNSUPPORTED).  The
+ * CMCG_FP32 or CMCG_MIXED and CMCG_FLAG_INEXACT_RIESZ, and neither CMCG_FLAG_FILTER nor
+ * CMCG_FLAG_NO_CG (else CMCG_ERR_UNSUPPORTED).  The
  * batched kernel is a cooperative launch whose grid barrier waits are bounded; a wait that
  * runs out returns CMCG_ERR_DEVICE_TIMEOUT from cmcg_engine_tick. */
 typedef struct cmcg_engine cmcg_engine;

@@ -19,6 +19,10 @@ Modules
            shift removal of Sec. 2.1.
   direct   the plain definition of the method's fixed point: a direct sparse solve of the
            time-discrete Helmholtz system (K - wt^2 M - i wh B) U = F.
+  first_order
+           the first-order formulation of Sec. 3 on a staggered grid (v on nodes, p on links):
+           its leapfrog period, literal transpose, J^, CMCG without a Riesz solve, and the two
+           recoveries (Eq. mix_solution, Eq. TH_FILTERED_MIXED_SOLUTION).
 
 Parity status of each function is stated in its module header.
 """

@@ -10,7 +10,6 @@ autotune_cache.json next to this file.  Solver() looks the class up when no tile
 from __future__ import annotations
 
 import argparse
-import itertools
 import json
 import math
 import os
@@ -18,7 +17,17 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 
-CANDIDATES_3D = {"zc1": (8, 16, 32), "zc2": (8, 12, 16, 24, 32), "ty": (8, 16), "scheme": (1, 2, 3)}
+def candidates_3d():
+    """cmcg_options.tile candidates: scheme 1 (one z-plane per loop trip) and 3 (two), tile[0] =
+    z-planes per thread; scheme 2 (two steps per launch), tile[1] = z-planes per block and
+    tile[2] = tile height (the two shapes that ranked best on 257^3 and 513^3); scheme 4
+    (bulk-copy staging), tile[0] = planes per CTA and tile[1] = band rows (0 = automatic)."""
+    out = []
+    for scheme in (1, 3):
+        out += [(zc, 0, 0, scheme) for zc in (8, 16, 32)]
+    out += [(16, 12, 16, 2), (16, 24, 16, 2)]
+    out += [(zc, ty, 0, 4) for zc in (0, 16, 32, 64) for ty in (0, 4, 8)]
+    return out
 
 
 def size_class(dim, n, precision):
@@ -53,10 +62,7 @@ def tune(dim, n, precision, reps=5):
     act = 1.0 - w.mask.astype("float64")
     a, b = [torch.as_tensor(x * act, device="cuda").reshape(-1) for x in wl.random_fields(w.shape, 2, 17)]
     results = []
-    for zc1, zc2, ty, scheme in itertools.product(*CANDIDATES_3D.values()):
-        if scheme != 2 and (zc2, ty) != (CANDIDATES_3D["zc2"][0], CANDIDATES_3D["ty"][0]):
-            continue  # the two-step knobs do not matter for one-step launches
-        tile = (zc1, zc2, ty, scheme)
+    for tile in candidates_3d():
         s = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, precision=precision, dt=w.dt_target, tile=tile)
         s.adjoint_period(a, b)  # warm-up
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -25,6 +25,9 @@ FP64, FP32, MIXED = 0, 1, 2
 FLAG_HOST_IO = 1
 FLAG_TIMING = 2
 FLAG_INEXACT_RIESZ = 4
+FLAG_FILTER = 8
+FLAG_NO_CG = 16
+FLAG_FIRST_ORDER = 32
 
 ERR_DEVICE_TIMEOUT = -7
 ENGINE_NO_GRAPH = 1
@@ -34,7 +37,8 @@ EXPORTED = (
     "cmcg_adjoint_period", "cmcg_riesz", "cmcg_solve", "cmcg_solve_host", "cmcg_status_string",
     "cmcg_engine_workspace_size", "cmcg_engine_create", "cmcg_engine_destroy", "cmcg_engine_submit",
     "cmcg_engine_tick", "cmcg_engine_result", "cmcg_engine_active", "cmcg_engine_info",
-    "cmcg_engine_barrier_selftest", "cmcg_engine_cuda_error",
+    "cmcg_engine_barrier_selftest", "cmcg_engine_cuda_error", "cmcg_fo_period", "cmcg_fo_adjoint_period",
+    "cmcg_bulk_wait_selftest",
 )
 
 
@@ -96,6 +100,12 @@ def load(path: str = LIB_PATH):
     lib.cmcg_wave_period.restype = I
     lib.cmcg_adjoint_period.argtypes = [P, P, P, P, P]
     lib.cmcg_adjoint_period.restype = I
+    lib.cmcg_bulk_wait_selftest.argtypes = [I, P]
+    lib.cmcg_bulk_wait_selftest.restype = I
+    lib.cmcg_fo_period.argtypes = [P, P, P, P, P]
+    lib.cmcg_fo_period.restype = I
+    lib.cmcg_fo_adjoint_period.argtypes = [P, P, P]
+    lib.cmcg_fo_adjoint_period.restype = I
     lib.cmcg_riesz.argtypes = [P, P, P]
     lib.cmcg_riesz.restype = I
     lib.cmcg_solve.argtypes = [P, P, P, D, P, C.POINTER(Stats)]
@@ -195,6 +205,20 @@ def cmcg_wave_period(h, u0, v0, f, g, uT, vT) -> None:
 
 def cmcg_adjoint_period(h, a, b, q0, q1) -> None:
     _check(load().cmcg_adjoint_period(h, _ptr(a), _ptr(b), _ptr(q0), _ptr(q1)), "cmcg_adjoint_period")
+
+
+def cmcg_bulk_wait_selftest(spin_limit: int, stream=None) -> int:
+    """Bounded-wait self-test of the bulk-copy step kernel; returns the status code
+    (ERR_DEVICE_TIMEOUT is the expected outcome)."""
+    return int(load().cmcg_bulk_wait_selftest(int(spin_limit), stream))
+
+
+def cmcg_fo_period(h, s0, f, g, sT) -> None:
+    _check(load().cmcg_fo_period(h, _ptr(s0), _ptr(f), _ptr(g), _ptr(sT)), "cmcg_fo_period")
+
+
+def cmcg_fo_adjoint_period(h, y, out) -> None:
+    _check(load().cmcg_fo_adjoint_period(h, _ptr(y), _ptr(out)), "cmcg_fo_adjoint_period")
 
 
 def cmcg_riesz(h, rhs, s) -> int:
@@ -319,6 +343,27 @@ class Solver:
         cmcg_adjoint_period(self.handle, a, b, q0, q1)
         self._before_caller()
         return q0.reshape(self.shape), q1.reshape(self.shape)
+
+    def fo_period(self, s0, f=None, g=None):
+        """First-order handles: one forward period of the state (p_x, p_y[, p_z], v), flattened
+        to (dim + 1) * N_p doubles."""
+        torch = self.torch
+        s0 = self._dev(s0, torch.float64)
+        f, g = self._dev(f, torch.complex128), self._dev(g, torch.complex128)
+        sT = torch.empty_like(s0)
+        self._after_caller()
+        cmcg_fo_period(self.handle, s0, f, g, sT)
+        self._before_caller()
+        return sT
+
+    def fo_adjoint_period(self, y):
+        torch = self.torch
+        y = self._dev(y, torch.float64)
+        out = torch.empty_like(y)
+        self._after_caller()
+        cmcg_fo_adjoint_period(self.handle, y, out)
+        self._before_caller()
+        return out
 
     def riesz(self, rhs):
         torch = self.torch

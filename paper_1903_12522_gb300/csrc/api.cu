@@ -112,8 +112,24 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
     H->mass = c.take<double>(np);
     H->minv = c.take<double>(np);
     H->mask = c.take<unsigned char>(np);
-    H->kap32 = o.precision != CMCG_FP64 ? c.take<float>(np) : nullptr;
+    H->kap32 = o.precision != CMCG_FP64 ? c.take<float>(np + 4) : nullptr;  // + 16 B for bulk copies
     H->S = c.take<double>(2 * np);
+    if (o.flags & CMCG_FLAG_FIRST_ORDER) {
+        // first-order state (p, v): CG vectors and the two stepping buffers; no Riesz map
+        const size_t ns = (size_t)(g.dim + 1) * np;
+        double** fo[] = {&H->fo_s, &H->fo_r, &H->fo_d, &H->fo_e, &H->fo_g, &H->fo_x};
+        for (double** p : fo) *p = c.take<double>(ns);
+        H->fo_a = c.take<double>(ns);
+        H->fo_b = c.take<double>(ns);
+        H->first_order = true;
+        H->nlev = 0;
+        H->stage = (o.flags & CMCG_FLAG_HOST_IO) ? c.take<double>(2 * np) : nullptr;
+        long long nb = std::max<long long>(kMaxBlocksReduce, plane_blocks(g, kZcEnds));
+        H->partials = c.take<double>((size_t)8 * nb);
+        H->tickets = c.take<unsigned>(kNumTickets);
+        H->sc = c.take<double>(SC_COUNT);
+        return c.off + 256;
+    }
     H->ya = c.take<double>(np);
     H->yb = c.take<double>(np);
     H->tmp = c.take<double>(np);
@@ -227,6 +243,21 @@ bool use_pairs(const cmcg_handle* H, bool src) {
     return H->opt.tile[3] == 2 && std::is_same<T, float>::value && !src && step2_supported(H->g, H->order);
 }
 
+// One leapfrog step cur -> prev (in place).  FP32 3D 7-point steps without a source go through
+// the bulk-copy kernel when tile[3] == 4 (tile[1] = band rows, tile[0] = planes per CTA).
+template <typename T>
+void step_one(cmcg_handle* H, const T* cur, T* prev, const T* kap, const double* S, double cs, double sn, int flags,
+              int zc) {
+    if (std::is_same<T, float>::value && H->opt.tile[3] == 4 && H->order == 2 && !(flags & kStepSrc)) {
+        int ty = 0, zb = 0;
+        if (step_bulk_plan(H->g, H->opt.tile[1], H->opt.tile[0], &ty, &zb)) {
+            launch_step_bulk(H->g, (const float*)cur, (float*)prev, (const float*)kap, flags, ty, zb, H->sc, H->st);
+            return;
+        }
+    }
+    launch_step<T>(H->g, H->order, cur, prev, kap, S, cs, sn, flags, zc, H->st);
+}
+
 // `count` homogeneous steps from b (in pairs where possible, else one by one).
 template <typename T>
 void plain_steps(cmcg_handle* H, PeriodBuffers& b, int count) {
@@ -258,7 +289,7 @@ void plain_steps(cmcg_handle* H, PeriodBuffers& b, int count) {
     if (count <= 0) return;
     const int tp = use_pairs<T>(H, false) ? -1 : timing_begin(H, std::is_same<T, float>::value, count);
     for (int n = 0; n < count; ++n) {
-        launch_step<T>(g, H->order, (const T*)b.cur, (T*)b.prev, kap, nullptr, 0.0, 0.0, 0, zc, H->st);
+        step_one<T>(H, (const T*)b.cur, (T*)b.prev, kap, nullptr, 0.0, 0.0, 0, zc);
         std::swap(b.cur, b.prev);
     }
     timing_end(H, tp);
@@ -330,13 +361,11 @@ int adj_step_flags(int k, int N) {
 
 template <typename T>
 void adj_steps(cmcg_handle* H, PeriodBuffers& b) {
-    const Geom& g = H->g;
     const int zc = step_zc(H);
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     const int n = H->N - 1;  // steps k = 0 .. N-2; the first and the last have their own variants
     auto single = [&](int k) {
-        launch_step<T>(g, H->order, (const T*)b.cur, (T*)b.prev, kap, nullptr, 0.0, 0.0, adj_step_flags(k, H->N), zc,
-                       H->st);
+        step_one<T>(H, (const T*)b.cur, (T*)b.prev, kap, nullptr, 0.0, 0.0, adj_step_flags(k, H->N), zc);
         std::swap(b.cur, b.prev);
     };
     if (use_pairs<T>(H, false)) {
@@ -649,7 +678,6 @@ int cg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_ou
 
 template <typename T>
 int solve_plain(cmcg_handle* H, double tol, cmcg_stats* stats) {
-    const long long n = H->g.np;
     // (1) v = 0 or the run-up state; (2)-(3) gradient with the sources and its Riesz map
     double gamma_zero = -1.0;
     int rc = initial_guess<T>(H, H->w0, H->w1, &gamma_zero, stats);
@@ -738,27 +766,61 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
 // Step (6): U = v0 + i v1 / omega_hat from (w0, w1), then the compatibility-condition shift
 //   lambda = (1.F + wt^2 1.M u + i wh 1.B u) / (wt^2 sum M + i wh sum B)
 // when there is no Dirichlet node.
+// lambda of the discrete compatibility condition (K - wt^2 M - i wh B)(u - lambda) = F^ from
+// the sums 1.F^, 1.M u, 1.B u in hsc[SC_R0..+5]; subtracts it from u (device).
+void compat_shift(cmcg_handle* h, double* u, double* lre, double* lim) {
+    const double* r = h->hsc + SC_R0;
+    const double wt2 = h->wt * h->wt;
+    const double nre = r[0] + wt2 * r[2] - h->wh * r[5];
+    const double nim = r[1] + wt2 * r[3] + h->wh * r[4];
+    const double dre = wt2 * h->sumM, dim = h->wh * h->sumB;
+    const double den = dre * dre + dim * dim;
+    *lre = (nre * dre + nim * dim) / den;
+    *lim = (nim * dre - nre * dim) / den;
+    launch_shift(h->g.np, u, h->kap64, *lre, *lim, h->st);
+}
+
 int recover(cmcg_handle* h, double* u, cmcg_stats* st) {
-    const long long n = h->g.np;
     launch_recover(h->g, h->w0, h->w1, h->wh, h->S, h->kap64, h->mass, u, h->red(), h->st);
     if (sync_read(h) != CMCG_OK) return CMCG_ERR_CUDA;
     double lre = 0.0, lim = 0.0;
-    if (!h->has_dir) {
-        const double* r = h->hsc + SC_R0;
-        const double wt2 = h->wt * h->wt;
-        const double nre = r[0] + wt2 * r[2] - h->wh * r[5];
-        const double nim = r[1] + wt2 * r[3] + h->wh * r[4];
-        const double dre = wt2 * h->sumM, dim = h->wh * h->sumB;
-        const double den = dre * dre + dim * dim;
-        lre = (nre * dre + nim * dim) / den;
-        lim = (nim * dre - nre * dim) / den;
-        launch_shift(n, u, h->kap64, lre, lim, h->st);
-    }
+    if (!h->has_dir) compat_shift(h, u, &lre, &lim);
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
     if (cuda_status() != CMCG_OK) return CMCG_ERR_CUDA;
     st->lambda_re = lre;
     st->lambda_im = lim;
     return CMCG_OK;
+}
+
+// Step (6) by the fundamental-frequency filter of Sec. 2.2 instead of the compatibility
+// condition: one forced FP64 period from (w0, w1), accumulating
+// U = (1/N) sum_n (y^n + (i/wh) v^n) e^{i w t_n} in u.  The filter removes lambda and the
+// T-periodic eigenmodes; a linearly growing part eta t of the minimiser survives as a constant.
+// It vanishes when there are absorbing faces or Dirichlet nodes; in the pure Neumann case it is
+// removed with the discrete compatibility condition (the discrete form of Eq. cc_neumann_eta),
+// and its value is returned in stats lambda.
+int filter_recover(cmcg_handle* h, double* u, cmcg_stats* st) {
+    const Geom& g = h->g;
+    const int zc = g.dim == 3 ? kZcStep3D : 1;
+    launch_filter_init(g.np, h->w0, h->w1, h->kap64, 1.0 / h->wh, u, h->st);
+    PeriodBuffers b = fwd_begin<double>(h, h->w0, h->w1, true);
+    const double cv = 1.0 / (2.0 * h->dt * h->wh);
+    for (int n = 1; n < h->N; ++n) {
+        const double t = n * h->dt, c = cos(h->omega * t), sn = sin(h->omega * t);
+        launch_step_filter(g, h->order, (const double*)b.cur, (double*)b.prev, h->kap64, h->S, c, sn, u, c, sn, cv, zc,
+                           h->st);
+        std::swap(b.cur, b.prev);
+    }
+    launch_scale_complex(g.np, u, 1.0 / h->N, h->st);
+    h->periods += 1;
+    st->lambda_re = st->lambda_im = 0.0;
+    if (!h->has_dir && g.abc == 0u) {
+        launch_compat_sums(g, u, h->S, h->kap64, h->mass, h->red(), h->st);
+        if (sync_read(h) != CMCG_OK) return CMCG_ERR_CUDA;
+        compat_shift(h, u, &st->lambda_re, &st->lambda_im);
+    }
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return cuda_status();
 }
 
 // Steps (1)-(6) with the source S already in the workspace; U into u (device).
@@ -772,7 +834,41 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
     h->periods = 0;
     const long long n = h->g.np;
     int rc;
-    if (h->opt.precision == CMCG_FP64)
+    if (h->first_order) {
+        // Sec. 3: CMCG on the first-order state, J^ at the result, step (6)
+        rc = fo_solve(h, tol, st);
+        if (rc < 0) return rc;
+        const long long periods_solve = h->periods;
+        if (want_J) {
+            fo_J(h);
+            if (sync_read(h) != CMCG_OK) return CMCG_ERR_CUDA;
+            st->J_final = h->hsc[SC_J];
+        }
+        if (fo_recover(h, u) != CMCG_OK) return CMCG_ERR_CUDA;
+        st->steps_per_period = h->N;
+        st->dt = h->dt;
+        st->omega_tilde = h->wt;
+        st->omega_hat = h->wh;
+        st->periods = (int)periods_solve;
+        st->point_updates = periods_solve * (long long)h->N * n;
+        st->kernel_launches = launch_count() - launches0;
+        if (h->timing) collect_timing(h);
+        st->step_seconds_fp64 = h->step_s[0];
+        st->step_seconds_fp32 = h->step_s[1];
+        st->step_launches_fp64 = h->step_n[0];
+        st->step_launches_fp32 = h->step_n[1];
+        return rc;
+    }
+    if (h->opt.flags & CMCG_FLAG_NO_CG) {
+        // do-nothing: the run-up's final state is the answer
+        const int ell = runup_count(h);
+        st->runup_periods = ell;
+        if (h->opt.precision == CMCG_FP64)
+            runup<double>(h, ell, h->w0, h->w1);
+        else
+            runup<float>(h, ell, h->w0, h->w1);
+        rc = cuda_status();
+    } else if (h->opt.precision == CMCG_FP64)
         rc = solve_plain<double>(h, tol, st);
     else if (h->opt.precision == CMCG_FP32)
         rc = solve_plain<float>(h, tol, st);
@@ -786,8 +882,12 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
         if (sync_read(h) != CMCG_OK) return CMCG_ERR_CUDA;
         st->J_final = h->hsc[SC_J];
     }
-    // (6) recovery and the compatibility-condition shift
-    if (recover(h, u, st) != CMCG_OK) return CMCG_ERR_CUDA;
+    // (6) recovery: the compatibility-condition shift, or the filter of Sec. 2.2
+    if (h->opt.flags & CMCG_FLAG_FILTER) {
+        if (filter_recover(h, u, st) != CMCG_OK) return CMCG_ERR_CUDA;
+    } else if (recover(h, u, st) != CMCG_OK) {
+        return CMCG_ERR_CUDA;
+    }
     st->steps_per_period = h->N;
     st->dt = h->dt;
     st->omega_tilde = h->wt;
@@ -926,7 +1026,14 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     cmcg_options o{};
     if (opts) o = *opts;
     if (o.precision < CMCG_FP64 || o.precision > CMCG_MIXED) return CMCG_ERR_INVALID_ARG;
-    if (o.flags & ~(CMCG_FLAG_HOST_IO | CMCG_FLAG_TIMING | CMCG_FLAG_INEXACT_RIESZ)) return CMCG_ERR_INVALID_ARG;
+    if (o.flags & ~(CMCG_FLAG_HOST_IO | CMCG_FLAG_TIMING | CMCG_FLAG_INEXACT_RIESZ | CMCG_FLAG_FILTER |
+                    CMCG_FLAG_NO_CG | CMCG_FLAG_FIRST_ORDER))
+        return CMCG_ERR_INVALID_ARG;
+    if ((o.flags & CMCG_FLAG_NO_CG) && o.runup_periods == 0) return CMCG_ERR_INVALID_ARG;
+    if ((o.flags & CMCG_FLAG_FIRST_ORDER) &&
+        (grid->order != 2 || o.runup_periods != 0 ||
+         (o.flags & (CMCG_FLAG_INEXACT_RIESZ | CMCG_FLAG_NO_CG))))
+        return CMCG_ERR_UNSUPPORTED;
     if (o.dt < 0 || !isfinite(o.dt)) return CMCG_ERR_INVALID_ARG;
     fill_defaults(&o);
     unsigned abc = 0, dir = 0;
@@ -984,7 +1091,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     if (H->has_dir && H->sumW <= 0) return fail(CMCG_ERR_INVALID_ARG);
     if (o.runup_periods < -1 || o.runup_periods > 100000) return fail(CMCG_ERR_INVALID_ARG);
     if (o.tile[0] < 0 || o.tile[0] > 512 || o.tile[1] < 0 || o.tile[1] > 512 || o.tile[2] < 0 || o.tile[2] > 16 ||
-        o.tile[3] < 0 || o.tile[3] > 3)
+        o.tile[3] < 0 || o.tile[3] > 4)
         return fail(CMCG_ERR_INVALID_ARG);
     // time step: N = ceil(T / dt_target - 1e-9), dt = T / N
     const double dt_target = o.dt > 0 ? o.dt : 0.5 * grid->h / (sqrt((double)grid->dim) * cmax);
@@ -1045,6 +1152,7 @@ int cmcg_get_info(const cmcg_handle* h, cmcg_info* info) {
 int cmcg_wave_period(cmcg_handle* h, const double* u0, const double* v0, const double* f, const double* g,
                      double* uT, double* vT) {
     if (!h || !u0 || !v0 || !uT || !vT) return CMCG_ERR_INVALID_ARG;
+    if (h->first_order) return CMCG_ERR_UNSUPPORTED;
     const bool src = f || g;
     if (src) launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
     launch_mask_copy(h->g, u0, h->kap64, h->z0, h->st);
@@ -1059,6 +1167,7 @@ int cmcg_wave_period(cmcg_handle* h, const double* u0, const double* v0, const d
 
 int cmcg_adjoint_period(cmcg_handle* h, const double* a, const double* b, double* q0, double* q1) {
     if (!h || !a || !b || !q0 || !q1) return CMCG_ERR_INVALID_ARG;
+    if (h->first_order) return CMCG_ERR_UNSUPPORTED;
     launch_mask_copy(h->g, a, h->kap64, h->z0, h->st);
     launch_mask_copy(h->g, b, h->kap64, h->z1, h->st);
     if (h->opt.precision == CMCG_FP32)
@@ -1071,9 +1180,33 @@ int cmcg_adjoint_period(cmcg_handle* h, const double* a, const double* b, double
 
 int cmcg_riesz(cmcg_handle* h, const double* rhs, double* s) {
     if (!h || !rhs || !s) return CMCG_ERR_INVALID_ARG;
+    if (h->first_order) return CMCG_ERR_UNSUPPORTED;
     int rc = riesz_solve(h, rhs, s, nullptr);
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
     return rc;
+}
+
+int cmcg_bulk_wait_selftest(int spin_limit, void* stream) {
+    if (spin_limit < 1) return CMCG_ERR_INVALID_ARG;
+    return bulk_wait_selftest(spin_limit, (cudaStream_t)stream);
+}
+
+int cmcg_fo_period(cmcg_handle* h, const double* s0, const double* f, const double* g, double* sT) {
+    if (!h || !s0 || !sT) return CMCG_ERR_INVALID_ARG;
+    if (!h->first_order) return CMCG_ERR_UNSUPPORTED;
+    const bool src = f || g;
+    if (src) launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
+    if (fo_period(h, s0, src, sT) != CMCG_OK) return CMCG_ERR_CUDA;
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return cuda_status();
+}
+
+int cmcg_fo_adjoint_period(cmcg_handle* h, const double* y, double* out) {
+    if (!h || !y || !out) return CMCG_ERR_INVALID_ARG;
+    if (!h->first_order) return CMCG_ERR_UNSUPPORTED;
+    if (fo_adjoint(h, y, out) != CMCG_OK) return CMCG_ERR_CUDA;
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
+    return cuda_status();
 }
 
 int cmcg_solve(cmcg_handle* h, const double* f, const double* g, double tol, double* u, cmcg_stats* stats) {

@@ -210,6 +210,7 @@ enum Slot {
     SC_P_XW,         // sum(W x) for the mean removal
     // recovery
     SC_R0, SC_R1, SC_R2, SC_R3, SC_R4, SC_R5, SC_R6, SC_R7,
+    SC_DEVERR,       // nonzero: a kernel's bounded wait ran out (the CMCG status code it reports)
     SC_COUNT
 };
 

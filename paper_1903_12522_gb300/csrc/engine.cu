@@ -343,7 +343,8 @@ int cmcg_engine_destroy(cmcg_engine* e) {
 
 int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const double* g, double tol, double* u) {
     if (!e || !h || !u || !(tol > 0)) return CMCG_ERR_INVALID_ARG;
-    if (h->st != e->st || h->opt.precision == CMCG_FP64 || !(h->opt.flags & CMCG_FLAG_INEXACT_RIESZ))
+    if (h->st != e->st || h->opt.precision == CMCG_FP64 || !(h->opt.flags & CMCG_FLAG_INEXACT_RIESZ) ||
+        (h->opt.flags & (CMCG_FLAG_FILTER | CMCG_FLAG_NO_CG | CMCG_FLAG_FIRST_ORDER)))
         return CMCG_ERR_UNSUPPORTED;
     int s = -1;
     for (int i = 0; i < e->max_slots; ++i) {

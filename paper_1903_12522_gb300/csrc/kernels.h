@@ -61,9 +61,29 @@ int batch_steps_max_blocks();
 cudaError_t launch_batch_steps(const BatchItem* items, int nitems, int total_blocks, int max_steps, unsigned* bar,
                                int* err, int grid, cudaStream_t st);
 cudaError_t launch_barrier_selftest(unsigned* bar, int* err, long long spin_limit, cudaStream_t st);
+// Fundamental-frequency filter (Sec. 2.2) fused into a forced FP64 forward period.
+void launch_filter_init(long long n, const double* w0, const double* w1, const double* kap64, double inv_wh,
+                        double* acc, cudaStream_t st);
+void launch_step_filter(const Geom& g, int order, const double* cur, double* prev, const double* kap,
+                        const double* S, double cs, double sn, double* acc, double fc, double fs, double cv, int zc,
+                        cudaStream_t st);
+void launch_scale_complex(long long n, double* u, double s, cudaStream_t st);
 void launch_make_source(const Geom& g, const double* f, const double* gb, const double* kap64, double* S, int zc,
                         bool accumulate, cudaStream_t st);
 long long plane_blocks(const Geom& g, int zc);
+
+// ---- step_bulk.cu -----------------------------------------------------------------------
+// FP32 3D 7-point leapfrog step with TMA bulk-copy staging (homogeneous; flags 0, PREV_SCALED,
+// NO_DIV).  step_bulk_plan picks the band height ty and the planes per CTA zc (requests <= 0 mean
+// automatic) and returns false when the grid does not fit the kernel.  The fields must have 16
+// bytes of readable memory past their last node.  A timed-out wait sets sc[SC_DEVERR].
+int step_bulk_smem(int sx, int ty);
+// Runs the bulk kernel's bounded mbarrier wait on a phase that never completes; returns
+// CMCG_ERR_DEVICE_TIMEOUT when the wait runs out as it must (CMCG_OK would mean it did not).
+int bulk_wait_selftest(int spin_limit, cudaStream_t st);
+bool step_bulk_plan(const Geom& g, int ty_req, int zc_req, int* ty, int* zc);
+void launch_step_bulk(const Geom& g, const float* cur, float* prev, const float* kap, int flags, int ty, int zc,
+                      double* sc, cudaStream_t st);
 
 // ---- linalg.cu ------------------------------------------------------------------------
 // Setup: kappa = c^2 dt^2 / h^2 (0 on Dirichlet nodes), M = W / c^2 (0 on Dirichlet nodes),
@@ -98,6 +118,9 @@ void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_
                      double* z1, Red red, bool first, cudaStream_t st);
 void launch_wsum_float(const Geom& g, const float* x, Red red, cudaStream_t st);
 void launch_shift(long long n, double* u, const double* kap64, double lre, double lim, cudaStream_t st);
+// Sums of the compatibility condition for a complex field u: 1.F^, 1.M u, 1.B u -> sc[SC_R0..+5].
+void launch_compat_sums(const Geom& g, const double* u, const double* S, const double* kap64, const double* mass,
+                        Red red, cudaStream_t st);
 void launch_scalar_residual(long long n, const double* r0, const double* r1, const double* rh0,
                             const double* rh1, Red red, int slot, cudaStream_t st);
 

@@ -232,6 +232,39 @@ __global__ void __launch_bounds__(kT) k_recover(Geom g, const double* __restrict
     }
 }
 
+// The sums of the discrete compatibility condition for a complex field u (interleaved):
+// 1.F^ (re, im), 1.M u (re, im), 1.B u (re, im) into sc[SC_R0 .. SC_R0 + 5].
+__global__ void __launch_bounds__(kT) k_compat_sums(Geom g, const double* __restrict__ u, const double* __restrict__ S,
+                                                    const double* __restrict__ kap64,
+                                                    const double* __restrict__ mass, Red red) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
+        const double k = kap64[j];
+        if (k == 0.0) continue;
+        const unsigned t = (unsigned)j / (unsigned)g.sx;
+        const int ix = (int)((unsigned)j - t * (unsigned)g.sx);
+        const int iz = (int)(t / (unsigned)g.sy);
+        const int iy = (int)(t - (unsigned)iz * (unsigned)g.sy);
+        const double re = u[2 * j], im = u[2 * j + 1];
+        const double W = weight(g, ix, iy, iz);
+        const double M = mass[j];
+        const double B = 2.0 * num_abc(g, ix, iy, iz) / g.h * sqrt(W * M);
+        if (S) {
+            const double sc = W / (k * g.h * g.h);
+            acc[0] += sc * S[2 * j];
+            acc[1] += sc * S[2 * j + 1];
+        }
+        acc[2] += M * re;
+        acc[3] += M * im;
+        acc[4] += B * re;
+        acc[5] += B * im;
+    }
+    if (grid_sum<6>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) red.sc[SC_R0 + k] = acc[k];
+    }
+}
+
 __global__ void k_axpy(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) y[j] += a * x[j];
@@ -382,6 +415,12 @@ void launch_recover(const Geom& g, const double* w0, const double* w1, double om
                     const double* kap64, const double* mass, double* u, Red red, cudaStream_t st) {
     note_launch(1);
     k_recover<<<vec_blocks(g.np), kT, 0, st>>>(g, w0, w1, 1.0 / omega_hat, S, kap64, mass, u, red);
+}
+
+void launch_compat_sums(const Geom& g, const double* u, const double* S, const double* kap64, const double* mass,
+                        Red red, cudaStream_t st) {
+    note_launch(1);
+    k_compat_sums<<<vec_blocks(g.np), kT, 0, st>>>(g, u, S, kap64, mass, red);
 }
 
 void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t st) {

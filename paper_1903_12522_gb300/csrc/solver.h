@@ -44,6 +44,11 @@ struct cmcg_handle {
     int blk_level = -1;       // first level run inside one thread block (-1: none)
     BlockLevels blk{};
     int riesz_guess = 0;      // PCG iterations of the previous Riesz solve
+    // first-order formulation (CMCG_FLAG_FIRST_ORDER): CG vectors on the state (p, v) of
+    // (dim + 1) N_p doubles, and the two stepping buffers (sized for double)
+    double *fo_s = nullptr, *fo_r = nullptr, *fo_d = nullptr, *fo_e = nullptr, *fo_g = nullptr, *fo_x = nullptr;
+    void *fo_a = nullptr, *fo_b = nullptr;
+    bool first_order = false;
     // host staging
     double* stage = nullptr;
     // reductions
@@ -100,6 +105,19 @@ void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src
 // Step (6): U from (w0, w1) into u and the compatibility-condition shift; fills st's
 // lambda fields.  Synchronises the stream.
 int recover(cmcg_handle* h, double* u, cmcg_stats* st);
+int timing_begin(cmcg_handle* H, bool fp32, int steps);
+void timing_end(cmcg_handle* H, int p);
+
+// First-order formulation (first_order.cu).  fo_solve runs steps (1)-(5) on the state in
+// fo_s; fo_recover writes U (step (6), Eq. mix_solution or, with CMCG_FLAG_FILTER, Eq.
+// TH_FILTERED_MIXED_SOLUTION) and synchronises; fo_J evaluates J^ at fo_s into sc[SC_J];
+// fo_period / fo_adjoint are one forward period (with the sources when src) and the plain
+// transpose of the homogeneous period.
+int fo_solve(cmcg_handle* H, double tol, cmcg_stats* st);
+int fo_recover(cmcg_handle* H, double* u);
+void fo_J(cmcg_handle* H);
+int fo_period(cmcg_handle* H, const double* s0, bool src, double* out);
+int fo_adjoint(cmcg_handle* H, const double* y, double* out);
 
 }  // namespace detail
 }  // namespace cmcg

@@ -17,6 +17,8 @@
 // step returns s = (1 + beta) u_0 = M^-1 ybar_1, which the final kernel needs).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -90,6 +92,57 @@ __global__ void __launch_bounds__(kThreads) k_step(const T* __restrict__ cur, T*
         }
         prev_out[j] = out;
     }
+}
+
+// Fundamental-frequency filter of Sec. 2.2, fused into a forced forward period:
+//   U = (1/N) sum_{n=0}^{N-1} (y^n + (i/wh) v^n) e^{i w t_n},  v^n = (y^{n+1} - y^{n-1}) / (2 dt)
+// (rectangle rule; exact for the discrete time-harmonic solution, and the constant shift of
+// Theorem 1 and the other harmonics drop out).  The step below is the forced leapfrog step
+// that also adds its term n to the complex accumulator acc (interleaved re, im).
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_step_filter(const double* __restrict__ cur, double* __restrict__ prev_out,
+                                                          const double* __restrict__ kap, const double* __restrict__ S,
+                                                          double cs, double sn, double* __restrict__ acc, double fc,
+                                                          double fs, double cv, Geom g, int zc) {
+    const PlaneMap m = plane_map(g, zc);
+    if (!m.valid) return;
+    Ld<double> f{cur};
+    for (int iz = m.z0; iz < m.z1; ++iz) {
+        const long long j = node(g, m.ix, m.iy, iz);
+        const double L = lap_t<ORDER, double>(g, f, j, m.ix, m.iy, iz);
+        const double k = kap[j];
+        const double yp = prev_out[j];
+        const double yc = cur[j];
+        const double rhs = 2.0 * yc - k * L + (S[2 * j] * cs + S[2 * j + 1] * sn);
+        const int nb = num_abc(g, m.ix, m.iy, iz);
+        double out;
+        if (nb == 0) {
+            out = rhs - yp;
+        } else {
+            const double beta = nb * sqrt(k);
+            out = (rhs - (1.0 - beta) * yp) / (1.0 + beta);
+        }
+        prev_out[j] = out;
+        const double a = yc, b = cv * (out - yp);  // y^n and v^n / wh
+        acc[2 * j] += a * fc - b * fs;
+        acc[2 * j + 1] += a * fs + b * fc;
+    }
+}
+
+// acc = w0 + i w1 / wh (the n = 0 term; zero on Dirichlet nodes).
+__global__ void k_filter_init(long long n, const double* __restrict__ w0, const double* __restrict__ w1,
+                              const double* __restrict__ kap64, double inv_wh, double* __restrict__ acc) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const bool act = kap64[j] != 0.0;
+        acc[2 * j] = act ? w0[j] : 0.0;
+        acc[2 * j + 1] = act ? w1[j] * inv_wh : 0.0;
+    }
+}
+
+__global__ void k_scale_complex(long long n, double* __restrict__ u, double s) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < 2 * n; j += stride) u[j] *= s;
 }
 
 // Leapfrog step, 3D 2nd order: z-neighbours carried in registers along the march.
@@ -934,6 +987,33 @@ void launch_step2(const Geom& g, const float* A, const float* B, const float* ka
     const size_t smem = sizeof(float) * (4 * (size_t)(TX + 4) * (TY + 4) + 4 * (size_t)(TX + 2) * (TY + 2));
     const dim3 grid((unsigned)((g.sx + TX - 1) / TX), (unsigned)((g.sy + TY - 1) / TY), (unsigned)((g.sz + zc - 1) / zc));
     k_step3d7_x2<<<grid, kTbThreads, smem, st>>>(A, B, kap, C, D, g, TX, TY, zc);
+}
+
+}  // namespace cmcg
+
+namespace cmcg {
+
+void launch_filter_init(long long n, const double* w0, const double* w1, const double* kap64, double inv_wh,
+                        double* acc, cudaStream_t st) {
+    note_launch(1);
+    const unsigned blocks = (unsigned)std::min<long long>((n + kThreads - 1) / kThreads, 152 * 8);
+    k_filter_init<<<blocks, kThreads, 0, st>>>(n, w0, w1, kap64, inv_wh, acc);
+}
+
+void launch_step_filter(const Geom& g, int order, const double* cur, double* prev, const double* kap,
+                        const double* S, double cs, double sn, double* acc, double fc, double fs, double cv, int zc,
+                        cudaStream_t st) {
+    note_launch(1);
+    if (order == 2)
+        k_step_filter<2><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, acc, fc, fs, cv, g, zc);
+    else
+        k_step_filter<4><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, acc, fc, fs, cv, g, zc);
+}
+
+void launch_scale_complex(long long n, double* u, double s, cudaStream_t st) {
+    note_launch(1);
+    const unsigned blocks = (unsigned)std::min<long long>((2 * n + kThreads - 1) / kThreads, 152 * 8);
+    k_scale_complex<<<blocks, kThreads, 0, st>>>(n, u, s);
 }
 
 }  // namespace cmcg

@@ -136,10 +136,12 @@ def test_adjoint_period(case, precision, tol):
     assert rel(g1.cpu().numpy(), q1) <= tol, name
 
 
-@pytest.mark.parametrize("tile", [(0, 0, 0, 2), (0, 8, 8, 2), (0, 3, 16, 2), (16, 0, 0, 3), (3, 0, 0, 3)])
+@pytest.mark.parametrize("tile", [(0, 0, 0, 2), (0, 8, 8, 2), (0, 3, 16, 2), (16, 0, 0, 3), (3, 0, 0, 3),
+                                  (0, 0, 0, 4), (3, 0, 0, 4), (0, 2, 0, 4), (5, 1, 0, 4)])
 def test_step_scheme_variants(case, tile):
     # FP32 periods with the alternative step kernels: two steps per launch (temporal blocking,
-    # scheme 2) and two z-planes per thread iteration (scheme 3)
+    # scheme 2), two z-planes per thread iteration (scheme 3), and operands staged by bulk
+    # copies into a shared-memory ring (scheme 4: tile[0] planes per CTA, tile[1] band rows)
     name, w, dz = case
     if w.dim != 3 or w.order != 2:
         pytest.skip("the two-step kernel covers 3D 7-point grids")
@@ -218,6 +220,48 @@ def test_runup_keeps_the_fixed_point_and_saves_iterations(precision, flags, tol,
     assert st1["status"] == cmcg.OK and st1["runup_periods"] > 0
     assert wrel(dz, u1.cpu().numpy(), U) <= bound
     assert st1["iterations"] < st0["iterations"], (st0["iterations"], st1["iterations"])
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(cmcg.FP64, 1e-13, 1e-10), (cmcg.MIXED, 1e-9, 1e-6)])
+def test_filter_recovery_matches_direct(case, precision, tol, bound):
+    # Sec. 2.2: the fundamental-frequency filter over one forced period gives U without the
+    # compatibility-condition shift
+    name, w, dz = case
+    s = solver_of(w, precision, flags=cmcg.FLAG_FILTER)
+    U = direct.solve(dz, dz.load(w.f, w.g))
+    u, st = s.solve(w.f, w.g, tol=tol)
+    assert st["status"] == cmcg.OK and st["lambda_re"] == 0.0
+    assert wrel(dz, u.cpu().numpy(), U) <= bound, name
+
+
+@pytest.mark.parametrize("flags", [0, cmcg.FLAG_FILTER])
+def test_pure_neumann_after_runup(flags):
+    # Sec. 2.2 and 3.4: pure Neumann box (k = pi/4); from a run-up the minimiser grows
+    # linearly (eta t).  Plain recovery removes the constant with lambda; the filter removes
+    # the rest and fixes the constant by the discrete form of Eq. cc_neumann_eta
+    w = wl.neumann_box_2d(40)
+    dz = dz_of(w)
+    F = dz.load(w.f, None)
+    U = direct.solve(dz, F)
+    u, st = solver_of(w, cmcg.FP64, flags=flags, runup_periods=2).solve(w.f, None, tol=1e-12)
+    assert st["status"] == cmcg.OK and st["runup_periods"] == 2
+    assert abs(complex(st["lambda_re"], st["lambda_im"])) > 1e-2
+    assert wrel(dz, u.cpu().numpy(), U) <= 1e-8
+
+
+@pytest.mark.parametrize("precision,bound", [(cmcg.FP64, 1e-11), (cmcg.FP32, 1e-4)])
+def test_do_nothing_matches_oracle_long_time(case, precision, bound):
+    # Sec. 4.2 (Eq. AP_SOLUTION): l = 3 periods of the forced wave equation from rest with the
+    # ramped sources of Sec. 4.3, recovered as in step (6); no CG
+    name, w, dz = case
+    F = dz.load(w.f, w.g)
+    y, v = wave.long_time(dz, F, 3)
+    ref = ocmcg.asymptotic(dz, y, v, F)
+    s = solver_of(w, precision, flags=cmcg.FLAG_NO_CG, runup_periods=3)
+    u, st = s.solve(w.f, w.g, tol=1e-6)
+    assert st["status"] == cmcg.OK and st["iterations"] == 0 and st["runup_periods"] == 3
+    assert st["periods"] == 3 and st["point_updates"] == 3 * dz.N * dz.size
+    assert wrel(dz, u.cpu().numpy(), ref) <= bound, name
 
 
 def test_fp64_iterations_and_shift_match_oracle(case):
@@ -322,7 +366,8 @@ def full_size():
 
 
 @pytest.mark.parametrize("precision,tol,tile", [(cmcg.FP64, 1e-11, None), (cmcg.FP32, 1e-4, None),
-                                               (cmcg.FP32, 1e-4, (0, 0, 0, 2)), (cmcg.FP32, 1e-4, (16, 0, 0, 3))])
+                                               (cmcg.FP32, 1e-4, (0, 0, 0, 2)), (cmcg.FP32, 1e-4, (16, 0, 0, 3)),
+                                               (cmcg.FP32, 1e-4, (0, 0, 0, 4))])
 def test_full_size_period_sampled(full_size, precision, tol, tile):
     w, y0, v0 = full_size
     s = solver_of(w, precision, tile=tile)
@@ -341,6 +386,32 @@ def test_full_size_period_sampled(full_size, precision, tol, tile):
         assert abs(uT[sl][local] - yT[local]) <= tol * scale, (cidx, uT[sl][local], yT[local])
         scale_v = max(np.abs(vTo).max(), 1e-30)
         assert abs(vT[sl][local] - vTo[local]) <= tol * scale_v, cidx
+
+
+@pytest.mark.parametrize("tile", [(0, 0, 0, 3), (0, 0, 0, 4)])
+def test_full_size_step_kernels_agree(full_size, tile):
+    # the z-pair and bulk-copy kernels evaluate the single-step kernel's expression in the same
+    # order; their FP32 periods agree with it to rounding
+    w, y0, v0 = full_size
+    ref = [t.reshape(-1) for t in solver_of(w, cmcg.FP32, tile=(0, 0, 0, 1)).wave_period(y0, v0)]
+    out = [t.reshape(-1) for t in solver_of(w, cmcg.FP32, tile=tile).wave_period(y0, v0)]
+    adj_ref = [t.reshape(-1) for t in solver_of(w, cmcg.FP32, tile=(0, 0, 0, 1)).adjoint_period(y0, v0)]
+    adj = [t.reshape(-1) for t in solver_of(w, cmcg.FP32, tile=tile).adjoint_period(y0, v0)]
+    for a, b in zip(out + adj, ref + adj_ref):
+        assert float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) <= 1e-6
+    print("bitwise equal:", all(torch.equal(a, b) for a, b in zip(out + adj, ref + adj_ref)))
+
+
+def test_bulk_wait_times_out_and_context_survives():
+    # the bulk-copy kernel's mbarrier waits are bounded: a wait on a phase that nothing
+    # completes runs out and reports a time-out; the context stays usable afterwards
+    assert cmcg.cmcg_bulk_wait_selftest(2000) == cmcg.ERR_DEVICE_TIMEOUT
+    w = wl.sphere_3d(n=16)
+    dz = dz_of(w)
+    y0, v0 = rand_state(dz, 9)
+    yT, _ = wave.period(dz, y0, v0, None)
+    uT, _ = solver_of(w, cmcg.FP32, tile=(0, 0, 0, 4)).wave_period(y0, v0)
+    assert rel(uT.cpu().numpy(), yT) <= 2e-5
 
 
 def test_full_size_adjoint_dot(full_size):
