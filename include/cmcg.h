@@ -141,14 +141,16 @@ typedef struct {
                                relative tolerance of cmcg_solve refers to the residual of the
                                zero initial guess (one extra gradient evaluation), so the accuracy
                                at a given tol does not depend on the run-up.                  */
-    int tile[4];            /* launch shape of the leapfrog kernels, 0 = default: [0] z-planes
-                               per thread of the one-step 3D kernel (16), [1] z-planes per block
-                               of the two-step kernel (24), [2] maximum interior tile height of
-                               the two-step kernel (16, at most 16), [3] step scheme of FP32 3D
-                               7-point homogeneous steps: 0 or 1 = one step per launch, 2 = two
-                               steps per launch (temporal blocking), 3 = one step per launch with
-                               two z-planes per thread iteration.  Chosen per grid class by
-                               the autotuner (paper_1903_12522_gb300/autotune.py). */
+    int tile[4];            /* launch shape of the leapfrog kernels, 0 = default.  [3] selects
+                               the step scheme of 3D 7-point steps (the others keep one step per
+                               launch): 0 or 1 = one step per launch, [0] z-planes per thread
+                               (16); 2 = two FP32 steps per launch (temporal blocking), [1]
+                               z-planes per block (24), [2] maximum interior tile height (16, at
+                               most 16); 3 = one step per launch with [2] = 2 (default) or 4
+                               z-planes per loop iteration, [0] z-planes per thread; 4 = FP32
+                               steps with operands staged by TMA bulk copies, [0] z-planes per
+                               CTA and [1] rows per band (0 = automatic).  Chosen per grid
+                               class by the autotuner (paper_1903_12522_gb300/autotune.py). */
 } cmcg_options;
 
 typedef struct {

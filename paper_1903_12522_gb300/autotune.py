@@ -18,13 +18,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 
 def candidates_3d():
-    """cmcg_options.tile candidates: scheme 1 (one z-plane per loop trip) and 3 (two), tile[0] =
-    z-planes per thread; scheme 2 (two steps per launch), tile[1] = z-planes per block and
+    """cmcg_options.tile candidates: scheme 1 (one z-plane per loop trip) and 3 (two, or four
+    with tile[2] = 4), tile[0] = z-planes per thread; scheme 2 (two steps per launch), tile[1] = z-planes per block and
     tile[2] = tile height (the two shapes that ranked best on 257^3 and 513^3); scheme 4
     (bulk-copy staging), tile[0] = planes per CTA and tile[1] = band rows (0 = automatic)."""
     out = []
     for scheme in (1, 3):
         out += [(zc, 0, 0, scheme) for zc in (8, 16, 32)]
+    out += [(zc, 0, 4, 3) for zc in (8, 16, 32)]  # scheme 3 with four planes per loop iteration
     out += [(16, 12, 16, 2), (16, 24, 16, 2)]
     out += [(zc, ty, 0, 4) for zc in (0, 16, 32, 64) for ty in (0, 4, 8)]
     return out

@@ -76,6 +76,9 @@ __device__ __forceinline__ double e_weight(const Geom& g, const double* mass, co
 
 // One staggered leapfrog step for a column of z-planes (3D) or one node (2D).  SRC adds the
 // source at t_{n+1/2} (cs, sn already divided by dt); ACC accumulates v^n e^{i w t_n} into acc.
+// Consecutive lanes hold consecutive nodes of a row, so v_{j-1}, v_{j+1} and the old value of
+// the link (j - 1, j) come from the neighbouring lanes (lane 0 and lane 31 load them); lanes
+// past the last column take part in the shuffles but touch no memory.
 template <typename T, int DIM, bool SRC, bool ACC>
 __global__ void __launch_bounds__(kFT) k_fo_step(const T* __restrict__ sin_, T* __restrict__ sout,
                                                  const T* __restrict__ kap, const double* __restrict__ S, double cs,
@@ -83,12 +86,14 @@ __global__ void __launch_bounds__(kFT) k_fo_step(const T* __restrict__ sin_, T* 
                                                  double ca, double sa) {
     const long long plane = (long long)g.sx * g.sy;
     const long long pidx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pidx >= plane) return;
-    const int iy = (int)(pidx / g.sx);
-    const int ix = (int)(pidx - (long long)iy * g.sx);
+    const bool valid = pidx < plane;
+    const long long pc = valid ? pidx : plane - 1;  // in-range stand-in for idle lanes
+    const int iy = (int)(pc / g.sx);
+    const int ix = (int)(pc - (long long)iy * g.sx);
+    const int lane = threadIdx.x & 31;
     const int z0 = DIM == 3 ? (int)blockIdx.y * zc : 0;
     const int z1 = DIM == 3 ? min(z0 + zc, g.sz) : 1;
-    if (z0 >= z1) return;
+    if (z0 >= z1) return;  // uniform over the block
     const long long np = g.np;
     const long long sZ = plane;
     const T* px = sin_;
@@ -100,12 +105,14 @@ __global__ void __launch_bounds__(kFT) k_fo_step(const T* __restrict__ sin_, T* 
     T* qz = sout + 2 * np;
     T* w = sout + (long long)DIM * np;
     const T rx = (T)inv_w(ix, g.nx), ry = (T)inv_w(iy, g.ny);
+    const bool hx0 = ix > 0, hx1 = ix < g.nx, hy0 = iy > 0, hy1 = iy < g.ny;
     int nbxy = 0;
     nbxy += (ix == 0) & (int)(g.abc & 1u);
     nbxy += (ix == g.nx) & (int)((g.abc >> 1) & 1u);
     nbxy += (iy == 0) & (int)((g.abc >> 2) & 1u);
     nbxy += (iy == g.ny) & (int)((g.abc >> 3) & 1u);
-    long long j = (long long)ix + (long long)g.sx * iy + sZ * z0;
+    constexpr unsigned kAll = 0xffffffffu;
+    long long j = pc + sZ * z0;
     T vc = v[j];
     T pzl = T(0);  // new value of the z-link below (j - sZ, j)
     if (DIM == 3 && z0 > 0) pzl = pz[j - sZ] + tau * (vc - v[j - sZ]);
@@ -115,17 +122,23 @@ __global__ void __launch_bounds__(kFT) k_fo_step(const T* __restrict__ sin_, T* 
             vz = v[j + sZ];
             pzr = pz[j] + tau * (vz - vc);
         }
-        const T pxr = ix < g.nx ? px[j] + tau * (v[j + 1] - vc) : T(0);
-        const T pxl = ix > 0 ? px[j - 1] + tau * (vc - v[j - 1]) : T(0);
-        const T pyr = iy < g.ny ? py[j] + tau * (v[j + g.sx] - vc) : T(0);
-        const T pyl = iy > 0 ? py[j - g.sx] + tau * (vc - v[j - g.sx]) : T(0);
+        const T pxo = px[j];  // old value of the link (j, j + 1) (0 in the slot j_x = n_x)
+        const T vl = __shfl_up_sync(kAll, vc, 1), vr = __shfl_down_sync(kAll, vc, 1);
+        const T pl = __shfl_up_sync(kAll, pxo, 1);
+        const T vxm = hx0 ? (lane > 0 ? vl : v[j - 1]) : T(0);
+        const T vxp = hx1 ? (lane < 31 ? vr : v[j + 1]) : T(0);
+        const T pxlo = hx0 ? (lane > 0 ? pl : px[j - 1]) : T(0);
+        const T pxr = hx1 ? pxo + tau * (vxp - vc) : T(0);
+        const T pxl = hx0 ? pxlo + tau * (vc - vxm) : T(0);
+        const T pyr = hy1 ? py[j] + tau * (v[j + g.sx] - vc) : T(0);
+        const T pyl = hy0 ? py[j - g.sx] + tau * (vc - v[j - g.sx]) : T(0);
         T div = (pxl - pxr) * rx + (pyl - pyr) * ry;
         int nb = nbxy;
         if (DIM == 3) {
             div += (pzl - pzr) * (T)inv_w(iz, g.nz);
             nb += ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         }
-        const T k = kap[j];
+        const T k = __ldcs(kap + j);  // streamed: the fields are what the next step re-reads
         T out = T(0);
         if (k != T(0)) {
             const T beta = (T)nb * sqrt(k);
@@ -133,14 +146,16 @@ __global__ void __launch_bounds__(kFT) k_fo_step(const T* __restrict__ sin_, T* 
             if (SRC) rhs += (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
             out = nb == 0 ? rhs : rhs / (T(1) + beta);
         }
-        if (ACC) {
-            acc[2 * j] += (double)vc * ca;
-            acc[2 * j + 1] += (double)vc * sa;
+        if (valid) {
+            if (ACC) {
+                acc[2 * j] += (double)vc * ca;
+                acc[2 * j + 1] += (double)vc * sa;
+            }
+            qx[j] = pxr;
+            qy[j] = pyr;
+            if (DIM == 3) qz[j] = pzr;
+            w[j] = out;
         }
-        qx[j] = pxr;
-        qy[j] = pyr;
-        if (DIM == 3) qz[j] = pzr;
-        w[j] = out;
         if (DIM == 3) {
             pzl = pzr;
             vc = vz;

@@ -7,16 +7,17 @@
 // Work split: a CTA owns a band of ty full x-rows (y0 .. y1-1) and marches z over planes
 // z0 .. z1-1.  The rows of a band are one contiguous range of a plane, so each plane's operands
 // come in as one bulk copy per field:
-//   cur ring, kNC = 4 slots : rows y0-1 .. y1 of planes z-1, z, z+1 and the plane in flight
+//   cur ring, kNC = 5 slots : rows y0-1 .. y1 of planes z-1, z, z+1 and the two planes in flight
 //   prev / kappa rings, kNP = 3 slots : rows y0 .. y1-1 of planes z, z+1, z+2
 // A bulk copy starts and ends on 16-byte boundaries, so each copies the aligned superset of its
 // range (at most 3 floats either side) and the kernel indexes from the start's remainder.
 // Mirror neighbours at the faces (y = -1, y = ny + 1, z = -1, z = nz + 1) are read from the
 // mirrored row / plane, which the staged ranges contain.
 //
-// One thread (tid 0) initialises the barriers and issues every copy; all threads wait on a
-// slot's barrier (bounded spin) before reading it.  After a plane, a CTA barrier frees the
-// slots of plane z-1 (cur) and plane z (prev/kappa), which are refilled with planes z+3.  If a
+// One thread (tid 0) initialises the barriers and issues every copy; lane 0 of each warp waits
+// on a slot's barrier (bounded spin) and a warp barrier then releases its lanes.  After a
+// plane, a CTA barrier frees the slots of plane z-1 (cur) and plane z (prev/kappa), which are
+// refilled with planes z+4 and z+3.  If a
 // wait runs out, the kernel records CMCG_ERR_DEVICE_TIMEOUT in sc[SC_DEVERR], waits (again
 // bounded) for the copies it issued, and returns.
 #include <cuda_runtime.h>
@@ -31,8 +32,8 @@
 namespace cmcg {
 namespace {
 
-constexpr int kBT = 256;                  // threads per CTA
-constexpr int kNC = 4;                    // cur ring slots
+constexpr int kBT = 512;                  // threads per CTA
+constexpr int kNC = 5;                    // cur ring slots (two planes in flight)
 constexpr int kNP = 3;                    // prev / kappa ring slots
 constexpr int kBarBytes = 128;            // barrier + flag header of the shared memory
 constexpr int kWaitLimit = 1 << 22;       // try_wait polls before a wait counts as timed out
@@ -164,11 +165,16 @@ __global__ void __launch_bounds__(kBT) k_step3d7_bulk(const float* __restrict__ 
               ay1 = (int)((abc >> 3) & 1u), az0 = (int)((abc >> 4) & 1u), az1 = (int)((abc >> 5) & 1u);
     const int nout = nrow * sx;
 
+    const int lane = tid & 31;
     for (int z = z0; z < z1; ++z) {
-        const bool ready = mbar_wait(cur_bar(z - 1), cur_par(z - 1)) && mbar_wait(cur_bar(z), cur_par(z)) &&
-                           mbar_wait(cur_bar(z + 1), cur_par(z + 1)) && mbar_wait(p_bar(z), p_par(z));
-        if (!ready) {
-            *s_abort = 1;
+        if (lane == 0) {
+            const bool ready = mbar_wait(cur_bar(z - 1), cur_par(z - 1)) && mbar_wait(cur_bar(z), cur_par(z)) &&
+                               mbar_wait(cur_bar(z + 1), cur_par(z + 1)) && mbar_wait(p_bar(z), p_par(z));
+            if (!ready) *s_abort = 1;
+        }
+        __syncwarp();  // orders lane 0's completed waits before the other lanes' reads
+        if (*s_abort) {
+            // skip the plane; the CTA barrier below ends the march
         } else {
             const float* cm = s_cur + (size_t)((z - 1 - (z0 - 1)) % kNC) * cur_cap + cur_off(z - 1);
             const float* cc = s_cur + (size_t)((z - (z0 - 1)) % kNC) * cur_cap + cur_off(z);

@@ -33,6 +33,23 @@ struct PlaneMap {
     bool valid;
 };
 
+// 2D thread tiles: a block of tbx x (kThreads / tbx) threads covers that many columns of
+// consecutive rows, so most y-neighbour loads hit lines that the block's other warps load.
+__device__ __forceinline__ PlaneMap plane_map_tiled(const Geom& g, int zc, int tbx) {
+    PlaneMap m;
+    const int tby = kThreads / tbx;
+    const int ntx = (g.sx + tbx - 1) / tbx;
+    const int bx = (int)blockIdx.x % ntx, by = (int)blockIdx.x / ntx;
+    const int t = (int)threadIdx.x;
+    m.ix = bx * tbx + t % tbx;
+    m.iy = by * tby + t / tbx;
+    m.valid = m.ix < g.sx && m.iy < g.sy;
+    if (!m.valid) m.ix = m.iy = 0;
+    m.z0 = blockIdx.y * zc;
+    m.z1 = min(m.z0 + zc, g.sz);
+    return m;
+}
+
 __device__ __forceinline__ PlaneMap plane_map(const Geom& g, int zc) {
     PlaneMap m;
     const long long plane = (long long)g.sx * g.sy;
@@ -186,10 +203,79 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Leapfrog step, 3D 2nd order, two z-planes per loop iteration: both planes' loads are
-// issued before either update (more loads in flight per thread).
-template <typename T, int FLAGS>
+// issued before either update (more loads in flight per thread).  With pf > 0 each loop trip
+// also prefetches into L2 the y^n, y^{n-1} and kappa entries of the column pf planes ahead
+// (within the thread's chunk), which shortens the latency of the later loads.
+template <typename T, int FLAGS, bool PF = false>
 __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ cur, T* __restrict__ prev_out,
+                                                         const T* __restrict__ kap, const double* __restrict__ S,
+                                                         double cs, double sn, Geom g, int zc, int pf = 0,
+                                                         int tbx = 0) {
+    const PlaneMap m = tbx > 0 ? plane_map_tiled(g, zc, tbx) : plane_map(g, zc);
+    if (!m.valid || m.z0 >= m.z1) return;
+    const long long sZ = (long long)g.sx * g.sy;
+    long long j = node(g, m.ix, m.iy, m.z0);
+    const long long oxm = off_m1(m.ix, 1), oxp = off_p1(m.ix, g.nx, 1);
+    const long long oym = off_m1(m.iy, g.sx), oyp = off_p1(m.iy, g.ny, g.sx);
+    int nbxy = 0;
+    nbxy += (m.ix == 0) & (int)(g.abc & 1u);
+    nbxy += (m.ix == g.nx) & (int)((g.abc >> 1) & 1u);
+    nbxy += (m.iy == 0) & (int)((g.abc >> 2) & 1u);
+    nbxy += (m.iy == g.ny) & (int)((g.abc >> 3) & 1u);
+    auto update = [&](T yc, T ym, T yz, long long jj, int iz, T sxy, T k, T yp) {
+        const T L = T(6) * yc - (sxy + (ym + yz));
+        T rhs = T(2) * yc - k * L;
+        if (FLAGS & kStepSrc) rhs += (T)(S[2 * jj] * cs + S[2 * jj + 1] * sn);
+        const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
+        T out;
+        if (nb == 0) {
+            out = rhs - yp;
+        } else {
+            const T beta = (T)nb * sqrt(k);
+            const T v = rhs - ((FLAGS & kStepPrevScaled) ? yp : (T(1) - beta) * yp);
+            out = (FLAGS & kStepNoDiv) ? v : v / (T(1) + beta);
+        }
+        prev_out[jj] = out;
+    };
+    T ym = cur[j + (m.z0 > 0 ? -sZ : sZ)];
+    T yc = cur[j];
+    int iz = m.z0;
+    for (; iz + 1 < m.z1; iz += 2) {
+        if (PF && iz + pf + 2 < m.z1) {  // every prefetched plane lies inside the chunk
+            const long long jp = j + (long long)pf * sZ;
+            prefetch_l2(cur + jp + 2 * sZ);
+            prefetch_l2(prev_out + jp);
+            prefetch_l2(prev_out + jp + sZ);
+            prefetch_l2(kap + jp);
+            prefetch_l2(kap + jp + sZ);
+        }
+        const long long j1 = j + sZ;
+        const T y1 = cur[j1];                                    // plane iz+1 (exists: iz+1 < z1 <= sz)
+        const T y2 = cur[j1 + (iz + 1 < g.nz ? sZ : -sZ)];       // plane iz+2 (mirrored at the top)
+        const T s0 = (cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]);
+        const T s1 = (cur[j1 + oxm] + cur[j1 + oxp]) + (cur[j1 + oym] + cur[j1 + oyp]);
+        const T k0 = __ldcs(kap + j), k1 = __ldcs(kap + j1);
+        const T p0 = prev_out[j], p1 = prev_out[j1];
+        update(yc, ym, y1, j, iz, s0, k0, p0);
+        update(y1, yc, y2, j1, iz + 1, s1, k1, p1);
+        ym = y1;
+        yc = y2;
+        j += 2 * sZ;
+    }
+    if (iz < m.z1) {
+        const T yz = cur[j + (iz < g.nz ? sZ : -sZ)];
+        const T s0 = (cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]);
+        update(yc, ym, yz, j, iz, s0, __ldcs(kap + j), prev_out[j]);
+    }
+}
+
+// Leapfrog step, 3D 2nd order, K z-planes per loop iteration (K >= 2): all K planes' loads are
+// issued before any update.  Same expression, in the same order, as k_step3d7.
+template <typename T, int FLAGS, int K>
+__global__ void __launch_bounds__(kThreads) k_step3d7_zk(const T* __restrict__ cur, T* __restrict__ prev_out,
                                                          const T* __restrict__ kap, const double* __restrict__ S,
                                                          double cs, double sn, Geom g, int zc) {
     const PlaneMap m = plane_map(g, zc);
@@ -221,24 +307,39 @@ __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ c
     T ym = cur[j + (m.z0 > 0 ? -sZ : sZ)];
     T yc = cur[j];
     int iz = m.z0;
-    for (; iz + 1 < m.z1; iz += 2) {
-        const long long j1 = j + sZ;
-        const T y1 = cur[j1];                                    // plane iz+1 (exists: iz+1 < z1 <= sz)
-        const T y2 = cur[j1 + (iz + 1 < g.nz ? sZ : -sZ)];       // plane iz+2 (mirrored at the top)
-        const T s0 = (cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]);
-        const T s1 = (cur[j1 + oxm] + cur[j1 + oxp]) + (cur[j1 + oym] + cur[j1 + oyp]);
-        const T k0 = __ldcs(kap + j), k1 = __ldcs(kap + j1);
-        const T p0 = prev_out[j], p1 = prev_out[j1];
-        update(yc, ym, y1, j, iz, s0, k0, p0);
-        update(y1, yc, y2, j1, iz + 1, s1, k1, p1);
-        ym = y1;
-        yc = y2;
-        j += 2 * sZ;
+    for (; iz + K - 1 < m.z1; iz += K) {
+        T y[K + 1], sxy[K], kk[K], pp[K];
+        // planes iz+1 .. iz+K (the top one mirrored to nz-1 past the last plane)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int q = iz + k + 1;
+            y[k + 1] = cur[j + (long long)(q <= g.nz ? k + 1 : k - 1) * sZ];
+        }
+        y[0] = yc;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const long long jk = j + (long long)k * sZ;
+            sxy[k] = (cur[jk + oxm] + cur[jk + oxp]) + (cur[jk + oym] + cur[jk + oyp]);
+            kk[k] = __ldcs(kap + jk);
+            pp[k] = prev_out[jk];
+        }
+        T below = ym;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            update(y[k], below, y[k + 1], j + (long long)k * sZ, iz + k, sxy[k], kk[k], pp[k]);
+            below = y[k];
+        }
+        ym = y[K - 1];
+        yc = y[K];
+        j += (long long)K * sZ;
     }
-    if (iz < m.z1) {
+    for (; iz < m.z1; ++iz) {
         const T yz = cur[j + (iz < g.nz ? sZ : -sZ)];
         const T s0 = (cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]);
         update(yc, ym, yz, j, iz, s0, __ldcs(kap + j), prev_out[j]);
+        ym = yc;
+        yc = yz;
+        j += sZ;
     }
 }
 
@@ -790,8 +891,21 @@ inline dim3 plane_grid(const Geom& g, int zc) {
 template <typename T, int ORDER, int FLAGS>
 void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const double* S, double cs, double sn,
                    int zc, cudaStream_t st) {
-    // zc < 0 selects the two-planes-per-iteration variant of the 3D 7-point kernel
-    if (ORDER == 2 && g.dim == 3 && zc < 0) {
+    // zc < 0 selects the variants of the 3D 7-point kernel with several z-planes per loop
+    // iteration: -zc = planes per thread, plus kZk4 for four planes per iteration (else two),
+    // or plus kZpf * d for two planes per iteration with an L2 prefetch d planes ahead
+    if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZtile) {
+        const int z = (-zc) % kZtile, tbx = (-zc) / kZtile;
+        const int ntx = (g.sx + tbx - 1) / tbx, nty = (g.sy + kThreads / tbx - 1) / (kThreads / tbx);
+        const dim3 grid((unsigned)(ntx * nty), (unsigned)((g.sz + z - 1) / z));
+        k_step3d7_z2<T, FLAGS><<<grid, kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z, 0, tbx);
+    } else if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZpf) {
+        const int z = (-zc) % kZpf, d = (-zc) / kZpf;
+        k_step3d7_z2<T, FLAGS, true><<<plane_grid(g, z), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z, d);
+    } else if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZk4) {
+        const int z = -zc - kZk4;
+        k_step3d7_zk<T, FLAGS, 4><<<plane_grid(g, z), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z);
+    } else if (ORDER == 2 && g.dim == 3 && zc < 0) {
         k_step3d7_z2<T, FLAGS><<<plane_grid(g, -zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, -zc);
     } else if (ORDER == 2 && g.dim == 3) {
         k_step3d7<T, FLAGS><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, zc);

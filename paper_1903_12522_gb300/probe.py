@@ -36,7 +36,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("mode", choices=["period", "adjoint", "solve", "riesz", "obstacles", "fo-period", "fo-adjoint",
-                                     "fo-solve"])
+                                     "fo-solve", "stream"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=3)
@@ -50,6 +50,8 @@ def main():
     a = ap.parse_args()
     if a.mode == "obstacles":
         return obstacles(a.n)
+    if a.mode == "stream":
+        return stream(a.n, a.reps)
     prec = {"fp32": cmcg.FP32, "fp64": cmcg.FP64, "mixed": cmcg.MIXED}[a.precision]
     w = {"sphere": wl.sphere_3d, "layered": wl.layered_3d, "gauss2d": wl.gaussian_2d}[a.workload](n=a.n)
     fo = a.mode.startswith("fo-")
@@ -128,6 +130,35 @@ def obstacles(n: int, ells=(10, 25, 50, 100, 200, 400)):
                          "do_nothing_misfit": math.sqrt(max(s_dn["J_final"], 0.0)) / fnorm,
                          "cmcg_misfit": math.sqrt(max(s_cg["J_final"], 0.0)) / fnorm})
         print(json.dumps({"workload": w.name, "reference_cg_iterations": st["iterations"], "rows": rows}), flush=True)
+
+
+def stream(n: int, reps: int):
+    """Bandwidth calibration with PyTorch's own elementwise kernels on (n+1)^3 FP32 arrays: a
+    copy (1 read + 1 write) and p += a * b in place (3 reads + 1 write, the access mix of the
+    one-step leapfrog kernel without its neighbour loads).  Prints GB/s per pattern."""
+    import json
+
+    import torch
+
+    m = (n + 1) ** 3
+    a, b, p, q = [torch.rand(m, device="cuda", dtype=torch.float32) for _ in range(4)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    out = {}
+    for name, fn, nbytes in (("copy_1r1w", lambda: q.copy_(a), 8 * m), ("addcmul_3r1w", lambda: p.addcmul_(a, b), 16 * m)):
+        for _ in range(3):
+            fn()
+        times = []
+        for _ in range(max(reps, 5)):
+            flush.zero_()  # evict L2 between runs
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+        t = sorted(times)[len(times) // 2]
+        out[name] = {"us": t * 1e6, "GB_s": nbytes / t / 1e9}
+    print(json.dumps({"n": n, "nodes": m, "median": out}), flush=True)
 
 
 def _axis_weights(n: int) -> np.ndarray:
