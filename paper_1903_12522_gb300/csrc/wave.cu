@@ -82,6 +82,47 @@ struct DiffT {  // a[i] - b[i] in T
     __device__ __forceinline__ T operator()(long long i) const { return a[i] - b[i]; }
 };
 
+// Unscaled 7-point Laplacian of f along a thread's z-column, with the z-neighbours carried in
+// registers from plane to plane (mirror at the z faces).  Same sum, in the same order, as
+// lap_t<2> ((x- + x+) + (y- + y+)) + (z- + z+), so the results are bitwise equal.
+template <typename T, typename F>
+struct ColumnLap7 {
+    F f;
+    long long sZ, oxm, oxp, oym, oyp;
+    int nz;
+    T below, here, above;  // f at iz - 1, iz, iz + 1 (mirrored at the faces)
+    __device__ __forceinline__ void start(long long j, int iz) {
+        here = f(j);
+        below = f(j + (iz > 0 ? -sZ : sZ));
+        above = f(j + (iz < nz ? sZ : -sZ));
+    }
+    __device__ __forceinline__ T lap(long long j) const {
+        T acc = f(j + oxm) + f(j + oxp);
+        acc += f(j + oym) + f(j + oyp);
+        acc += below + above;
+        return T(6) * here - acc;
+    }
+    // move to plane iz + 1 (node j + sZ); valid while iz + 1 <= nz
+    __device__ __forceinline__ void advance(long long j, int iz) {
+        below = here;
+        here = above;
+        above = f(j + sZ + (iz + 1 < nz ? sZ : -sZ));
+    }
+};
+
+template <typename T, typename F>
+__device__ __forceinline__ ColumnLap7<T, F> column_lap(const Geom& g, F f, int ix, int iy) {
+    ColumnLap7<T, F> c;
+    c.f = f;
+    c.sZ = (long long)g.sx * g.sy;
+    c.oxm = off_m1(ix, 1);
+    c.oxp = off_p1(ix, g.nx, 1);
+    c.oym = off_m1(iy, g.sx);
+    c.oyp = off_p1(iy, g.ny, g.sx);
+    c.nz = g.nz;
+    return c;
+}
+
 // ---------------------------------------------------------------------------------------
 // Leapfrog step, generic (any dim / order): one thread per (x, y) column, marching z.
 template <typename T, int ORDER, int FLAGS>
@@ -417,24 +458,28 @@ __global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, c
                                                     const T* __restrict__ kap, const double* __restrict__ S,
                                                     Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
-    if (!m.valid) return;
+    if (!m.valid || m.z0 >= m.z1) return;
     Ld<T> f{w0t};
     const T dtT = (T)dt;
+    const bool col = ORDER == 2 && g.dim == 3;
+    auto cl = column_lap<T>(g, f, m.ix, m.iy);
+    if (col) cl.start(node(g, m.ix, m.iy, m.z0), m.z0);
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
         const T k = kap[j];
         if (k == T(0)) {
             y0[j] = T(0);
             y1[j] = T(0);
-            continue;
+        } else {
+            const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+            const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+            const T w0j = w0t[j];
+            T v = w0j + dtT * (T(1) - beta) * (T)w1[j] - T(0.5) * k * L;
+            if (SRC) v += (T)(0.5 * S[2 * j]);
+            y0[j] = w0j;
+            y1[j] = v;
         }
-        const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
-        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-        const T w0j = w0t[j];
-        T v = w0j + dtT * (T(1) - beta) * (T)w1[j] - T(0.5) * k * L;
-        if (SRC) v += (T)(0.5 * S[2 * j]);
-        y0[j] = w0j;
-        y1[j] = v;
+        if (col && iz + 1 < m.z1) cl.advance(j, iz);
     }
 }
 
@@ -448,20 +493,31 @@ __global__ void __launch_bounds__(kThreads) k_end(const T* __restrict__ yN, cons
                                                   Red red, Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
     double acc[1] = {0.0};
-    if (m.valid) {
+    if (m.valid && m.z0 < m.z1) {
         Ld<T> fy{yN};
         DiffT<T> fe{yN, w0t};
         const T ih2 = T(1) / (T)(g.h * g.h);
         const T dtT = (T)dt;
+        const bool col = ORDER == 2 && g.dim == 3;
+        auto cy = column_lap<T>(g, fy, m.ix, m.iy);
+        auto ce = column_lap<T>(g, fe, m.ix, m.iy);
+        if (col) {
+            cy.start(node(g, m.ix, m.iy, m.z0), m.z0);
+            if (MODE == 0) ce.start(node(g, m.ix, m.iy, m.z0), m.z0);
+        }
         for (int iz = m.z0; iz < m.z1; ++iz) {
             const long long j = node(g, m.ix, m.iy, iz);
             const T k = kap[j];
             if (k == T(0)) {
                 out0[j] = 0.0;
                 out1[j] = 0.0;
+                if (col && iz + 1 < m.z1) {
+                    cy.advance(j, iz);
+                    if (MODE == 0) ce.advance(j, iz);
+                }
                 continue;
             }
-            const T L = lap_t<ORDER, T>(g, fy, j, m.ix, m.iy, iz);
+            const T L = col ? cy.lap(j) : lap_t<ORDER, T>(g, fy, j, m.ix, m.iy, iz);
             const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
             T src = T(0);
             if (SRC) src = (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
@@ -474,11 +530,15 @@ __global__ void __launch_bounds__(kThreads) k_end(const T* __restrict__ yN, cons
                 const T e0 = yn - w0t[j];
                 const T e1 = vN - (T)w1[j];
                 const T W = weight_t<T>(g, m.ix, m.iy, iz);
-                const T z0 = W * ih2 * lap_t<ORDER, T>(g, fe, j, m.ix, m.iy, iz);
+                const T z0 = W * ih2 * (col ? ce.lap(j) : lap_t<ORDER, T>(g, fe, j, m.ix, m.iy, iz));
                 const T z1 = (T)mass[j] * e1;
                 out0[j] = (double)z0;
                 out1[j] = (double)z1;
                 acc[0] += 0.5 * (double)(e0 * z0 + e1 * z1);
+            }
+            if (col && iz + 1 < m.z1) {
+                cy.advance(j, iz);
+                if (MODE == 0) ce.advance(j, iz);
             }
         }
     }
@@ -513,23 +573,27 @@ __global__ void __launch_bounds__(kThreads) k_adj_start(const double* __restrict
                                                         T* __restrict__ cur, T* __restrict__ prev, Geom g, double dt,
                                                         int zc) {
     const PlaneMap m = plane_map(g, zc);
-    if (!m.valid) return;
+    if (!m.valid || m.z0 >= m.z1) return;
     Ld<T> f{t};
     const T dtT = (T)dt;
+    const bool col = ORDER == 2 && g.dim == 3;
+    auto cl = column_lap<T>(g, f, m.ix, m.iy);
+    if (col) cl.start(node(g, m.ix, m.iy, m.z0), m.z0);
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
         const T k = kap[j];
         if (k == T(0)) {
             cur[j] = T(0);
             prev[j] = T(0);
-            continue;
+        } else {
+            const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+            const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+            const T tj = t[j];
+            const T u = ((T)a[j] / (T)mass[j] + tj / dtT - k * L / (T(2) * dtT)) / (T(1) + beta);
+            cur[j] = u;
+            prev[j] = tj / dtT;
         }
-        const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
-        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-        const T tj = t[j];
-        const T u = ((T)a[j] / (T)mass[j] + tj / dtT - k * L / (T(2) * dtT)) / (T(1) + beta);
-        cur[j] = u;
-        prev[j] = tj / dtT;
+        if (col && iz + 1 < m.z1) cl.advance(j, iz);
     }
 }
 
@@ -547,10 +611,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
                                                         double* __restrict__ gt1, Red red, Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
     double acc[2] = {0.0, 0.0};
-    if (m.valid) {
+    if (m.valid && m.z0 < m.z1) {
         Ld<T> f{s};
         const T ih2 = T(1) / (T)(g.h * g.h);
         const T dtT = (T)dt;
+        const bool col = ORDER == 2 && g.dim == 3;
+        auto cl = column_lap<T>(g, f, m.ix, m.iy);
+        if (col) cl.start(node(g, m.ix, m.iy, m.z0), m.z0);
         for (int iz = m.z0; iz < m.z1; ++iz) {
             const long long j = node(g, m.ix, m.iy, iz);
             const T k = kap[j];
@@ -558,9 +625,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
                 o0[j] = 0.0;
                 o1[j] = 0.0;
                 if (MODE == 0) gt1[j] = 0.0;
+                if (col && iz + 1 < m.z1) cl.advance(j, iz);
                 continue;
             }
-            const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+            const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
             const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
             const T W = weight_t<T>(g, m.ix, m.iy, iz);
             const T M = (T)mass[j];
@@ -579,6 +647,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
                 acc[0] += g0 * d0[j] + g1 * d1[j];
                 acc[1] += g0;
             }
+            if (col && iz + 1 < m.z1) cl.advance(j, iz);
         }
     }
     if (MODE == 0) {
