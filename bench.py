@@ -199,8 +199,7 @@ def kernel_src_hash(name="k_step3d7("):
     fname = "step_bulk.cu" if "bulk" in name else "wave.cu"
     src = open(os.path.join(ROOT, "paper_1903_12522_gb300", "csrc", fname)).read()
     start = src.index(name)
-    ends = [src.find(m, start) for m in ("\ntemplate", "\n__global__", "\n// ----")]
-    end = min(e for e in ends if e >= 0)
+    end = src.index("\n}\n", start) + 2  # the kernel's closing brace
     return hashlib.sha256(src[start:end].encode()).hexdigest()
 
 

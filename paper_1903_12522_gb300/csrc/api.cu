@@ -233,13 +233,7 @@ PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool
 int step_zc(const cmcg_handle* H) {
     if (H->g.dim != 3) return 1;
     const int zc = H->opt.tile[0] > 0 ? H->opt.tile[0] : kZcStep3D;
-    if (H->order != 2) return zc;
-    if (H->opt.tile[3] == 5) return -(zc + kZpf * std::max(1, std::min(H->opt.tile[1], 64)));  // L2 prefetch distance
-    if (H->opt.tile[3] == 6) {  // 2D thread tiles tile[1] columns wide (32, 64 or 128)
-        const int tbx = H->opt.tile[1] == 64 || H->opt.tile[1] == 128 ? H->opt.tile[1] : 32;
-        return -(zc + kZtile * tbx);
-    }
-    if (H->opt.tile[3] != 3) return zc;
+    if (H->order != 2 || H->opt.tile[3] != 3) return zc;
     return H->opt.tile[2] == 4 ? -(zc + kZk4) : -zc;  // tile[2]: planes per loop iteration (2 or 4)
 }
 
@@ -1098,7 +1092,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     if (H->has_dir && H->sumW <= 0) return fail(CMCG_ERR_INVALID_ARG);
     if (o.runup_periods < -1 || o.runup_periods > 100000) return fail(CMCG_ERR_INVALID_ARG);
     if (o.tile[0] < 0 || o.tile[0] > 512 || o.tile[1] < 0 || o.tile[1] > 512 || o.tile[2] < 0 || o.tile[2] > 16 ||
-        o.tile[3] < 0 || o.tile[3] > 6)
+        o.tile[3] < 0 || o.tile[3] > 4)
         return fail(CMCG_ERR_INVALID_ARG);
     // time step: N = ceil(T / dt_target - 1e-9), dt = T / N
     const double dt_target = o.dt > 0 ? o.dt : 0.5 * grid->h / (sqrt((double)grid->dim) * cmax);

@@ -18,12 +18,6 @@ struct Red {
 enum StepFlags { kStepSrc = 1, kStepPrevScaled = 2, kStepNoDiv = 4 };
 // Added to the (negated) planes-per-thread of a step launch: four z-planes per loop iteration.
 constexpr int kZk4 = 1 << 12;
-// Multiplied by the prefetch distance and added to the (negated) planes-per-thread: the two-plane
-// kernel with an L2 prefetch that many planes ahead.
-constexpr int kZpf = 1 << 13;
-// Multiplied by the tile width (32, 64 or 128 columns) and added to the (negated) planes-per-thread:
-// the two-plane kernel on 2D thread tiles.  Larger than kZpf * 64.
-constexpr int kZtile = 1 << 20;
 
 // Process-wide count of kernels launched by this library (every launcher records its launches).
 void note_launch(long long k);

@@ -33,23 +33,6 @@ struct PlaneMap {
     bool valid;
 };
 
-// 2D thread tiles: a block of tbx x (kThreads / tbx) threads covers that many columns of
-// consecutive rows, so most y-neighbour loads hit lines that the block's other warps load.
-__device__ __forceinline__ PlaneMap plane_map_tiled(const Geom& g, int zc, int tbx) {
-    PlaneMap m;
-    const int tby = kThreads / tbx;
-    const int ntx = (g.sx + tbx - 1) / tbx;
-    const int bx = (int)blockIdx.x % ntx, by = (int)blockIdx.x / ntx;
-    const int t = (int)threadIdx.x;
-    m.ix = bx * tbx + t % tbx;
-    m.iy = by * tby + t / tbx;
-    m.valid = m.ix < g.sx && m.iy < g.sy;
-    if (!m.valid) m.ix = m.iy = 0;
-    m.z0 = blockIdx.y * zc;
-    m.z1 = min(m.z0 + zc, g.sz);
-    return m;
-}
-
 __device__ __forceinline__ PlaneMap plane_map(const Geom& g, int zc) {
     PlaneMap m;
     const long long plane = (long long)g.sx * g.sy;
@@ -244,18 +227,13 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
     }
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
 // Leapfrog step, 3D 2nd order, two z-planes per loop iteration: both planes' loads are
-// issued before either update (more loads in flight per thread).  With pf > 0 each loop trip
-// also prefetches into L2 the y^n, y^{n-1} and kappa entries of the column pf planes ahead
-// (within the thread's chunk), which shortens the latency of the later loads.
-template <typename T, int FLAGS, bool PF = false>
+// issued before either update (more loads in flight per thread).
+template <typename T, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ cur, T* __restrict__ prev_out,
                                                          const T* __restrict__ kap, const double* __restrict__ S,
-                                                         double cs, double sn, Geom g, int zc, int pf = 0,
-                                                         int tbx = 0) {
-    const PlaneMap m = tbx > 0 ? plane_map_tiled(g, zc, tbx) : plane_map(g, zc);
+                                                         double cs, double sn, Geom g, int zc) {
+    const PlaneMap m = plane_map(g, zc);
     if (!m.valid || m.z0 >= m.z1) return;
     const long long sZ = (long long)g.sx * g.sy;
     long long j = node(g, m.ix, m.iy, m.z0);
@@ -285,14 +263,6 @@ __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ c
     T yc = cur[j];
     int iz = m.z0;
     for (; iz + 1 < m.z1; iz += 2) {
-        if (PF && iz + pf + 2 < m.z1) {  // every prefetched plane lies inside the chunk
-            const long long jp = j + (long long)pf * sZ;
-            prefetch_l2(cur + jp + 2 * sZ);
-            prefetch_l2(prev_out + jp);
-            prefetch_l2(prev_out + jp + sZ);
-            prefetch_l2(kap + jp);
-            prefetch_l2(kap + jp + sZ);
-        }
         const long long j1 = j + sZ;
         const T y1 = cur[j1];                                    // plane iz+1 (exists: iz+1 < z1 <= sz)
         const T y2 = cur[j1 + (iz + 1 < g.nz ? sZ : -sZ)];       // plane iz+2 (mirrored at the top)
@@ -493,31 +463,20 @@ __global__ void __launch_bounds__(kThreads) k_end(const T* __restrict__ yN, cons
                                                   Red red, Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
     double acc[1] = {0.0};
-    if (m.valid && m.z0 < m.z1) {
+    if (m.valid) {
         Ld<T> fy{yN};
         DiffT<T> fe{yN, w0t};
         const T ih2 = T(1) / (T)(g.h * g.h);
         const T dtT = (T)dt;
-        const bool col = ORDER == 2 && g.dim == 3;
-        auto cy = column_lap<T>(g, fy, m.ix, m.iy);
-        auto ce = column_lap<T>(g, fe, m.ix, m.iy);
-        if (col) {
-            cy.start(node(g, m.ix, m.iy, m.z0), m.z0);
-            if (MODE == 0) ce.start(node(g, m.ix, m.iy, m.z0), m.z0);
-        }
         for (int iz = m.z0; iz < m.z1; ++iz) {
             const long long j = node(g, m.ix, m.iy, iz);
             const T k = kap[j];
             if (k == T(0)) {
                 out0[j] = 0.0;
                 out1[j] = 0.0;
-                if (col && iz + 1 < m.z1) {
-                    cy.advance(j, iz);
-                    if (MODE == 0) ce.advance(j, iz);
-                }
                 continue;
             }
-            const T L = col ? cy.lap(j) : lap_t<ORDER, T>(g, fy, j, m.ix, m.iy, iz);
+            const T L = lap_t<ORDER, T>(g, fy, j, m.ix, m.iy, iz);
             const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
             T src = T(0);
             if (SRC) src = (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
@@ -530,15 +489,11 @@ __global__ void __launch_bounds__(kThreads) k_end(const T* __restrict__ yN, cons
                 const T e0 = yn - w0t[j];
                 const T e1 = vN - (T)w1[j];
                 const T W = weight_t<T>(g, m.ix, m.iy, iz);
-                const T z0 = W * ih2 * (col ? ce.lap(j) : lap_t<ORDER, T>(g, fe, j, m.ix, m.iy, iz));
+                const T z0 = W * ih2 * lap_t<ORDER, T>(g, fe, j, m.ix, m.iy, iz);
                 const T z1 = (T)mass[j] * e1;
                 out0[j] = (double)z0;
                 out1[j] = (double)z1;
                 acc[0] += 0.5 * (double)(e0 * z0 + e1 * z1);
-            }
-            if (col && iz + 1 < m.z1) {
-                cy.advance(j, iz);
-                if (MODE == 0) ce.advance(j, iz);
             }
         }
     }
@@ -573,27 +528,23 @@ __global__ void __launch_bounds__(kThreads) k_adj_start(const double* __restrict
                                                         T* __restrict__ cur, T* __restrict__ prev, Geom g, double dt,
                                                         int zc) {
     const PlaneMap m = plane_map(g, zc);
-    if (!m.valid || m.z0 >= m.z1) return;
+    if (!m.valid) return;
     Ld<T> f{t};
     const T dtT = (T)dt;
-    const bool col = ORDER == 2 && g.dim == 3;
-    auto cl = column_lap<T>(g, f, m.ix, m.iy);
-    if (col) cl.start(node(g, m.ix, m.iy, m.z0), m.z0);
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
         const T k = kap[j];
         if (k == T(0)) {
             cur[j] = T(0);
             prev[j] = T(0);
-        } else {
-            const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
-            const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-            const T tj = t[j];
-            const T u = ((T)a[j] / (T)mass[j] + tj / dtT - k * L / (T(2) * dtT)) / (T(1) + beta);
-            cur[j] = u;
-            prev[j] = tj / dtT;
+            continue;
         }
-        if (col && iz + 1 < m.z1) cl.advance(j, iz);
+        const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+        const T tj = t[j];
+        const T u = ((T)a[j] / (T)mass[j] + tj / dtT - k * L / (T(2) * dtT)) / (T(1) + beta);
+        cur[j] = u;
+        prev[j] = tj / dtT;
     }
 }
 
@@ -961,17 +912,8 @@ template <typename T, int ORDER, int FLAGS>
 void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const double* S, double cs, double sn,
                    int zc, cudaStream_t st) {
     // zc < 0 selects the variants of the 3D 7-point kernel with several z-planes per loop
-    // iteration: -zc = planes per thread, plus kZk4 for four planes per iteration (else two),
-    // or plus kZpf * d for two planes per iteration with an L2 prefetch d planes ahead
-    if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZtile) {
-        const int z = (-zc) % kZtile, tbx = (-zc) / kZtile;
-        const int ntx = (g.sx + tbx - 1) / tbx, nty = (g.sy + kThreads / tbx - 1) / (kThreads / tbx);
-        const dim3 grid((unsigned)(ntx * nty), (unsigned)((g.sz + z - 1) / z));
-        k_step3d7_z2<T, FLAGS><<<grid, kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z, 0, tbx);
-    } else if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZpf) {
-        const int z = (-zc) % kZpf, d = (-zc) / kZpf;
-        k_step3d7_z2<T, FLAGS, true><<<plane_grid(g, z), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z, d);
-    } else if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZk4) {
+    // iteration: -zc = planes per thread, plus kZk4 for four planes per iteration (else two)
+    if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZk4) {
         const int z = -zc - kZk4;
         k_step3d7_zk<T, FLAGS, 4><<<plane_grid(g, z), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z);
     } else if (ORDER == 2 && g.dim == 3 && zc < 0) {

@@ -137,8 +137,7 @@ def test_adjoint_period(case, precision, tol):
 
 
 @pytest.mark.parametrize("tile", [(0, 0, 0, 2), (0, 8, 8, 2), (0, 3, 16, 2), (16, 0, 0, 3), (3, 0, 0, 3),
-                                  (0, 0, 0, 4), (3, 0, 0, 4), (0, 2, 0, 4), (5, 1, 0, 4), (16, 0, 4, 3), (5, 0, 4, 3), (16, 4, 0, 5), (6, 1, 0, 5),
-                                  (8, 32, 0, 6), (5, 64, 0, 6), (16, 128, 0, 6)])
+                                  (0, 0, 0, 4), (3, 0, 0, 4), (0, 2, 0, 4), (5, 1, 0, 4), (16, 0, 4, 3), (5, 0, 4, 3)])
 def test_step_scheme_variants(case, tile):
     # FP32 periods with the alternative step kernels: two steps per launch (temporal blocking,
     # scheme 2), two z-planes per thread iteration (scheme 3), and operands staged by bulk
@@ -389,7 +388,7 @@ def test_full_size_period_sampled(full_size, precision, tol, tile):
         assert abs(vT[sl][local] - vTo[local]) <= tol * scale_v, cidx
 
 
-@pytest.mark.parametrize("tile", [(0, 0, 0, 3), (0, 0, 0, 4), (16, 0, 4, 3), (16, 4, 0, 5), (8, 32, 0, 6)])
+@pytest.mark.parametrize("tile", [(0, 0, 0, 3), (0, 0, 0, 4), (16, 0, 4, 3)])
 def test_full_size_step_kernels_agree(full_size, tile):
     # the z-pair and bulk-copy kernels evaluate the single-step kernel's expression in the same
     # order; their FP32 periods agree with it to rounding
