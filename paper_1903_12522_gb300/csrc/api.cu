@@ -557,13 +557,14 @@ bool inexact(const cmcg_handle* H) { return (H->opt.flags & CMCG_FLAG_INEXACT_RI
 
 // Approximate Riesz map z = B rhat into (r0, r1): one V-cycle on rhat0 (W-mean removed when K
 // is singular), M^-1 rhat1; reduces gamma = z . rhat (and the Polak-Ribiere beta unless first).
-void apply_B(cmcg_handle* H, bool first) {
+// lowp: inside a solve with FP32 periods, the pointwise work and the dots run in FP32.
+void apply_B(cmcg_handle* H, bool first, bool lowp) {
     const Geom& g = H->g;
     Red red = H->red();
     launch_to_float(g.np, H->rh0, H->lv[0].b, H->st);
     vcycle(H, 0);
     if (!H->has_dir) launch_wsum_float(g, H->lv[0].x, red, H->st);
-    launch_fcg_dots(g, H->lv[0].x, H->volume, !H->has_dir, H->rh0, H->rh1, H->minv, H->gh0, H->gh1, H->r0, H->r1,
+    launch_fcg_dots(g, H->lv[0].x, H->volume, !H->has_dir, lowp, H->rh0, H->rh1, H->minv, H->gh0, H->gh1, H->r0, H->r1,
                     red, first, H->st);
     H->riesz_iters += 1;
 }
@@ -576,7 +577,7 @@ int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_o
     Red red = H->red();
     cudaMemcpyAsync(H->rh0, H->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
     cudaMemcpyAsync(H->rh1, H->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
-    apply_B(H, true);
+    apply_B(H, true, std::is_same<T, float>::value);
     cudaMemcpyAsync(H->d0, H->r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
     cudaMemcpyAsync(H->d1, H->r1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
     int rc = sync_read(H);
@@ -588,7 +589,7 @@ int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_o
         for (it = 1; it <= max_iter; ++it) {
             gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1, false);        // 5.1: ghat_d = H d
             launch_fcg_update(n, H->w0, H->w1, H->rh0, H->rh1, H->d0, H->d1, H->gh0, H->gh1, red, H->st);
-            apply_B(H, false);                                             // 5.2 on the residual
+            apply_B(H, false, std::is_same<T, float>::value);              // 5.2 on the residual
             launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st);  // 5.7
             rc = sync_read(H);
             if (rc != CMCG_OK) return rc;
@@ -610,7 +611,7 @@ int gradient_norm(cmcg_handle* H, double* gamma) {
     if (inexact(H)) {
         cudaMemcpyAsync(H->rh0, H->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
         cudaMemcpyAsync(H->rh1, H->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
-        apply_B(H, true);
+        apply_B(H, true, false);
         launch_scalar_residual(n, H->r0, H->r1, H->rh0, H->rh1, red, SC_R7, H->st);
     } else {
         launch_scalar_residual(n, H->gt0, H->gt1, H->gh0, H->gh1, red, SC_R7, H->st);
@@ -727,7 +728,7 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
         if (inexact(H)) {
             cudaMemcpyAsync(H->rh0, H->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
             cudaMemcpyAsync(H->rh1, H->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
-            apply_B(H, true);
+            apply_B(H, true, false);
             launch_scalar_residual(n, H->r0, H->r1, H->rh0, H->rh1, red, SC_R7, H->st);
         } else {
             launch_scalar_residual(n, H->gt0, H->gt1, H->gh0, H->gh1, red, SC_R7, H->st);

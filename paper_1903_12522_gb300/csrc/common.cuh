@@ -186,6 +186,19 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsi
     return true;
 }
 
+// Compensated (Kahan) FP32 running sum: a thread's partial sum of FP32 products without
+// FP64 arithmetic (GB300 issues FP64 at 1/64 of the FP32 rate); converted to double once.
+struct KahanF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // Device scalar slots of the CG recurrences (double sc[]).
 enum Slot {
     SC_GAMMA = 0,    // gamma = r . rhat = ||r||_E^2

@@ -116,7 +116,7 @@ void reset_direction(cmcg_handle* h) {
     const long long n = h->g.np;
     cudaMemcpyAsync(h->rh0, h->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
     cudaMemcpyAsync(h->rh1, h->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
-    apply_B(h, true);
+    apply_B(h, true, false);
     cudaMemcpyAsync(h->d0, h->r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
     cudaMemcpyAsync(h->d1, h->r1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
 }
@@ -214,7 +214,7 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
                                hh->gt1);
                 launch_fcg_update(n, hh->w0, hh->w1, hh->rh0, hh->rh1, hh->d0, hh->d1, hh->gh0, hh->gh1, hh->red(),
                                   hh->st);
-                apply_B(hh, false);
+                apply_B(hh, false, true);
                 launch_cg_direction(n, hh->r0, hh->r1, hh->d0, hh->d1, hh->red(), hh->st);
             });
         }

@@ -115,7 +115,8 @@ void launch_reciprocal(long long n, const double* m, double* out, cudaStream_t s
 // Flexible CG with an approximate Riesz map (one multigrid V-cycle).
 void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double* rh1, const double* d0,
                        const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st);
-void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, const double* rh0,
+// lowp: FP32 arithmetic with compensated FP32 partial sums (inside an FP32-period solve).
+void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, bool lowp, const double* rh0,
                      const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,
                      double* z1, Red red, bool first, cudaStream_t st);
 void launch_wsum_float(const Geom& g, const float* x, Red red, cudaStream_t st);

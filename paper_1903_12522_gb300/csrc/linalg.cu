@@ -315,18 +315,37 @@ __global__ void __launch_bounds__(kT) k_fcg_dots(Geom g, const float* __restrict
                                                  const double* __restrict__ rh1, const double* __restrict__ minv,
                                                  const double* __restrict__ gh0, const double* __restrict__ gh1,
                                                  double* __restrict__ z0, double* __restrict__ z1, Red red,
-                                                 int first) {
+                                                 int first, int lowp) {
     const double mu = remove_mean ? red.sc[SC_P_XW] * inv_volume : 0.0;
     double acc[2] = {0.0, 0.0};
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
-        const double m = minv[j];
-        const double a0 = m != 0.0 ? (double)zf[j] - mu : 0.0;
-        const double a1 = rh1[j] * m;
-        z0[j] = a0;
-        z1[j] = a1;
-        acc[0] += a0 * rh0[j] + a1 * rh1[j];
-        if (!first) acc[1] += a0 * gh0[j] + a1 * gh1[j];
+    if (lowp) {
+        // inside an FP32-period solve: the same quantities with FP32 arithmetic and
+        // compensated FP32 partial sums (no FP64 arithmetic per node)
+        KahanF s0, s1;
+        const float muf = (float)mu;
+        for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
+            const float m = (float)minv[j];
+            const float a0 = m != 0.0f ? zf[j] - muf : 0.0f;
+            const float r1 = (float)rh1[j];
+            const float a1 = r1 * m;
+            z0[j] = (double)a0;
+            z1[j] = (double)a1;
+            s0.add(a0 * (float)rh0[j] + a1 * r1);
+            if (!first) s1.add(a0 * (float)gh0[j] + a1 * (float)gh1[j]);
+        }
+        acc[0] = s0.value();
+        acc[1] = s1.value();
+    } else {
+        for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
+            const double m = minv[j];
+            const double a0 = m != 0.0 ? (double)zf[j] - mu : 0.0;
+            const double a1 = rh1[j] * m;
+            z0[j] = a0;
+            z1[j] = a1;
+            acc[0] += a0 * rh0[j] + a1 * rh1[j];
+            if (!first) acc[1] += a0 * gh0[j] + a1 * gh1[j];
+        }
     }
     if (grid_sum<2>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
         const double gnew = acc[0];
@@ -448,12 +467,12 @@ void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double*
     k_fcg_update<<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, rh0, rh1, d0, d1, gh0, gh1, red.sc);
 }
 
-void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, const double* rh0,
+void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, bool lowp, const double* rh0,
                      const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,
                      double* z1, Red red, bool first, cudaStream_t st) {
     note_launch(1);
     k_fcg_dots<<<vec_blocks(g.np), kT, 0, st>>>(g, zf, 1.0 / volume, remove_mean ? 1 : 0, rh0, rh1, minv, gh0, gh1,
-                                                z0, z1, red, first ? 1 : 0);
+                                                z0, z1, red, first ? 1 : 0, lowp ? 1 : 0);
 }
 
 void launch_wsum_float(const Geom& g, const float* x, Red red, cudaStream_t st) {

@@ -84,7 +84,7 @@ struct PeriodBuffers {
 int cuda_status();
 int sync_read(cmcg_handle* H);
 bool inexact(const cmcg_handle* H);
-void apply_B(cmcg_handle* H, bool first);
+void apply_B(cmcg_handle* H, bool first, bool lowp);
 int adj_step_flags(int k, int N);
 template <typename T>
 PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool src);

@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -463,6 +464,7 @@ __global__ void __launch_bounds__(kThreads) k_end(const T* __restrict__ yN, cons
                                                   Red red, Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
     double acc[1] = {0.0};
+    KahanF accf;  // FP32 periods: the thread's part of J without FP64 arithmetic
     if (m.valid) {
         Ld<T> fy{yN};
         DiffT<T> fe{yN, w0t};
@@ -493,11 +495,15 @@ __global__ void __launch_bounds__(kThreads) k_end(const T* __restrict__ yN, cons
                 const T z1 = (T)mass[j] * e1;
                 out0[j] = (double)z0;
                 out1[j] = (double)z1;
-                acc[0] += 0.5 * (double)(e0 * z0 + e1 * z1);
+                if (std::is_same<T, float>::value)
+                    accf.add((float)(e0 * z0 + e1 * z1));
+                else
+                    acc[0] += 0.5 * (double)(e0 * z0 + e1 * z1);
             }
         }
     }
     if (MODE == 0) {
+        if (std::is_same<T, float>::value) acc[0] = 0.5 * accf.value();
         if (grid_sum<1>(acc, red.partials, red.ticket) && threadIdx.x == 0) red.sc[SC_J] = acc[0];
     }
 }
@@ -562,6 +568,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
                                                         double* __restrict__ gt1, Red red, Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
     double acc[2] = {0.0, 0.0};
+    KahanF accf0, accf1;
     if (m.valid && m.z0 < m.z1) {
         Ld<T> f{s};
         const T ih2 = T(1) / (T)(g.h * g.h);
@@ -589,6 +596,16 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
             if (MODE == 1) {
                 o0[j] = (double)q0;
                 o1[j] = (double)q1;
+            } else if (std::is_same<T, float>::value) {
+                // FP32 periods: z came from FP32 values, so the differences and products stay in
+                // FP32 (FP64 only holds the stored vectors)
+                const float g0 = (float)q0 - (float)z0[j];
+                const float g1 = (float)q1 - (float)z1[j];
+                o0[j] = (double)g0;
+                o1[j] = (double)g1;
+                gt1[j] = (double)(g1 * (float)minv[j]);
+                accf0.add(g0 * (float)d0[j] + g1 * (float)d1[j]);
+                accf1.add(g0);
             } else {
                 const double g0 = (double)q0 - z0[j];
                 const double g1 = (double)q1 - z1[j];
@@ -602,6 +619,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
         }
     }
     if (MODE == 0) {
+        if (std::is_same<T, float>::value) {
+            acc[0] = accf0.value();
+            acc[1] = accf1.value();
+        }
         if (grid_sum<2>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
             red.sc[SC_GD] = acc[0];
             red.sc[SC_GSUM] = acc[1];

@@ -47,6 +47,7 @@ def main():
     ap.add_argument("--runup", type=int, default=0)
     ap.add_argument("--tile", type=int, nargs=4, default=None, help="cmcg_options.tile (default: autotuned)")
     ap.add_argument("--inner-tol", type=float, default=0.0)
+    ap.add_argument("--filter", action="store_true", help="recover U by the fundamental-frequency filter")
     a = ap.parse_args()
     if a.mode == "obstacles":
         return obstacles(a.n)
@@ -56,6 +57,8 @@ def main():
     w = {"sphere": wl.sphere_3d, "layered": wl.layered_3d, "gauss2d": wl.gaussian_2d}[a.workload](n=a.n)
     fo = a.mode.startswith("fo-")
     flags = cmcg.FLAG_FIRST_ORDER if fo else (cmcg.FLAG_INEXACT_RIESZ if a.inexact else 0)
+    if a.filter:
+        flags |= cmcg.FLAG_FILTER
     s = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, order=w.order, precision=prec, dt=w.dt_target,
                     max_iter=a.max_iter, flags=flags, runup_periods=a.runup, tile=None if fo else a.tile,
                     inner_tol=a.inner_tol)
