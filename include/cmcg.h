@@ -78,7 +78,7 @@ extern "C" {
 #define CMCG_FLAG_NO_CG 16  /* "do-nothing" long-time solver of Sec. 4.2 (Eq. AP_SOLUTION), the
                                comparator the paper uses to show why controllability is needed:
                                integrate the forced wave equation from rest for runup_periods = l
-                               periods (or the automatic count for -1; 0 is CMCG_ERR_INVALID_ARG)
+                               periods (or the automatic count for -k; 0 is CMCG_ERR_INVALID_ARG)
                                with the sources ramped by theta_tr over [0, l T] (Sec. 4.3) and
                                recover U from the state at t = l T as in step (6), without CG.
                                Near trapped modes (nonconvex obstacles) U converges very slowly
@@ -96,9 +96,9 @@ extern "C" {
                                FP32 CG, as for the second-order scheme; with FP32 periods use
                                CMCG_FLAG_FILTER: rounding excites the nearly periodic spurious
                                modes of Sec. 3.3, which Eq. mix_solution keeps and the filter
-                               removes), order 2, no run-up;
-                               order 4, runup_periods != 0, CMCG_FLAG_INEXACT_RIESZ and
-                               CMCG_FLAG_NO_CG are CMCG_ERR_UNSUPPORTED.  cmcg_wave_period, cmcg_adjoint_period and
+                               removes), order 2, and the run-up of Sec. 4.3 (runup_periods);
+                               order 4, CMCG_FLAG_INEXACT_RIESZ and CMCG_FLAG_NO_CG are
+                               CMCG_ERR_UNSUPPORTED.  cmcg_wave_period, cmcg_adjoint_period and
                                cmcg_riesz return CMCG_ERR_UNSUPPORTED on such a handle; use
                                cmcg_fo_period and cmcg_fo_adjoint_period. */
 
@@ -137,7 +137,9 @@ typedef struct {
                                for this many periods with the sources ramped in by
                                theta(t) = (2 - sin(pi t / (2 t_tr))) sin(pi t / (2 t_tr)),
                                t_tr = runup_periods T, and start CG from the final state.
-                               0 = none; -1 = ceil(diam(Omega) / (T c_min)).  With a run-up, the
+                               0 = none; -k (1 <= k <= 64) = ceil(k diam(Omega) / (T c_min)),
+                               the periods waves at the slowest speed need to cross the
+                               domain's diagonal k times.  With a run-up, the
                                relative tolerance of cmcg_solve refers to the residual of the
                                zero initial guess (one extra gradient evaluation), so the accuracy
                                at a given tol does not depend on the run-up.                  */
@@ -271,8 +273,10 @@ int cmcg_bulk_wait_selftest(int spin_limit, void* stream);
  * a CUDA graph and replayed while the set of active solves and their phases stay the same.
  * Solves finish independently; a finished solve's result is read with cmcg_engine_result,
  * which frees its slot.  Requirements: every handle uses the engine's stream, precision
- * CMCG_FP32 or CMCG_MIXED and CMCG_FLAG_INEXACT_RIESZ, and neither CMCG_FLAG_FILTER nor
- * CMCG_FLAG_NO_CG (else CMCG_ERR_UNSUPPORTED).  The
+ * CMCG_FP32 or CMCG_MIXED and CMCG_FLAG_INEXACT_RIESZ, none of CMCG_FLAG_FILTER,
+ * CMCG_FLAG_NO_CG and CMCG_FLAG_FIRST_ORDER, and a run-up only with CMCG_MIXED (else
+ * CMCG_ERR_UNSUPPORTED).  A mixed-precision slot with runup_periods != 0 runs its run-up as one
+ * unit after the zero guess's outer gradient (the tolerance reference).  The
  * batched kernel is a cooperative launch whose grid barrier waits are bounded; a wait that
  * runs out returns CMCG_ERR_DEVICE_TIMEOUT from cmcg_engine_tick. */
 typedef struct cmcg_engine cmcg_engine;

@@ -402,12 +402,15 @@ void adjoint_period(cmcg_handle* H, const double* a, const double* bb, int mode,
 }
 
 // ---- initial run-up (Sec. 4.3) ---------------------------------------------------------------
+// Run-up periods: runup_periods itself when positive; -k = the periods waves at the slowest
+// speed need to cross the domain's diagonal k times, ceil(k diam / (T c_min)).
 int runup_count(const cmcg_handle* H) {
     if (H->opt.runup_periods > 0) return H->opt.runup_periods;
     if (H->opt.runup_periods == 0) return 0;
     double d2 = (double)H->g.nx * H->g.nx + (double)H->g.ny * H->g.ny + (double)H->g.nz * H->g.nz;
     const double diam = H->g.h * sqrt(d2);
-    return std::max(1, (int)ceil(diam / (H->T * H->cmin)));
+    const double crossings = -(double)H->opt.runup_periods;
+    return std::max(1, (int)ceil(crossings * diam / (H->T * H->cmin) - 1e-9));
 }
 
 // theta_tr(t) = (2 - sin(pi t / (2 t_tr))) sin(pi t / (2 t_tr)) for t <= t_tr, 1 after.
@@ -917,6 +920,7 @@ template void adj_end<float>(cmcg_handle*, const PeriodBuffers&, const double*, 
                              const double*, double*, double*, double*);
 template void adj_end<double>(cmcg_handle*, const PeriodBuffers&, const double*, const double*, int, const double*,
                               const double*, double*, double*, double*);
+template void runup<float>(cmcg_handle*, int, double*, double*);
 template int gradient<double>(cmcg_handle*, const double*, const double*, bool, const double*, const double*, bool);
 template int gradient<float>(cmcg_handle*, const double*, const double*, bool, const double*, const double*, bool);
 template void forward_period<double>(cmcg_handle*, const double*, const double*, bool, int, double*, double*);
@@ -1033,7 +1037,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
         return CMCG_ERR_INVALID_ARG;
     if ((o.flags & CMCG_FLAG_NO_CG) && o.runup_periods == 0) return CMCG_ERR_INVALID_ARG;
     if ((o.flags & CMCG_FLAG_FIRST_ORDER) &&
-        (grid->order != 2 || o.runup_periods != 0 ||
+        (grid->order != 2 ||
          (o.flags & (CMCG_FLAG_INEXACT_RIESZ | CMCG_FLAG_NO_CG))))
         return CMCG_ERR_UNSUPPORTED;
     if (o.dt < 0 || !isfinite(o.dt)) return CMCG_ERR_INVALID_ARG;
@@ -1091,7 +1095,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     memcpy(&H->cmin, &bits, sizeof(double));
     if (H->has_dir && H->order == 4) return fail(CMCG_ERR_UNSUPPORTED);
     if (H->has_dir && H->sumW <= 0) return fail(CMCG_ERR_INVALID_ARG);
-    if (o.runup_periods < -1 || o.runup_periods > 100000) return fail(CMCG_ERR_INVALID_ARG);
+    if (o.runup_periods < -64 || o.runup_periods > 100000) return fail(CMCG_ERR_INVALID_ARG);
     if (o.tile[0] < 0 || o.tile[0] > 512 || o.tile[1] < 0 || o.tile[1] > 512 || o.tile[2] < 0 || o.tile[2] > 16 ||
         o.tile[3] < 0 || o.tile[3] > 4)
         return fail(CMCG_ERR_INVALID_ARG);

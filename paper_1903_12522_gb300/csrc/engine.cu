@@ -26,7 +26,9 @@ using namespace cmcg::detail;
 
 namespace {
 
-enum Unit { U_FREE = 0, U_INIT32, U_OUTER, U_INNER, U_DONE };
+// U_RUNUP: the initial run-up (Sec. 4.3) of a mixed-precision slot, between its first outer
+// unit (the zero guess, which sets the tolerance reference) and its second.
+enum Unit { U_FREE = 0, U_INIT32, U_OUTER, U_INNER, U_DONE, U_RUNUP };
 
 struct EngineSlot {
     cmcg_handle* h = nullptr;
@@ -37,6 +39,7 @@ struct EngineSlot {
     int iters = 0, inner_iters = 0, outer = 0;
     long long periods = 0, riesz = 0;  // counted per tick (graph replays skip the launch-time counters)
     double gamma_ref = -1, rel = 1, inner_tol = 1e-3;
+    int runup = 0;  // run-up periods still to run (mixed precision only)
     long long launches0 = 0;
     std::chrono::steady_clock::time_point t0;
     cmcg_stats st{};
@@ -168,6 +171,9 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
                 gradient<float>(h, h->w0, h->w1, true, h->w0, h->w1, false);
                 reset_direction(h);
             });
+        } else if (sl.unit == U_RUNUP) {
+            const int periods = sl.runup;
+            on_side(e, sl.h, lane++, [periods](cmcg_handle* h) { runup<float>(h, periods, h->wo0, h->wo1); });
         } else if (sl.unit == U_INNER) {
             inner.push_back(s);
         }
@@ -346,6 +352,7 @@ int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const do
     if (h->st != e->st || h->opt.precision == CMCG_FP64 || !(h->opt.flags & CMCG_FLAG_INEXACT_RIESZ) ||
         (h->opt.flags & (CMCG_FLAG_FILTER | CMCG_FLAG_NO_CG | CMCG_FLAG_FIRST_ORDER)))
         return CMCG_ERR_UNSUPPORTED;
+    if (h->opt.precision != CMCG_MIXED && runup_count(h) > 0) return CMCG_ERR_UNSUPPORTED;
     int s = -1;
     for (int i = 0; i < e->max_slots; ++i) {
         if (e->slots[i].h == h && e->slots[i].unit != U_FREE) return CMCG_ERR_INVALID_ARG;  // handle busy
@@ -359,6 +366,7 @@ int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const do
     sl.tol = tol;
     sl.t0 = std::chrono::steady_clock::now();
     sl.launches0 = launch_count();
+    sl.runup = h->opt.precision == CMCG_MIXED ? runup_count(h) : 0;
     h->riesz_iters = 0;
     h->periods = 0;
     if (f || g)
@@ -384,7 +392,7 @@ int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_fin
     std::vector<int> act;
     for (int i = 0; i < e->max_slots; ++i) {
         const int u = e->slots[i].unit;
-        if (u == U_INIT32 || u == U_OUTER || u == U_INNER) act.push_back(i);
+        if (u == U_INIT32 || u == U_OUTER || u == U_INNER || u == U_RUNUP) act.push_back(i);
     }
     if (act.empty()) return CMCG_OK;
     // configuration signature: (slot, unit, handle) of every active slot
@@ -465,7 +473,14 @@ int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_fin
         cmcg_handle* h = sl.h;
         const double* sc = h->hsc;
         bool done = false;
-        sl.periods += 2;  // every unit runs one forward and one adjoint period
+        if (sl.unit == U_RUNUP) {  // the run-up state is the next outer unit's iterate
+            sl.periods += sl.runup;
+            sl.st.runup_periods = sl.runup;
+            sl.runup = 0;
+            sl.unit = U_OUTER;
+            continue;
+        }
+        sl.periods += 2;  // every other unit runs one forward and one adjoint period
         sl.riesz += 1;    // and one approximate Riesz map
         if (timeout && sl.unit == U_INNER) {
             sl.status = CMCG_ERR_DEVICE_TIMEOUT;
@@ -484,6 +499,8 @@ int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_fin
             if (sl.rel <= sl.tol) {
                 sl.status = CMCG_OK;
                 done = true;
+            } else if (sl.runup > 0) {
+                sl.unit = U_RUNUP;  // the zero guess set the reference; now the run-up
             } else if (sl.iters >= h->opt.max_iter || sl.outer > 50) {
                 sl.status = CMCG_NOT_CONVERGED;
                 done = true;
@@ -540,7 +557,8 @@ int cmcg_engine_result(cmcg_engine* e, int slot, cmcg_stats* stats) {
 int cmcg_engine_active(const cmcg_engine* e) {
     if (!e) return CMCG_ERR_INVALID_ARG;
     int n = 0;
-    for (const EngineSlot& sl : e->slots) n += (sl.unit == U_INIT32 || sl.unit == U_OUTER || sl.unit == U_INNER) ? 1 : 0;
+    for (const EngineSlot& sl : e->slots)
+        n += (sl.unit == U_INIT32 || sl.unit == U_OUTER || sl.unit == U_INNER || sl.unit == U_RUNUP) ? 1 : 0;
     return n;
 }
 

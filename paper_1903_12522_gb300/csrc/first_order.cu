@@ -394,10 +394,11 @@ const T* fo_kap(const cmcg_handle* H) {
 }
 
 template <typename T>
-void fo_step(cmcg_handle* H, const T* a, T* b, bool src, int n, bool backward, double* acc) {
+void fo_step(cmcg_handle* H, const T* a, T* b, bool src, int n, bool backward, double* acc, double theta = 1.0) {
     const Geom& g = H->g;
-    const double t = (n + 0.5) * H->dt;
-    const double cs = src ? cos(H->omega * t) / H->dt : 0.0, sn = src ? sin(H->omega * t) / H->dt : 0.0;
+    const double t = (n + 0.5) * H->dt;  // the source is T-periodic: n may count past one period
+    const double cs = src ? theta * cos(H->omega * t) / H->dt : 0.0;
+    const double sn = src ? theta * sin(H->omega * t) / H->dt : 0.0;
     const double tn = n * H->dt;
     const double ca = acc ? cos(H->omega * tn) : 0.0, sa = acc ? sin(H->omega * tn) : 0.0;
     const double tau = (backward ? -1.0 : 1.0) * H->dt / g.h;
@@ -471,7 +472,8 @@ template <typename T>
 int fo_cg_iterate(cmcg_handle* H, double* x, double tol, int max_iter, int* it_out, double* rel_out) {
     const Geom& g = H->g;
     const long long n = (long long)(g.dim + 1) * g.np;
-    double rel = H->hsc[SC_GAMMA0] > 0.0 ? 1.0 : 0.0;
+    // relative to the reference in SC_GAMMA0 (the start gradient's, or the zero guess's after a run-up)
+    double rel = H->hsc[SC_GAMMA0] > 0.0 ? sqrt(std::max(H->hsc[SC_GAMMA], 0.0) / H->hsc[SC_GAMMA0]) : 0.0;
     double best = rel;
     int it = 0;
     if (rel > tol) {
@@ -517,10 +519,54 @@ int fo_cg_start(cmcg_handle* H, double* x) {
     return sync_read(H) == CMCG_OK ? CMCG_OK : CMCG_ERR_CUDA;
 }
 
+// Initial run-up (Sec. 4.3) on the first-order state: the forced staggered leapfrog from rest for
+// `periods` periods with the sources ramped in by theta_tr over [0, periods T]; the state at
+// t = periods T goes to out (FP64).
+template <typename T>
+void fo_runup(cmcg_handle* H, int periods, double* out) {
+    const Geom& g = H->g;
+    const long long n = (long long)(g.dim + 1) * g.np;
+    T* a = (T*)H->fo_a;
+    T* b = (T*)H->fo_b;
+    cudaMemsetAsync(a, 0, sizeof(T) * n, H->st);
+    const long long total = (long long)periods * H->N;
+    const double ttr = total * H->dt;
+    for (long long k = 0; k < total; ++k) {
+        fo_step<T>(H, a, b, true, (int)(k % H->N), false, nullptr, ramp((k + 0.5) * H->dt, ttr));
+        std::swap(a, b);
+    }
+    note_launch(1);
+    k_fo_end<T, 1><<<fo_vec_blocks(n), kFT, 0, H->st>>>(a, out, out, H->mass, g, H->red());
+    H->periods += periods;
+}
+
+// With a run-up: the zero-guess gradient's gamma (the tolerance reference, and J0), then the
+// run-up state into x and its gradient with r = d = g, and SC_GAMMA0 set to the reference.
+// Without: x = 0 and its gradient.  Returns the number of run-up periods (or a negative status).
+template <typename T>
+int fo_start_with_runup(cmcg_handle* H, double* x, cmcg_stats* st) {
+    const Geom& g = H->g;
+    const long long n = (long long)(g.dim + 1) * g.np;
+    if (fo_cg_start<T>(H, x) != CMCG_OK) return CMCG_ERR_CUDA;
+    st->J0 = H->hsc[SC_J];
+    const int ell = runup_count(H);
+    if (ell <= 0) return 0;
+    const double gamma_zero = H->hsc[SC_GAMMA0];
+    fo_runup<T>(H, ell, x);
+    fo_forward<T>(H, x, true, 0, H->fo_e, nullptr);
+    fo_backward<T>(H, H->fo_e, H->fo_e, 0, H->fo_g);
+    note_launch(1);
+    k_fo_cg_init<<<fo_vec_blocks(n), kFT, 0, H->st>>>(H->fo_g, H->fo_r, H->fo_d, H->mass, g, H->red());
+    cudaMemcpyAsync(H->sc + SC_GAMMA0, &gamma_zero, sizeof(double), cudaMemcpyHostToDevice, H->st);
+    if (sync_read(H) != CMCG_OK) return CMCG_ERR_CUDA;
+    return ell;
+}
+
 template <typename T>
 int fo_cg(cmcg_handle* H, double tol, cmcg_stats* st) {
-    if (fo_cg_start<T>(H, H->fo_s) != CMCG_OK) return CMCG_ERR_CUDA;
-    st->J0 = H->hsc[SC_J];
+    const int ell = fo_start_with_runup<T>(H, H->fo_s, st);
+    if (ell < 0) return ell;
+    st->runup_periods = ell;
     int it = 0;
     double rel = 1.0;
     const int rc = fo_cg_iterate<T>(H, H->fo_s, tol, H->opt.max_iter, &it, &rel);
@@ -541,6 +587,19 @@ int fo_mixed(cmcg_handle* H, double tol, cmcg_stats* st) {
     double gamma_ref = -1.0, rel = 1.0;
     int total = 0, outer = 0;
     const int max_outer = 50;
+    const int ell = runup_count(H);
+    if (ell > 0) {
+        // the tolerance reference is the FP64 gradient of the zero guess; then an FP32 run-up
+        fo_forward<double>(H, H->fo_s, true, 0, H->fo_e, nullptr);
+        fo_backward<double>(H, H->fo_e, H->fo_e, 0, H->fo_g);
+        note_launch(1);
+        k_fo_cg_init<<<fo_vec_blocks(n), kFT, 0, H->st>>>(H->fo_g, H->fo_r, H->fo_d, H->mass, g, H->red());
+        if (sync_read(H) != CMCG_OK) return CMCG_ERR_CUDA;
+        gamma_ref = H->hsc[SC_GAMMA0];
+        st->J0 = H->hsc[SC_J];
+        fo_runup<float>(H, ell, H->fo_s);
+        st->runup_periods = ell;
+    }
     for (outer = 0; outer < max_outer; ++outer) {
         fo_forward<double>(H, H->fo_s, true, 0, H->fo_e, nullptr);
         fo_backward<double>(H, H->fo_e, H->fo_e, 0, H->fo_g);
@@ -549,7 +608,7 @@ int fo_mixed(cmcg_handle* H, double tol, cmcg_stats* st) {
         if (sync_read(H) != CMCG_OK) return CMCG_ERR_CUDA;
         const double gam = H->hsc[SC_GAMMA0];
         if (!(gam == gam) || gam < 0) return CMCG_ERR_DIVERGED;
-        if (outer == 0) {
+        if (gamma_ref < 0) {
             gamma_ref = gam;
             st->J0 = H->hsc[SC_J];
         }

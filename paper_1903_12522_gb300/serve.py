@@ -106,10 +106,10 @@ def poisson_requests(count, rate, seed=5, two_d=(128, 512), three_d=(64, 256), f
 
 
 # ---- engine driver -------------------------------------------------------------------------
-def make_solver(req, c, precision, stream):
+def make_solver(req, c, precision, stream, runup=0):
     faces = (cmcg.BC_ABC,) * 6
     return cmcg.Solver(req.grid(), req.h, c, req.omega, faces, precision=precision, dt=req.dt_target,
-                       flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream)
+                       flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream, runup_periods=runup)
 
 
 def workspace_bytes(req, precision):
@@ -118,7 +118,7 @@ def workspace_bytes(req, precision):
 
 
 def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, device="cuda", log=None,
-          keep_results=False, stream=None):
+          keep_results=False, stream=None, runup=0):
     """Run the request stream in real time; returns per-request records and totals."""
     import torch
 
@@ -143,7 +143,7 @@ def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, 
             if used + nb > budget_bytes:
                 continue
             c, f = req.build(device)
-            s = make_solver(req, c, precision, stream)
+            s = make_solver(req, c, precision, stream, runup)
             slot = eng.submit(s, f, None, tol)
             req.admitted = time.perf_counter() - t0
             running[slot] = (req, s, nb)
@@ -184,7 +184,7 @@ def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, 
     }
 
 
-def batch(count=64, max_n=None, precision=cmcg.MIXED, tol=1e-6, device="cuda"):
+def batch(count=64, max_n=None, precision=cmcg.MIXED, tol=1e-6, device="cuda", runup=0):
     """The uneven 2D batch solved together; returns totals."""
     import torch
 
@@ -197,7 +197,7 @@ def batch(count=64, max_n=None, precision=cmcg.MIXED, tol=1e-6, device="cuda"):
             w = wl.random_2d_instance(i, n=max_n)
         ws.append(w)
     solvers = [cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, precision=precision, dt=w.dt_target,
-                           flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream) for w in ws]
+                           flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream, runup_periods=runup) for w in ws]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s, w in zip(solvers, ws):
@@ -231,14 +231,16 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
+    ap.add_argument("--runup", type=int, default=0,
+                    help="run-up periods per solve (Sec. 4.3; -k = k domain crossings; mixed precision only)")
     ap.add_argument("--max-3d", type=int, default=256)
     a = ap.parse_args()
     prec = cmcg.MIXED if a.precision == "mixed" else cmcg.FP32
     if a.mode == "batch":
-        out = batch(a.count, a.max_n, prec, a.tol)
+        out = batch(a.count, a.max_n, prec, a.tol, runup=a.runup)
     else:
         reqs = poisson_requests(a.requests, a.rate, three_d=(64, a.max_3d))
-        out = serve(reqs, int(a.budget_gb * 1e9), precision=prec, tol=a.tol)
+        out = serve(reqs, int(a.budget_gb * 1e9), precision=prec, tol=a.tol, runup=a.runup)
     print(json.dumps(out), flush=True)
 
 

@@ -37,9 +37,9 @@ def mix():
     return [wl.gaussian_2d(n=40), odd_2d(), wl.sphere_3d(n=16), small_random(3, 45), small_random(7, 60)]
 
 
-def solver(w, precision, stream):
+def solver(w, precision, stream, runup=0):
     return cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, order=w.order, precision=precision,
-                       dt=w.dt_target, flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream)
+                       dt=w.dt_target, flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream, runup_periods=runup)
 
 
 def wrel(dz, a, b):
@@ -56,10 +56,10 @@ def engine_stream():
     return STREAM
 
 
-def run_engine(ws, precision, tol, flags=0):
+def run_engine(ws, precision, tol, flags=0, runup=0):
     stream = engine_stream()
     eng = cmcg.Engine(max_slots=len(ws), stream=stream, flags=flags)
-    solvers = [solver(w, precision, stream) for w in ws]
+    solvers = [solver(w, precision, stream, runup) for w in ws]
     slots = [eng.submit(s, w.f, w.g, tol) for s, w in zip(solvers, ws)]
     res = eng.run_all()
     out = [res[sl] for sl in slots]
@@ -99,6 +99,32 @@ def test_graph_and_plain_launches_agree():
     assert info["graph_builds"] == 0
     for (ua, _), (ub, _) in zip(a, b):
         assert torch.equal(ua, ub)
+
+
+def test_runup_in_the_engine():
+    # Sec. 4.3 inside the engine (mixed precision): the zero guess sets the tolerance reference,
+    # then each slot runs its ramped run-up as one unit; same fixed point, fewer CG iterations
+    ws = mix()
+    out0, _ = run_engine(ws, cmcg.MIXED, 1e-9)
+    out1, info = run_engine(ws, cmcg.MIXED, 1e-9, runup=-1)
+    for w, (u, st), (_, st0) in zip(ws, out1, out0):
+        assert st["status"] == cmcg.OK and st["runup_periods"] > 0, (w.name, st)
+        dz = Discretization(w.n, w.h, w.c, w.omega, w.faces, w.dt_target, order=w.order, mask=w.mask)
+        U = direct.solve(dz, dz.load(w.f, w.g))
+        assert wrel(dz, u.cpu().numpy(), U) <= 1e-6, (w.name, st)
+        assert st["J0"] == pytest.approx(st0["J0"], rel=1e-9)
+    assert sum(st["iterations"] for _, st in out1) < sum(st["iterations"] for _, st in out0)
+    # a solve alone gives the same bits as in the mix
+    alone, _ = run_engine([ws[2]], cmcg.MIXED, 1e-9, runup=-1)
+    assert torch.equal(alone[0][0], out1[2][0])
+    # FP32 slots take no run-up
+    stream = engine_stream()
+    eng = cmcg.Engine(max_slots=1, stream=stream)
+    w = wl.gaussian_2d(n=24)
+    with pytest.raises(cmcg.CMCGError) as e:
+        eng.submit(solver(w, cmcg.FP32, stream, -1), w.f, None, 1e-6)
+    assert e.value.code == cmcg.ERR_UNSUPPORTED
+    eng.close()
 
 
 def test_admission_errors():

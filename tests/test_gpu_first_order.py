@@ -167,10 +167,26 @@ def test_fo_iterations_match_oracle(case):
     assert stats["J0"] == pytest.approx(ref.J_history[0], rel=1e-10)
 
 
+@pytest.mark.parametrize("precision,flags,tol,bound", [(cmcg.FP64, cmcg.FLAG_FILTER, 1e-12, 1e-9),
+                                                       (cmcg.MIXED, cmcg.FLAG_FILTER, 1e-10, 1e-8)])
+@pytest.mark.parametrize("runup", [-1, -4])
+def test_fo_runup_keeps_the_fixed_point_and_saves_iterations(precision, flags, tol, bound, runup):
+    # Sec. 4.3 on the first-order state: the ramped run-up gives the initial guess, the
+    # tolerance stays referenced to the zero guess, so the answer's accuracy is unchanged
+    w = wl.sphere_3d(n=24)
+    dz = Discretization(w.n, w.h, w.c, w.omega, w.faces, w.dt_target, mask=w.mask)
+    U = direct.solve(dz, dz.load(w.f, w.g))
+    _, st0 = solver_of(w, precision, flags).solve(w.f, w.g, tol=tol)
+    u1, st1 = solver_of(w, precision, flags, runup_periods=runup).solve(w.f, w.g, tol=tol)
+    assert st1["status"] == cmcg.OK and st1["runup_periods"] > 0, st1
+    assert wrel(dz, u1.cpu().numpy(), U) <= bound
+    assert st1["iterations"] < st0["iterations"], (st0["iterations"], st1["iterations"])
+    assert st1["J0"] == pytest.approx(st0["J0"], rel=1e-6)
+
+
 def test_fo_unsupported_combinations():
     w = wl.gaussian_2d(n=24)
-    for kw in ({"flags": cmcg.FLAG_INEXACT_RIESZ}, {"runup_periods": 2},
-               {"flags": cmcg.FLAG_NO_CG, "runup_periods": 2}):
+    for kw in ({"flags": cmcg.FLAG_INEXACT_RIESZ}, {"flags": cmcg.FLAG_NO_CG, "runup_periods": 2}):
         kw = dict(kw)
         flags = kw.pop("flags", 0)
         with pytest.raises(cmcg.CMCGError) as e:

@@ -207,17 +207,21 @@ def test_inexact_riesz_solve_matches_direct(case, precision, tol, bound):
     assert st["riesz_iterations"] >= st["iterations"]
 
 
+@pytest.mark.parametrize("runup", [-1, -4])
 @pytest.mark.parametrize("precision,flags,tol,bound", [(cmcg.FP64, 0, 1e-12, 1e-9),
                                                        (cmcg.MIXED, cmcg.FLAG_INEXACT_RIESZ, 1e-9, 1e-6)])
-def test_runup_keeps_the_fixed_point_and_saves_iterations(precision, flags, tol, bound):
+def test_runup_keeps_the_fixed_point_and_saves_iterations(precision, flags, tol, bound, runup):
     # Sec. 4.3: a run-up from rest with ramped sources gives the initial guess; the tolerance
     # refers to the zero-guess residual, so the answer's accuracy is unchanged
     w = wl.sphere_3d(n=24)
     dz = dz_of(w)
     U = direct.solve(dz, dz.load(w.f, w.g))
     _, st0 = solver_of(w, precision, flags=flags).solve(w.f, w.g, tol=tol)
-    u1, st1 = solver_of(w, precision, flags=flags, runup_periods=-1).solve(w.f, w.g, tol=tol)
+    u1, st1 = solver_of(w, precision, flags=flags, runup_periods=runup).solve(w.f, w.g, tol=tol)
     assert st1["status"] == cmcg.OK and st1["runup_periods"] > 0
+    # -k: the periods waves at c_min need to cross the domain's diagonal k times
+    diam = w.h * math.sqrt(sum(m * m for m in w.n))
+    assert st1["runup_periods"] == max(1, math.ceil(-runup * diam * w.omega / (2 * math.pi * 0.7) - 1e-9))
     assert wrel(dz, u1.cpu().numpy(), U) <= bound
     assert st1["iterations"] < st0["iterations"], (st0["iterations"], st1["iterations"])
 
