@@ -231,7 +231,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
-    ap.add_argument("--runup", type=int, default=0,
+    ap.add_argument("--runup", type=int, default=-2,
                     help="run-up periods per solve (Sec. 4.3; -k = k domain crossings; mixed precision only)")
     ap.add_argument("--max-3d", type=int, default=256)
     a = ap.parse_args()

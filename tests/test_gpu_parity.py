@@ -315,6 +315,36 @@ def test_not_converged_returns_last_iterate():
     assert 0 < st["rel_residual"] < 1 and float(u.abs().max()) > 0
 
 
+def tiny(n, faces, seed):
+    h = 1.0 / max(n)
+    shape = tuple(m + 1 for m in reversed(n))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = 1.0 + 0.3 * rng.random(shape)
+    f = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex128)
+    return wl.Workload(name=f"tiny{n}", n=n, h=h, c=c, omega=2.5, faces=faces, dt_target=0.2 * h, f=f)
+
+
+@pytest.mark.parametrize("n,faces", [((2, 2), (ABC,) * 4 + (NEU, NEU)), ((3, 2), (ABC, DIR, NEU, ABC, NEU, NEU)),
+                                     ((2, 3, 2), (ABC,) * 6), ((2, 2, 3), (ABC, NEU, DIR, ABC, NEU, ABC))])
+def test_smallest_grids(n, faces):
+    # the smallest grids the ABI accepts (2 intervals per axis, 3 nodes): every node is a
+    # boundary node, the multigrid has one level, and the step kernels' mirrors meet
+    w = tiny(n, faces, 31)
+    dz = dz_of(w)
+    y0, v0 = rand_state(dz, 32)
+    F = dz.load(w.f, None)
+    yT, vT = wave.period(dz, y0, v0, F)
+    for precision, tol in ((cmcg.FP64, 1e-12), (cmcg.FP32, 2e-5)):
+        uT, uV = solver_of(w, precision).wave_period(y0, v0, w.f, None)
+        assert rel(uT.cpu().numpy(), yT) <= tol and rel(uV.cpu().numpy(), vT) <= tol, (n, precision)
+    U = direct.solve(dz, F)
+    for precision, flags, tol, bound in ((cmcg.FP64, 0, 1e-12, 1e-9),
+                                         (cmcg.MIXED, cmcg.FLAG_INEXACT_RIESZ, 1e-10, 1e-7)):
+        u, st = solver_of(w, precision, flags=flags).solve(w.f, None, tol=tol)
+        assert st["status"] == cmcg.OK, (n, st)
+        assert wrel(dz, u.cpu().numpy(), U) <= bound, (n, precision)
+
+
 def test_invalid_arguments():
     w = wl.gaussian_2d(n=16)
     with pytest.raises(cmcg.CMCGError) as e:
