@@ -289,7 +289,12 @@ class Solver:
             self.bc.face[f] = int(faces[f])
         self.mask = None if mask is None else self._dev(mask, torch.uint8)
         self.bc.dirichlet_mask = _ptr(self.mask)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        # a stream of its own by default: the CG loop replays a captured CUDA graph, which the
+        # legacy default stream does not allow
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        for t in (self.workspace, self.c, self.mask):
+            if t is not None:
+                t.record_stream(self.stream)
         self._after_caller()
         self.handle = cmcg_create(self.grid, self.c, omega, self.bc, self.opts, self.workspace, self.stream.cuda_stream)
         self.info = cmcg_get_info(self.handle)
@@ -316,6 +321,7 @@ class Solver:
 
     def close(self):
         if getattr(self, "handle", None) is not None:
+            self.stream.synchronize()
             cmcg_destroy(self.handle)
             self.handle = None
 

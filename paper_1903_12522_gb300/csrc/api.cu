@@ -572,6 +572,52 @@ void apply_B(cmcg_handle* H, bool first, bool lowp) {
     H->riesz_iters += 1;
 }
 
+// One CG iteration captured as a CUDA graph.  Capture needs a created stream that is not
+// already being captured, and no step timing (its event bookkeeping runs on the host); any
+// failure leaves the caller on plain launches.  A replay advances the host-side counters
+// (periods, Riesz maps, launches) by what the captured iteration would have added.
+struct IterationGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long periods = 0, riesz = 0, launches = 0;
+    template <typename F>
+    void capture(cmcg_handle* H, F body) {
+        cudaStream_t st = H->st;
+        if (H->timing || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return;
+        }
+        const long long p0 = H->periods, r0 = H->riesz_iters, l0 = launch_count();
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        body();
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        periods = H->periods - p0;
+        riesz = H->riesz_iters - r0;
+        launches = launch_count() - l0;
+        H->periods = p0;  // nothing ran yet
+        H->riesz_iters = r0;
+        note_launch(-launches);
+        if (ce == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
+    bool replay(cmcg_handle* H) {
+        if (!exec || cudaGraphLaunch(exec, H->st) != cudaSuccess) return false;
+        H->periods += periods;
+        H->riesz_iters += riesz;
+        note_launch(launches);
+        return true;
+    }
+    ~IterationGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
 // Flexible CG (Polak-Ribiere) on the current gradient in (gh0, gh1) with z = B rhat;
 // iterate accumulated into (w0, w1) (v -= alpha d).
 template <typename T>
@@ -588,12 +634,20 @@ int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_o
     if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
     double rel = H->hsc[SC_REL];
     int it = 0;
+    auto body = [&]() {
+        gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1, false);        // 5.1: ghat_d = H d
+        launch_fcg_update(n, H->w0, H->w1, H->rh0, H->rh1, H->d0, H->d1, H->gh0, H->gh1, red, H->st);
+        apply_B(H, false, std::is_same<T, float>::value);              // 5.2 on the residual
+        launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st);  // 5.7
+    };
+    // The iteration's launches and arguments do not change (its scalars live on the device), so
+    // it is captured once as a CUDA graph and replayed: on small grids the host's launch rate,
+    // not the GPU, sets the pace of a plain loop.
+    IterationGraph graph;
+    if (rel > tol && max_iter > 1) graph.capture(H, body);
     if (rel > tol) {
         for (it = 1; it <= max_iter; ++it) {
-            gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1, false);        // 5.1: ghat_d = H d
-            launch_fcg_update(n, H->w0, H->w1, H->rh0, H->rh1, H->d0, H->d1, H->gh0, H->gh1, red, H->st);
-            apply_B(H, false, std::is_same<T, float>::value);              // 5.2 on the residual
-            launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st);  // 5.7
+            if (!graph.replay(H)) body();
             rc = sync_read(H);
             if (rc != CMCG_OK) return rc;
             if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;

@@ -279,6 +279,21 @@ def test_fp64_iterations_and_shift_match_oracle(case):
     assert abs(st["J0"] - ref.J_history[0]) <= 1e-10 * ref.J_history[0]
 
 
+@pytest.mark.parametrize("precision,tol", [(cmcg.FP64, 1e-9), (cmcg.MIXED, 1e-9), (cmcg.FP32, 1e-6)])
+def test_graph_replayed_iterations_match_plain_launches(precision, tol):
+    # on its own stream a solve replays each flexible-CG iteration as a captured CUDA graph; on
+    # the legacy default stream it launches the kernels one by one: same bits, same counts
+    w = wl.sphere_3d(n=16)
+    out = {}
+    for name, stream in (("graph", torch.cuda.Stream()), ("plain", torch.cuda.default_stream())):
+        s = solver_of(w, precision, flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream)
+        out[name] = s.solve(w.f, w.g, tol=tol)
+    (ug, sg), (up, sp) = out["graph"], out["plain"]
+    assert torch.equal(ug, up)
+    for k in ("iterations", "periods", "riesz_iterations", "kernel_launches", "outer_iterations"):
+        assert sg[k] == sp[k], (k, sg[k], sp[k])
+
+
 def test_solve_host_matches_device():
     w = wl.gaussian_2d(n=48)
     s = solver_of(w, flags=cmcg.FLAG_HOST_IO)
