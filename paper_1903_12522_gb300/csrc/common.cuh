@@ -95,6 +95,47 @@ __device__ __forceinline__ R lap_t(const Geom& g, F f, long long j, int ix, int 
     }
 }
 
+// Unscaled 7-point Laplacian of f along a thread's z-column, with the z-neighbours carried in
+// registers from plane to plane (mirror at the z faces).  Same sum, in the same order, as
+// lap_t<2> ((x- + x+) + (y- + y+)) + (z- + z+), so the results are bitwise equal.
+template <typename T, typename F>
+struct ColumnLap7 {
+    F f;
+    long long sZ, oxm, oxp, oym, oyp;
+    int nz;
+    T below, here, above;  // f at iz - 1, iz, iz + 1 (mirrored at the faces)
+    __device__ __forceinline__ void start(long long j, int iz) {
+        here = f(j);
+        below = f(j + (iz > 0 ? -sZ : sZ));
+        above = f(j + (iz < nz ? sZ : -sZ));
+    }
+    __device__ __forceinline__ T lap(long long j) const {
+        T acc = f(j + oxm) + f(j + oxp);
+        acc += f(j + oym) + f(j + oyp);
+        acc += below + above;
+        return T(6) * here - acc;
+    }
+    // move to plane iz + 1 (node j + sZ); valid while iz + 1 <= nz
+    __device__ __forceinline__ void advance(long long j, int iz) {
+        below = here;
+        here = above;
+        above = f(j + sZ + (iz + 1 < nz ? sZ : -sZ));
+    }
+};
+
+template <typename T, typename F>
+__device__ __forceinline__ ColumnLap7<T, F> column_lap(const Geom& g, F f, int ix, int iy) {
+    ColumnLap7<T, F> c;
+    c.f = f;
+    c.sZ = (long long)g.sx * g.sy;
+    c.oxm = off_m1(ix, 1);
+    c.oxp = off_p1(ix, g.nx, 1);
+    c.oym = off_m1(iy, g.sx);
+    c.oyp = off_p1(iy, g.ny, g.sx);
+    c.nz = g.nz;
+    return c;
+}
+
 // ---- deterministic block reductions -------------------------------------------------
 // Each block reduces NV doubles; thread 0 stores them in partials[k * gridDim.x + block].
 // The last block to finish (atomic ticket) sums the partials in a fixed order and writes

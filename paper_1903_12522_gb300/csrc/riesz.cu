@@ -244,11 +244,11 @@ __global__ void __launch_bounds__(kT) k_jacobi(Geom g, const unsigned char* __re
     const MGConst c = mg_const(g);
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
-        if (mask && mask[j]) {
-            xout[j] = 0.f;
-            continue;
-        }
-        xout[j] = jacobi_node(g, c, xin, b[j], omega, j, m.ix, m.iy, iz);
+        // the mask, b and the stencil are loaded together and the mask selects at the end: a
+        // branch on the mask byte would put its load's latency before every other load
+        const bool dir = mask && mask[j];
+        const float v = jacobi_node(g, c, xin, b[j], omega, j, m.ix, m.iy, iz);
+        xout[j] = dir ? 0.f : v;
     }
 }
 
@@ -260,11 +260,9 @@ __global__ void __launch_bounds__(kT) k_residual(Geom g, const unsigned char* __
     const MGConst c = mg_const(g);
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
-        if (mask && mask[j]) {
-            r[j] = 0.f;
-            continue;
-        }
-        r[j] = residual_node(g, c, x, b[j], j, m.ix, m.iy, iz);
+        const bool dir = mask && mask[j];  // selected at the end (see k_jacobi)
+        const float v = residual_node(g, c, x, b[j], j, m.ix, m.iy, iz);
+        r[j] = dir ? 0.f : v;
     }
 }
 
@@ -276,7 +274,9 @@ __global__ void __launch_bounds__(kT) k_restrict(Geom gf, const float* __restric
     if (!m.valid) return;
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long J = node(gc, m.ix, m.iy, iz);
-        bc[J] = (maskc && maskc[J]) ? 0.f : restrict_node(gf, gc, rf, m.ix, m.iy, iz);
+        const bool dir = maskc && maskc[J];  // selected at the end (see k_jacobi)
+        const float v = restrict_node(gf, gc, rf, m.ix, m.iy, iz);
+        bc[J] = dir ? 0.f : v;
     }
 }
 
@@ -288,8 +288,10 @@ __global__ void __launch_bounds__(kT) k_prolong_add(Geom gc, const float* __rest
     if (!m.valid) return;
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long i = node(gf, m.ix, m.iy, iz);
-        if (maskf && maskf[i]) continue;
-        xf[i] += prolong_node(gc, xc, gf, m.ix, m.iy, iz);
+        const bool dir = maskf && maskf[i];  // tested at the store (see k_jacobi)
+        const float v = prolong_node(gc, xc, gf, m.ix, m.iy, iz);
+        const float x0 = xf[i];
+        if (!dir) xf[i] = x0 + v;
     }
 }
 

@@ -66,46 +66,6 @@ struct DiffT {  // a[i] - b[i] in T
     __device__ __forceinline__ T operator()(long long i) const { return a[i] - b[i]; }
 };
 
-// Unscaled 7-point Laplacian of f along a thread's z-column, with the z-neighbours carried in
-// registers from plane to plane (mirror at the z faces).  Same sum, in the same order, as
-// lap_t<2> ((x- + x+) + (y- + y+)) + (z- + z+), so the results are bitwise equal.
-template <typename T, typename F>
-struct ColumnLap7 {
-    F f;
-    long long sZ, oxm, oxp, oym, oyp;
-    int nz;
-    T below, here, above;  // f at iz - 1, iz, iz + 1 (mirrored at the faces)
-    __device__ __forceinline__ void start(long long j, int iz) {
-        here = f(j);
-        below = f(j + (iz > 0 ? -sZ : sZ));
-        above = f(j + (iz < nz ? sZ : -sZ));
-    }
-    __device__ __forceinline__ T lap(long long j) const {
-        T acc = f(j + oxm) + f(j + oxp);
-        acc += f(j + oym) + f(j + oyp);
-        acc += below + above;
-        return T(6) * here - acc;
-    }
-    // move to plane iz + 1 (node j + sZ); valid while iz + 1 <= nz
-    __device__ __forceinline__ void advance(long long j, int iz) {
-        below = here;
-        here = above;
-        above = f(j + sZ + (iz + 1 < nz ? sZ : -sZ));
-    }
-};
-
-template <typename T, typename F>
-__device__ __forceinline__ ColumnLap7<T, F> column_lap(const Geom& g, F f, int ix, int iy) {
-    ColumnLap7<T, F> c;
-    c.f = f;
-    c.sZ = (long long)g.sx * g.sy;
-    c.oxm = off_m1(ix, 1);
-    c.oxp = off_p1(ix, g.nx, 1);
-    c.oym = off_m1(iy, g.sx);
-    c.oyp = off_p1(iy, g.ny, g.sx);
-    c.nz = g.nz;
-    return c;
-}
 
 // ---------------------------------------------------------------------------------------
 // Leapfrog step, generic (any dim / order): one thread per (x, y) column, marching z.
@@ -437,19 +397,17 @@ __global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, c
     if (col) cl.start(node(g, m.ix, m.iy, m.z0), m.z0);
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
+        // every load is issued before the Dirichlet test (kappa = 0), which only selects the
+        // stores: a branch on kappa would put its load's latency before all the others
         const T k = kap[j];
-        if (k == T(0)) {
-            y0[j] = T(0);
-            y1[j] = T(0);
-        } else {
-            const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
-            const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-            const T w0j = w0t[j];
-            T v = w0j + dtT * (T(1) - beta) * (T)w1[j] - T(0.5) * k * L;
-            if (SRC) v += (T)(0.5 * S[2 * j]);
-            y0[j] = w0j;
-            y1[j] = v;
-        }
+        const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+        const T w0j = w0t[j];
+        T v = w0j + dtT * (T(1) - beta) * (T)w1[j] - T(0.5) * k * L;
+        if (SRC) v += (T)(0.5 * S[2 * j]);
+        const bool dir = k == T(0);
+        y0[j] = dir ? T(0) : w0j;
+        y1[j] = dir ? T(0) : v;
         if (col && iz + 1 < m.z1) cl.advance(j, iz);
     }
 }
@@ -477,12 +435,8 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __r
         const T dtT = (T)dt;
         for (int iz = m.z0; iz < m.z1; ++iz) {
             const long long j = node(g, m.ix, m.iy, iz);
-            const T k = kap[j];
-            if (k == T(0)) {
-                out0[j] = 0.0;
-                out1[j] = 0.0;
-                continue;
-            }
+            const T k = kap[j];  // Dirichlet (kappa = 0) only selects the stores (see k_start)
+            const bool dir = k == T(0);
             const T L = lap_t<ORDER, T>(g, fy, j, m.ix, m.iy, iz);
             const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
             T src = T(0);
@@ -490,20 +444,20 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __r
             const T yn = yN[j];
             const T vN = ((yn - yNm1[j]) / dtT + (src - k * L) / (T(2) * dtT)) / (T(1) + beta);
             if (MODE == 1) {
-                out0[j] = (double)yn;
-                out1[j] = (double)vN;
+                out0[j] = dir ? 0.0 : (double)yn;
+                out1[j] = dir ? 0.0 : (double)vN;
             } else {
                 const T e0 = yn - w0t[j];
                 const T e1 = vN - (T)w1[j];
                 const T W = weight_t<T>(g, m.ix, m.iy, iz);
                 const T z0 = W * ih2 * lap_t<ORDER, T>(g, fe, j, m.ix, m.iy, iz);
                 const T z1 = (T)mass[j] * e1;
-                out0[j] = (double)z0;
-                out1[j] = (double)z1;
+                out0[j] = dir ? 0.0 : (double)z0;
+                out1[j] = dir ? 0.0 : (double)z1;
                 if (std::is_same<T, float>::value)
-                    accf.add((float)(e0 * z0 + e1 * z1));
+                    accf.add(dir ? 0.0f : (float)(e0 * z0 + e1 * z1));
                 else
-                    acc[0] += 0.5 * (double)(e0 * z0 + e1 * z1);
+                    acc[0] += dir ? 0.0 : 0.5 * (double)(e0 * z0 + e1 * z1);
             }
         }
     }
@@ -521,13 +475,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_prep(const double* __restrict_
     if (!m.valid) return;
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
-        const T k = kap[j];
-        if (k == T(0)) {
-            t[j] = T(0);
-            continue;
-        }
+        const T k = kap[j];  // Dirichlet (kappa = 0) only selects the store (see k_start)
         const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
-        t[j] = (T)b[j] / ((T)mass[j] * (T(1) + beta));
+        const T v = (T)b[j] / ((T)mass[j] * (T(1) + beta));  // 0/0 on Dirichlet nodes: not stored
+        t[j] = k == T(0) ? T(0) : v;
     }
 }
 
@@ -544,18 +495,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_start(const double* __restrict
     const T dtT = (T)dt;
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
-        const T k = kap[j];
-        if (k == T(0)) {
-            cur[j] = T(0);
-            prev[j] = T(0);
-            continue;
-        }
+        const T k = kap[j];  // Dirichlet (kappa = 0) only selects the stores (see k_start)
         const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
         const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
         const T tj = t[j];
-        const T u = ((T)a[j] / (T)mass[j] + tj / dtT - k * L / (T(2) * dtT)) / (T(1) + beta);
-        cur[j] = u;
-        prev[j] = tj / dtT;
+        const T u = ((T)a[j] / (T)mass[j] + tj / dtT - k * L / (T(2) * dtT)) / (T(1) + beta);  // 0/0 at Dirichlet
+        const bool dir = k == T(0);
+        cur[j] = dir ? T(0) : u;
+        prev[j] = dir ? T(0) : tj / dtT;
     }
 }
 
@@ -583,14 +530,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
         if (col) cl.start(node(g, m.ix, m.iy, m.z0), m.z0);
         for (int iz = m.z0; iz < m.z1; ++iz) {
             const long long j = node(g, m.ix, m.iy, iz);
-            const T k = kap[j];
-            if (k == T(0)) {
-                o0[j] = 0.0;
-                o1[j] = 0.0;
-                if (MODE == 0) gt1[j] = 0.0;
-                if (col && iz + 1 < m.z1) cl.advance(j, iz);
-                continue;
-            }
+            const T k = kap[j];  // Dirichlet (kappa = 0) only selects the stores (see k_start)
+            const bool dir = k == T(0);
             const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
             const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
             const T W = weight_t<T>(g, m.ix, m.iy, iz);
@@ -599,26 +540,28 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
             const T q0 = M * (sj - (T(1) - beta) * u1[j]) - T(0.5) * dtT * dtT * W * ih2 * L;
             const T q1 = dtT * M * (T(1) - beta) * sj;
             if (MODE == 1) {
-                o0[j] = (double)q0;
-                o1[j] = (double)q1;
+                o0[j] = dir ? 0.0 : (double)q0;
+                o1[j] = dir ? 0.0 : (double)q1;
             } else if (std::is_same<T, float>::value) {
                 // FP32 periods: z came from FP32 values, so the differences and products stay in
                 // FP32 (FP64 only holds the stored vectors)
                 const float g0 = (float)q0 - (float)z0[j];
                 const float g1 = (float)q1 - (float)z1[j];
-                o0[j] = (double)g0;
-                o1[j] = (double)g1;
-                gt1[j] = (double)(g1 * (float)minv[j]);
-                accf0.add(g0 * (float)d0[j] + g1 * (float)d1[j]);
-                accf1.add(g0);
+                const float pd = g0 * (float)d0[j] + g1 * (float)d1[j];
+                o0[j] = dir ? 0.0 : (double)g0;
+                o1[j] = dir ? 0.0 : (double)g1;
+                gt1[j] = dir ? 0.0 : (double)(g1 * (float)minv[j]);
+                accf0.add(dir ? 0.0f : pd);
+                accf1.add(dir ? 0.0f : g0);
             } else {
                 const double g0 = (double)q0 - z0[j];
                 const double g1 = (double)q1 - z1[j];
-                o0[j] = g0;
-                o1[j] = g1;
-                gt1[j] = g1 * minv[j];
-                acc[0] += g0 * d0[j] + g1 * d1[j];
-                acc[1] += g0;
+                const double pd = g0 * d0[j] + g1 * d1[j];
+                o0[j] = dir ? 0.0 : g0;
+                o1[j] = dir ? 0.0 : g1;
+                gt1[j] = dir ? 0.0 : g1 * minv[j];
+                acc[0] += dir ? 0.0 : pd;
+                acc[1] += dir ? 0.0 : g0;
             }
             if (col && iz + 1 < m.z1) cl.advance(j, iz);
         }
