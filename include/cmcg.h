@@ -177,6 +177,10 @@ typedef struct {
        (forward and adjoint), split by stepping precision; 0 otherwise */
     double step_seconds_fp32, step_seconds_fp64;
     long long step_launches_fp32, step_launches_fp64;
+    /* flexible-CG iterations (CMCG_FLAG_INEXACT_RIESZ) replayed as one captured CUDA graph
+       each; the rest ran as separate launches (the solve's stream was 0, the legacy or the
+       per-thread default stream, or capture failed) */
+    long long graph_replays;
 } cmcg_stats;
 
 typedef struct {

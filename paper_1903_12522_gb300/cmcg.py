@@ -64,7 +64,7 @@ class Stats(C.Structure):
                 ("lambda_im", C.c_double), ("point_updates", C.c_longlong), ("seconds", C.c_double),
                 ("kernel_launches", C.c_longlong), ("runup_periods", C.c_int), ("step_seconds_fp32", C.c_double),
                 ("step_seconds_fp64", C.c_double), ("step_launches_fp32", C.c_longlong),
-                ("step_launches_fp64", C.c_longlong)]
+                ("step_launches_fp64", C.c_longlong), ("graph_replays", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -167,12 +167,17 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
 int cuda_status() { return cudaGetLastError() == cudaSuccess ? CMCG_OK : CMCG_ERR_CUDA; }
 
 // Fold completed event pairs into the per-precision step times.
+// A pair without an elapsed time is skipped, and the error it raised is cleared unless an
+// earlier one is pending.
 void collect_timing(cmcg_handle* H) {
+    const cudaError_t pending = cudaPeekAtLastError();
     for (int p = 0; p < H->ev_used; ++p) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, H->ev[2 * p], H->ev[2 * p + 1]) == cudaSuccess) {
             H->step_s[H->ev_fp32[p] ? 1 : 0] += 1e-3 * ms;
             H->step_n[H->ev_fp32[p] ? 1 : 0] += H->ev_steps[p];
+        } else if (pending == cudaSuccess) {
+            cudaGetLastError();
         }
     }
     H->ev_used = 0;
@@ -185,22 +190,42 @@ int sync_read(cmcg_handle* H) {
     return cuda_status();
 }
 
+// True while the handle's stream is being captured into a CUDA graph.
+static bool capturing(cmcg_handle* H) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(H->st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Inside a capture an event record becomes a graph node only when marked external; a replay
+// then records the event like a plain launch would.
+static void record_event(cmcg_handle* H, cudaEvent_t e) {
+    if (capturing(H))
+        cudaEventRecordWithFlags(e, H->st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, H->st);
+}
+
 // Event pair around a period's step loop (only with CMCG_FLAG_TIMING).  Returns the slot.
 int timing_begin(cmcg_handle* H, bool fp32, int steps) {
     if (!H->timing) return -1;
-    if (H->ev_used == 4) {  // all slots busy: wait for them
+    if (H->ev_used == 4) {  // all slots busy: wait for them (never inside a capture)
+        if (capturing(H)) return -1;
         cudaStreamSynchronize(H->st);
         collect_timing(H);
     }
     const int p = H->ev_used++;
     H->ev_fp32[p] = fp32;
     H->ev_steps[p] = steps;
-    cudaEventRecord(H->ev[2 * p], H->st);
+    record_event(H, H->ev[2 * p]);
     return p;
 }
 
 void timing_end(cmcg_handle* H, int p) {
-    if (p >= 0) cudaEventRecord(H->ev[2 * p + 1], H->st);
+    if (p >= 0) record_event(H, H->ev[2 * p + 1]);
 }
 
 // ---- period drivers ------------------------------------------------------------------------
@@ -573,20 +598,26 @@ void apply_B(cmcg_handle* H, bool first, bool lowp) {
 }
 
 // One CG iteration captured as a CUDA graph.  Capture needs a created stream that is not
-// already being captured, and no step timing (its event bookkeeping runs on the host); any
-// failure leaves the caller on plain launches.  A replay advances the host-side counters
-// (periods, Riesz maps, launches) by what the captured iteration would have added.
+// already being captured; any failure leaves the caller on plain launches.  A replay advances
+// the host-side counters (periods, Riesz maps, launches) by what the captured iteration would
+// have added.  With step timing the event records are graph nodes: a replay re-records the
+// same slots, and the host bookkeeping of those slots (precision, step count) is restored
+// from the capture.  If the first replay's events give no elapsed time, the graph is dropped
+// and timing goes on with plain launches.
 struct IterationGraph {
     cudaGraphExec_t exec = nullptr;
     long long periods = 0, riesz = 0, launches = 0;
+    int ev_used = 0;
+    bool ev_fp32[4] = {};
+    int ev_steps[4] = {};
+    long long timed_replays = 0;
     template <typename F>
     void capture(cmcg_handle* H, F body) {
         cudaStream_t st = H->st;
-        if (H->timing || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return;
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
-            cudaGetLastError();
-            return;
+        if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread || capturing(H)) return;
+        if (H->timing && H->ev_used != 0) {  // captured slots start at 0
+            if (cudaStreamSynchronize(st) != cudaSuccess) return;
+            collect_timing(H);
         }
         const long long p0 = H->periods, r0 = H->riesz_iters, l0 = launch_count();
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -599,23 +630,59 @@ struct IterationGraph {
         periods = H->periods - p0;
         riesz = H->riesz_iters - r0;
         launches = launch_count() - l0;
+        ev_used = H->ev_used;
+        for (int p = 0; p < ev_used; ++p) {
+            ev_fp32[p] = H->ev_fp32[p];
+            ev_steps[p] = H->ev_steps[p];
+        }
         H->periods = p0;  // nothing ran yet
         H->riesz_iters = r0;
+        H->ev_used = 0;
         note_launch(-launches);
         if (ce == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
     }
     bool replay(cmcg_handle* H) {
-        if (!exec || cudaGraphLaunch(exec, H->st) != cudaSuccess) return false;
+        if (!exec) return false;
+        if (H->timing && ev_used > 0) {
+            if (timed_replays == 1 && H->step_n[0] + H->step_n[1] == steps_before) {
+                drop();  // the graph's event records gave no elapsed time
+                return false;
+            }
+            if (H->ev_used != 0) {
+                cudaStreamSynchronize(H->st);
+                collect_timing(H);
+            }
+            if (timed_replays == 0) steps_before = H->step_n[0] + H->step_n[1];
+        }
+        if (cudaGraphLaunch(exec, H->st) != cudaSuccess) {
+            cudaGetLastError();
+            drop();
+            return false;
+        }
+        if (H->timing) {
+            H->ev_used = ev_used;
+            for (int p = 0; p < ev_used; ++p) {
+                H->ev_fp32[p] = ev_fp32[p];
+                H->ev_steps[p] = ev_steps[p];
+            }
+            ++timed_replays;
+        }
         H->periods += periods;
         H->riesz_iters += riesz;
+        ++H->graph_replays;
         note_launch(launches);
         return true;
     }
-    ~IterationGraph() {
+    void drop() {
         if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
     }
+    ~IterationGraph() { drop(); }
+
+  private:
+    long long steps_before = 0;
 };
 
 // Flexible CG (Polak-Ribiere) on the current gradient in (gh0, gh1) with z = B rhat;
@@ -891,6 +958,7 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
     h->ev_used = 0;
     h->riesz_iters = 0;
     h->periods = 0;
+    h->graph_replays = 0;
     const long long n = h->g.np;
     int rc;
     if (h->first_order) {
@@ -960,6 +1028,7 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
     st->step_seconds_fp32 = h->step_s[1];
     st->step_launches_fp64 = h->step_n[0];
     st->step_launches_fp32 = h->step_n[1];
+    st->graph_replays = h->graph_replays;
     return rc;
 }
 

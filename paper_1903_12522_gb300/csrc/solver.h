@@ -59,6 +59,7 @@ struct cmcg_handle {
     // counters of the current call
     long long riesz_iters = 0;
     long long periods = 0;
+    long long graph_replays = 0;
     // CMCG_FLAG_TIMING: event pairs around the step loops of the periods since the last sync
     bool timing = false;
     cudaEvent_t ev[8] = {};

@@ -292,6 +292,32 @@ def test_graph_replayed_iterations_match_plain_launches(precision, tol):
     assert torch.equal(ug, up)
     for k in ("iterations", "periods", "riesz_iterations", "kernel_launches", "outer_iterations"):
         assert sg[k] == sp[k], (k, sg[k], sp[k])
+    assert sp["graph_replays"] == 0
+    assert 0 < sg["graph_replays"] < sg["iterations"] + 1
+
+
+@pytest.mark.parametrize("precision", [cmcg.FP64, cmcg.MIXED])
+def test_step_timing_inside_replayed_graphs(precision):
+    # with step timing on, the event records are nodes of the captured iteration: the step
+    # kernels' device time and launch count come out as with plain launches, and the
+    # iterations are still replayed
+    w = wl.sphere_3d(n=24)
+    flags = cmcg.FLAG_INEXACT_RIESZ | cmcg.FLAG_TIMING
+    out = {}
+    for name, stream in (("graph", torch.cuda.Stream()), ("plain", torch.cuda.default_stream())):
+        s = solver_of(w, precision, flags=flags, stream=stream)
+        out[name] = s.solve(w.f, w.g, tol=1e-9)
+    (ug, sg), (up, sp) = out["graph"], out["plain"]
+    assert torch.equal(ug, up)
+    assert sg["graph_replays"] >= sg["iterations"] - 2 > 0, (sg["graph_replays"], sg["iterations"])
+    assert sp["graph_replays"] == 0
+    for k in ("step_launches_fp32", "step_launches_fp64", "kernel_launches", "periods"):
+        assert sg[k] == sp[k], (k, sg[k], sp[k])
+    key = "step_seconds_fp64" if precision == cmcg.FP64 else "step_seconds_fp32"
+    n_key = key.replace("seconds", "launches")
+    assert sg[n_key] > 0
+    per_g, per_p = sg[key] / sg[n_key], sp[key] / sp[n_key]
+    assert 0.25 * per_p < per_g < 4 * per_p, (per_g, per_p)
 
 
 def test_solve_host_matches_device():
