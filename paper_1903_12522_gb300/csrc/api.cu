@@ -233,7 +233,7 @@ void timing_end(cmcg_handle* H, int p) {
 // separate so that the multi-solve engine can run the step loops of many solves in one
 // batched kernel.
 template <typename T>
-PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool src) {
+PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool src, bool w0f_ready) {
     const Geom& g = H->g;
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
@@ -245,7 +245,7 @@ PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool
     b.w0t = w0;
     if (std::is_same<T, float>::value) {
         float* w0f = (float*)H->tmp;
-        launch_to_float(g.np, w0, w0f, H->st);
+        if (!w0f_ready) launch_to_float(g.np, w0, w0f, H->st);
         b.w0t = w0f;
     }
     launch_start<T>(g, H->order, (const T*)b.w0t, w1, (T*)b.prev, (T*)b.cur, kap, src ? H->S : nullptr, H->dt,
@@ -348,22 +348,23 @@ void fwd_end(cmcg_handle* H, const PeriodBuffers& b, const double* w1, bool src,
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     const double thN = H->omega * H->N * H->dt;
-    launch_end<T>(g, H->order, mode, (const T*)b.cur, (const T*)b.prev, (const T*)b.w0t, w1, kap, H->mass,
+    launch_end<T>(g, H->order, fp32_handoff<T>(mode) ? 2 : mode, (const T*)b.cur, (const T*)b.prev,
+                  (const T*)b.w0t, w1, kap, H->mass,
                   src ? H->S : nullptr, cos(thN), sin(thN), out0, out1, H->red(), H->dt, zce, H->st);
     H->periods += 1;
 }
 
 template <typename T>
 void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src, int mode, double* out0,
-                    double* out1) {
-    PeriodBuffers b = fwd_begin<T>(H, w0, w1, src);
+                    double* out1, bool w0f_ready) {
+    PeriodBuffers b = fwd_begin<T>(H, w0, w1, src, w0f_ready);
     fwd_steps<T>(H, b, src);
     fwd_end<T>(H, b, w1, src, mode, out0, out1);
 }
 
 // Adjoint (transposed) period of the cotangents (a, b).
 template <typename T>
-PeriodBuffers adj_begin(cmcg_handle* H, const double* a, const double* bb) {
+PeriodBuffers adj_begin(cmcg_handle* H, const double* a, const double* bb, int mode) {
     const Geom& g = H->g;
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
@@ -371,6 +372,13 @@ PeriodBuffers adj_begin(cmcg_handle* H, const double* a, const double* bb) {
     b.cur = H->ya;
     b.prev = H->yb;
     b.w0t = nullptr;
+    if constexpr (std::is_same<T, float>::value) {
+        if (fp32_handoff<T>(mode)) {  // t = D^-1 z1 came with z0 from the forward end
+            launch_adj_start<float, float>(g, H->order, (const float*)a, (const float*)bb, H->mass, kap,
+                                           (float*)b.cur, (float*)b.prev, H->dt, zce, H->st);
+            return b;
+        }
+    }
     T* t = (T*)H->tmp;
     launch_adj_prep<T>(g, bb, H->mass, kap, t, zce, H->st);
     launch_adj_start<T>(g, H->order, a, t, H->mass, kap, (T*)b.cur, (T*)b.prev, H->dt, zce, H->st);
@@ -413,15 +421,15 @@ void adj_end(cmcg_handle* H, const PeriodBuffers& b, const double* a, const doub
     const Geom& g = H->g;
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
-    launch_adj_final<T>(g, H->order, mode, (const T*)b.cur, (const T*)b.prev, H->mass, kap, H->minv, a, bb, d0, d1,
-                        o0, o1, gt1, H->red(), H->dt, zce, H->st);
+    launch_adj_final<T>(g, H->order, fp32_handoff<T>(mode) ? 2 : mode, (const T*)b.cur, (const T*)b.prev, H->mass,
+                        kap, H->minv, a, bb, d0, d1, o0, o1, gt1, H->red(), H->dt, zce, H->st);
     H->periods += 1;
 }
 
 template <typename T>
 void adjoint_period(cmcg_handle* H, const double* a, const double* bb, int mode, const double* d0, const double* d1,
                     double* o0, double* o1, double* gt1) {
-    PeriodBuffers b = adj_begin<T>(H, a, bb);
+    PeriodBuffers b = adj_begin<T>(H, a, bb, mode);
     adj_steps<T>(H, b);
     adj_end<T>(H, b, a, bb, mode, d0, d1, o0, o1, gt1);
 }
@@ -573,9 +581,9 @@ int riesz_solve(cmcg_handle* H, const double* rhs, double* x, int* iters_out) {
 // z -> (z0, z1); J -> sc[SC_J].
 template <typename T>
 int gradient(cmcg_handle* H, const double* w0, const double* w1, bool src, const double* dd0, const double* dd1,
-             bool riesz) {
-    forward_period<T>(H, w0, w1, src, 0, H->z0, H->z1);
-    adjoint_period<T>(H, H->z0, H->z1, 0, dd0, dd1, H->gh0, H->gh1, H->gt1);
+             bool riesz, bool w0f_ready) {
+    forward_period<T>(H, w0, w1, src, 0, H->z0, H->z1, w0f_ready);
+    adjoint_period<T>(H, H->z0, H->z1, 0, dd0, dd1, H->gh0, H->gh1, riesz ? H->gt1 : nullptr);
     if (!riesz) return CMCG_OK;
     int rc = riesz_solve(H, H->gh0, H->gt0, nullptr);
     return rc < 0 ? rc : CMCG_OK;
@@ -586,10 +594,10 @@ bool inexact(const cmcg_handle* H) { return (H->opt.flags & CMCG_FLAG_INEXACT_RI
 // Approximate Riesz map z = B rhat into (r0, r1): one V-cycle on rhat0 (W-mean removed when K
 // is singular), M^-1 rhat1; reduces gamma = z . rhat (and the Polak-Ribiere beta unless first).
 // lowp: inside a solve with FP32 periods, the pointwise work and the dots run in FP32.
-void apply_B(cmcg_handle* H, bool first, bool lowp) {
+void apply_B(cmcg_handle* H, bool first, bool lowp, bool b_ready) {
     const Geom& g = H->g;
     Red red = H->red();
-    launch_to_float(g.np, H->rh0, H->lv[0].b, H->st);
+    if (!b_ready) launch_to_float(g.np, H->rh0, H->lv[0].b, H->st);
     vcycle(H, 0);
     if (!H->has_dir) launch_wsum_float(g, H->lv[0].x, red, H->st);
     launch_fcg_dots(g, H->lv[0].x, H->volume, !H->has_dir, lowp, H->rh0, H->rh1, H->minv, H->gh0, H->gh1, H->r0, H->r1,
@@ -701,11 +709,16 @@ int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_o
     if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
     double rel = H->hsc[SC_REL];
     int it = 0;
+    // FP32 periods read float(d0); the direction update writes it for the next iteration, and
+    // the dual-residual update writes float(rhat0) for the V-cycle
+    const bool f32 = std::is_same<T, float>::value;
+    float* d0f = f32 ? (float*)H->tmp : nullptr;
+    if (f32) launch_to_float(n, H->d0, d0f, H->st);
     auto body = [&]() {
-        gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1, false);        // 5.1: ghat_d = H d
-        launch_fcg_update(n, H->w0, H->w1, H->rh0, H->rh1, H->d0, H->d1, H->gh0, H->gh1, red, H->st);
-        apply_B(H, false, std::is_same<T, float>::value);              // 5.2 on the residual
-        launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st);  // 5.7
+        gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1, false, f32);  // 5.1: ghat_d = H d
+        launch_fcg_update(n, H->w0, H->w1, H->rh0, H->rh1, H->d0, H->d1, H->gh0, H->gh1, red, H->st, H->lv[0].b);
+        apply_B(H, false, f32, true);                                      // 5.2 on the residual
+        launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st, d0f);  // 5.7
     };
     // The iteration's launches and arguments do not change (its scalars live on the device), so
     // it is captured once as a CUDA graph and replayed: on small grids the host's launch rate,
@@ -1033,20 +1046,22 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
 }
 
 
-template PeriodBuffers fwd_begin<float>(cmcg_handle*, const double*, const double*, bool);
-template PeriodBuffers fwd_begin<double>(cmcg_handle*, const double*, const double*, bool);
+template PeriodBuffers fwd_begin<float>(cmcg_handle*, const double*, const double*, bool, bool);
+template PeriodBuffers fwd_begin<double>(cmcg_handle*, const double*, const double*, bool, bool);
 template void fwd_end<float>(cmcg_handle*, const PeriodBuffers&, const double*, bool, int, double*, double*);
 template void fwd_end<double>(cmcg_handle*, const PeriodBuffers&, const double*, bool, int, double*, double*);
-template PeriodBuffers adj_begin<float>(cmcg_handle*, const double*, const double*);
-template PeriodBuffers adj_begin<double>(cmcg_handle*, const double*, const double*);
+template PeriodBuffers adj_begin<float>(cmcg_handle*, const double*, const double*, int);
+template PeriodBuffers adj_begin<double>(cmcg_handle*, const double*, const double*, int);
 template void adj_end<float>(cmcg_handle*, const PeriodBuffers&, const double*, const double*, int, const double*,
                              const double*, double*, double*, double*);
 template void adj_end<double>(cmcg_handle*, const PeriodBuffers&, const double*, const double*, int, const double*,
                               const double*, double*, double*, double*);
 template void runup<float>(cmcg_handle*, int, double*, double*);
-template int gradient<double>(cmcg_handle*, const double*, const double*, bool, const double*, const double*, bool);
-template int gradient<float>(cmcg_handle*, const double*, const double*, bool, const double*, const double*, bool);
-template void forward_period<double>(cmcg_handle*, const double*, const double*, bool, int, double*, double*);
+template int gradient<double>(cmcg_handle*, const double*, const double*, bool, const double*, const double*, bool,
+                               bool);
+template int gradient<float>(cmcg_handle*, const double*, const double*, bool, const double*, const double*, bool,
+                              bool);
+template void forward_period<double>(cmcg_handle*, const double*, const double*, bool, int, double*, double*, bool);
 
 }  // namespace detail
 }  // namespace cmcg

@@ -201,7 +201,7 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
             cmcg_handle* h = e->slots[inner[i]].h;
             on_side(e, h, lane + i, [&](cmcg_handle* hh) {
                 fwd_end<float>(hh, after_steps(fb[i], hh->N - 1), hh->d1, false, 0, hh->z0, hh->z1);
-                ab[i] = adj_begin<float>(hh, hh->z0, hh->z1);
+                ab[i] = adj_begin<float>(hh, hh->z0, hh->z1, 0);
             });
             items[m + i] = make_item(h, ab[i], true);
             items[m + i].offset = total_a;
@@ -217,10 +217,10 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
             on_side(e, h, lane + i, [&](cmcg_handle* hh) {
                 const long long n = hh->g.np;
                 adj_end<float>(hh, after_steps(ab[i], hh->N - 1), hh->z0, hh->z1, 0, hh->d0, hh->d1, hh->gh0, hh->gh1,
-                               hh->gt1);
+                               nullptr);
                 launch_fcg_update(n, hh->w0, hh->w1, hh->rh0, hh->rh1, hh->d0, hh->d1, hh->gh0, hh->gh1, hh->red(),
-                                  hh->st);
-                apply_B(hh, false, true);
+                                  hh->st, hh->lv[0].b);
+                apply_B(hh, false, true, true);
                 launch_cg_direction(n, hh->r0, hh->r1, hh->d0, hh->d1, hh->red(), hh->st);
             });
         }

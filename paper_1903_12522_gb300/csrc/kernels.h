@@ -30,6 +30,9 @@ void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, 
 template <typename T>
 void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y0, T* y1, const T* kap,
                   const double* S, double dt, int zc, cudaStream_t st);
+// mode 0: z = E (Pi(w) - w) and J; mode 1: (y(T), y_t(T)); mode 2 (T = float only): mode 0
+// with z0 and t = D^-1 z1 written as floats into out0 and out1 (the FP32 hand-off to the
+// adjoint period: launch_adj_start with a = z0 and t, then launch_adj_final mode 2).
 template <typename T>
 void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const T* w0t, const double* w1,
                 const T* kap, const double* mass, const double* S, double cs, double sn, double* out0, double* out1,
@@ -37,9 +40,12 @@ void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, 
 template <typename T>
 void launch_adj_prep(const Geom& g, const double* b, const double* mass, const T* kap, T* t, int zc,
                      cudaStream_t st);
-template <typename T>
-void launch_adj_start(const Geom& g, int order, const double* a, const T* t, const double* mass, const T* kap,
+// a: double, or (T = float) float for the FP32 hand-off.
+template <typename T, typename A>
+void launch_adj_start(const Geom& g, int order, const A* a, const T* t, const double* mass, const T* kap,
                       T* cur, T* prev, double dt, int zc, cudaStream_t st);
+// mode 0: gradient (gt1 may be null); mode 1: q; mode 2 (T = float only): mode 0 reading the
+// FP32 hand-off (z0, t) through z0 and z1.
 template <typename T>
 void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass, const T* kap,
                       const double* minv, const double* z0, const double* z1, const double* d0, const double* d1,
@@ -104,8 +110,9 @@ void launch_cg_init(long long n, const double* gt0, const double* gt1, const dou
 void launch_cg_update(long long n, double* w0, double* w1, double* r0, double* r1, double* rh0, double* rh1,
                       const double* d0, const double* d1, const double* gt0, const double* gt1, const double* gh0,
                       const double* gh1, double sign, Red red, cudaStream_t st);
+// d0f (optional): also float(d0).
 void launch_cg_direction(long long n, const double* r0, const double* r1, double* d0, double* d1, Red red,
-                         cudaStream_t st);
+                         cudaStream_t st, float* d0f = nullptr);
 // Reductions on the solution for the compatibility-condition shift: sums of
 // (F re, F im, (M u) re, (M u) im, (B u) re, (B u) im) into sc[SC_R0..SC_R5].
 void launch_recover(const Geom& g, const double* w0, const double* w1, double omega_hat, const double* S,
@@ -113,8 +120,10 @@ void launch_recover(const Geom& g, const double* w0, const double* w1, double om
 void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t st);
 void launch_reciprocal(long long n, const double* m, double* out, cudaStream_t st);
 // Flexible CG with an approximate Riesz map (one multigrid V-cycle).
+// bf (optional): also float(rhat0), the V-cycle's right-hand side.
 void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double* rh1, const double* d0,
-                       const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st);
+                       const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st,
+                       float* bf = nullptr);
 // lowp: FP32 arithmetic with compensated FP32 partial sums (inside an FP32-period solve).
 void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, bool lowp, const double* rh0,
                      const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,

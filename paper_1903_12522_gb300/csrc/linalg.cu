@@ -167,15 +167,18 @@ __global__ void __launch_bounds__(kT) k_cg_update(long long n, double* __restric
     }
 }
 
-// Step 5.7: d = r + beta d.
+// Step 5.7: d = r + beta d; with d0f, also float(d0) (what FP32 periods read).
 __global__ void __launch_bounds__(kT) k_cg_direction(long long n, const double* __restrict__ r0,
                                                      const double* __restrict__ r1, double* __restrict__ d0,
-                                                     double* __restrict__ d1, const double* __restrict__ sc) {
+                                                     double* __restrict__ d1, float* __restrict__ d0f,
+                                                     const double* __restrict__ sc) {
     const double beta = sc[SC_BETA];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        d0[j] = r0[j] + beta * d0[j];
+        const double v = r0[j] + beta * d0[j];
+        d0[j] = v;
         d1[j] = r1[j] + beta * d1[j];
+        if (d0f) d0f[j] = (float)v;
     }
 }
 
@@ -290,19 +293,22 @@ __global__ void k_reciprocal(long long n, const double* __restrict__ m, double* 
 
 // ---- flexible CG with an approximate Riesz map B ~ E^-1 --------------------------------
 // Step 5.3-5.5 with the dual residual: alpha = gamma / (ghat_d . d); v -= alpha d;
-// rhat -= alpha ghat_d.  The primal residual z = B rhat is formed afterwards (k_fcg_dots).
+// rhat -= alpha ghat_d.  The primal residual z = B rhat is formed afterwards (k_fcg_dots); with
+// bf, float(rhat0) is written for its V-cycle.
 __global__ void __launch_bounds__(kT) k_fcg_update(long long n, double* __restrict__ w0, double* __restrict__ w1,
                                                    double* __restrict__ rh0, double* __restrict__ rh1,
                                                    const double* __restrict__ d0, const double* __restrict__ d1,
                                                    const double* __restrict__ gh0, const double* __restrict__ gh1,
-                                                   double* __restrict__ sc) {
+                                                   float* __restrict__ bf, double* __restrict__ sc) {
     const double alpha = sc[SC_GAMMA] / sc[SC_GD];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         w0[j] -= alpha * d0[j];
         w1[j] -= alpha * d1[j];
-        rh0[j] -= alpha * gh0[j];
+        const double r = rh0[j] - alpha * gh0[j];
+        rh0[j] = r;
         rh1[j] -= alpha * gh1[j];
+        if (bf) bf[j] = (float)r;
     }
 }
 
@@ -419,9 +425,9 @@ void launch_cg_update(long long n, double* w0, double* w1, double* r0, double* r
 }
 
 void launch_cg_direction(long long n, const double* r0, const double* r1, double* d0, double* d1, Red red,
-                         cudaStream_t st) {
+                         cudaStream_t st, float* d0f) {
     note_launch(1);
-    k_cg_direction<<<vec_blocks(n), kT, 0, st>>>(n, r0, r1, d0, d1, red.sc);
+    k_cg_direction<<<vec_blocks(n), kT, 0, st>>>(n, r0, r1, d0, d1, d0f, red.sc);
 }
 
 void launch_scalar_residual(long long n, const double* r0, const double* r1, const double* rh0,
@@ -462,9 +468,9 @@ void launch_reciprocal(long long n, const double* m, double* out, cudaStream_t s
 }
 
 void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double* rh1, const double* d0,
-                       const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st) {
+                       const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st, float* bf) {
     note_launch(1);
-    k_fcg_update<<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, rh0, rh1, d0, d1, gh0, gh1, red.sc);
+    k_fcg_update<<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, rh0, rh1, d0, d1, gh0, gh1, bf, red.sc);
 }
 
 void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, bool lowp, const double* rh0,

@@ -1,6 +1,7 @@
 // Internal: the solver handle and the host-side pieces shared by the single-solve entry
 // points (api.cu) and the multi-solve engine (engine.cu).
 #pragma once
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -85,24 +86,35 @@ struct PeriodBuffers {
 int cuda_status();
 int sync_read(cmcg_handle* H);
 bool inexact(const cmcg_handle* H);
-void apply_B(cmcg_handle* H, bool first, bool lowp);
+// b_ready: the finest level's right-hand side already holds float(rhat0) (written by the
+// flexible-CG update), so the conversion pass is skipped.
+void apply_B(cmcg_handle* H, bool first, bool lowp, bool b_ready = false);
 int adj_step_flags(int k, int N);
+// Gradient periods (mode 0) in FP32 hand z from the forward end to the adjoint period as
+// floats in the z buffers: z0, and t = D^-1 z1 (D = M (1 + beta)) in place of z1.
 template <typename T>
-PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool src);
+constexpr bool fp32_handoff(int mode) {
+    return std::is_same<T, float>::value && mode == 0;
+}
+// w0f_ready (FP32): the temp buffer already holds float(w0) (written by the CG direction update).
+template <typename T>
+PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool src, bool w0f_ready = false);
 template <typename T>
 void fwd_end(cmcg_handle* H, const PeriodBuffers& b, const double* w1, bool src, int mode, double* out0,
              double* out1);
+// mode as for adj_end: with the FP32 hand-off (mode 0, T = float) a and bb are its float z0 and t.
 template <typename T>
-PeriodBuffers adj_begin(cmcg_handle* H, const double* a, const double* bb);
+PeriodBuffers adj_begin(cmcg_handle* H, const double* a, const double* bb, int mode);
 template <typename T>
 void adj_end(cmcg_handle* H, const PeriodBuffers& b, const double* a, const double* bb, int mode, const double* d0,
              const double* d1, double* o0, double* o1, double* gt1);
+// riesz: also the exact Riesz map of the gradient (needs g~1 = ghat1 / M, written only then).
 template <typename T>
 int gradient(cmcg_handle* H, const double* w0, const double* w1, bool src, const double* dd0, const double* dd1,
-             bool riesz);
+             bool riesz, bool w0f_ready = false);
 template <typename T>
 void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src, int mode, double* out0,
-                    double* out1);
+                    double* out1, bool w0f_ready = false);
 // Step (6): U from (w0, w1) into u and the compatibility-condition shift; fills st's
 // lambda fields.  Synchronises the stream.
 int recover(cmcg_handle* h, double* u, cmcg_stats* st);

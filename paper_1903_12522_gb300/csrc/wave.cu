@@ -412,7 +412,10 @@ __global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, c
     }
 }
 
-// Period end: vN, mismatch, energy operator and J (MODE 0), or (uT, vT) (MODE 1).
+// Period end: vN, mismatch, energy operator and J (MODE 0), or (uT, vT) (MODE 1).  MODE 2
+// (FP32 periods inside a gradient) is MODE 0 with an FP32 hand-off to the adjoint period: out0
+// holds z0 and out1 holds t = e1 / (1 + beta) = D^-1 z1 (D = M (1 + beta)), both as floats,
+// which is what the adjoint start needs, so it has no separate D^-1 pass.
 // The FP32 instantiation is held to fewer registers for occupancy (the FP64 one would spill):
 // 384 -> 323 us per launch at 257^3.
 template <typename T>
@@ -452,8 +455,13 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __r
                 const T W = weight_t<T>(g, m.ix, m.iy, iz);
                 const T z0 = W * ih2 * lap_t<ORDER, T>(g, fe, j, m.ix, m.iy, iz);
                 const T z1 = (T)mass[j] * e1;
-                out0[j] = dir ? 0.0 : (double)z0;
-                out1[j] = dir ? 0.0 : (double)z1;
+                if (MODE == 2) {
+                    ((float*)out0)[j] = dir ? 0.f : (float)z0;
+                    ((float*)out1)[j] = dir ? 0.f : (float)(e1 / (T(1) + beta));
+                } else {
+                    out0[j] = dir ? 0.0 : (double)z0;
+                    out1[j] = dir ? 0.0 : (double)z1;
+                }
                 if (std::is_same<T, float>::value)
                     accf.add(dir ? 0.0f : (float)(e0 * z0 + e1 * z1));
                 else
@@ -461,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __r
             }
         }
     }
-    if (MODE == 0) {
+    if (MODE != 1) {
         if (std::is_same<T, float>::value) acc[0] = 0.5 * accf.value();
         if (grid_sum<1>(acc, red.partials, red.ticket) && threadIdx.x == 0) red.sc[SC_J] = acc[0];
     }
@@ -484,8 +492,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_prep(const double* __restrict_
 
 // Adjoint start, part 2 (transposed end velocity):
 //   ybar_N = a + M t / dt - (dt/2) K t,  u_{N-1} = D^-1 ybar_N,  prev = C u_N / M = t / dt.
-template <typename T, int ORDER>
-__global__ void __launch_bounds__(kThreads) k_adj_start(const double* __restrict__ a, const T* __restrict__ t,
+template <typename T, int ORDER, typename A>
+__global__ void __launch_bounds__(kThreads) k_adj_start(const A* __restrict__ a, const T* __restrict__ t,
                                                         const double* __restrict__ mass, const T* __restrict__ kap,
                                                         T* __restrict__ cur, T* __restrict__ prev, Geom g, double dt,
                                                         int zc) {
@@ -508,10 +516,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_start(const double* __restrict
 
 // Adjoint final (transposed start half-kick), from s = M^-1 ybar_1 and u_1:
 //   q0 = M (s - (1 - beta) u_1) - (dt^2/2) K s,   q1 = dt M (1 - beta) s.
-// MODE 1 writes q.  MODE 0 forms the CG gradient ghat = q - z, g~1 = ghat1 / M, and reduces
-// (ghat . d, sum ghat0) in FP64.
+// MODE 1 writes q.  MODE 0 forms the CG gradient ghat = q - z, g~1 = ghat1 / M (only when gt1
+// is given: the exact Riesz map needs it, the V-cycle does not), and reduces
+// (ghat . d, sum ghat0).  MODE 2 (FP32) is MODE 0 on the FP32 hand-off of k_end: z0 in z0, and
+// z1 = M (1 + beta) t from t in z1.
 template <typename T, int ORDER, int MODE>
-__global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s, const T* __restrict__ u1,
+__global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_adj_final(const T* __restrict__ s, const T* __restrict__ u1,
                                                         const double* __restrict__ mass, const T* __restrict__ kap,
                                                         const double* __restrict__ minv,
                                                         const double* __restrict__ z0, const double* __restrict__ z1,
@@ -545,12 +555,20 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
             } else if (std::is_same<T, float>::value) {
                 // FP32 periods: z came from FP32 values, so the differences and products stay in
                 // FP32 (FP64 only holds the stored vectors)
-                const float g0 = (float)q0 - (float)z0[j];
-                const float g1 = (float)q1 - (float)z1[j];
+                float zz0, zz1;
+                if (MODE == 2) {
+                    zz0 = ((const float*)z0)[j];
+                    zz1 = (float)M * ((float)(T(1) + beta) * ((const float*)z1)[j]);
+                } else {
+                    zz0 = (float)z0[j];
+                    zz1 = (float)z1[j];
+                }
+                const float g0 = (float)q0 - zz0;
+                const float g1 = (float)q1 - zz1;
                 const float pd = g0 * (float)d0[j] + g1 * (float)d1[j];
                 o0[j] = dir ? 0.0 : (double)g0;
                 o1[j] = dir ? 0.0 : (double)g1;
-                gt1[j] = dir ? 0.0 : (double)(g1 * (float)minv[j]);
+                if (gt1) gt1[j] = dir ? 0.0 : (double)(g1 * (float)minv[j]);
                 accf0.add(dir ? 0.0f : pd);
                 accf1.add(dir ? 0.0f : g0);
             } else {
@@ -559,14 +577,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_final(const T* __restrict__ s,
                 const double pd = g0 * d0[j] + g1 * d1[j];
                 o0[j] = dir ? 0.0 : g0;
                 o1[j] = dir ? 0.0 : g1;
-                gt1[j] = dir ? 0.0 : g1 * minv[j];
+                if (gt1) gt1[j] = dir ? 0.0 : g1 * minv[j];
                 acc[0] += dir ? 0.0 : pd;
                 acc[1] += dir ? 0.0 : g0;
             }
             if (col && iz + 1 < m.z1) cl.advance(j, iz);
         }
     }
-    if (MODE == 0) {
+    if (MODE != 1) {
         if (std::is_same<T, float>::value) {
             acc[0] = accf0.value();
             acc[1] = accf1.value();
@@ -948,6 +966,13 @@ void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, 
     k_end<T, O, SRC, MODE><<<grid, kThreads, 0, st>>>(yN, yNm1, w0t, w1, kap, mass, S, cs, sn, out0, out1, red, \
                                                       g, dt, zc)
     const bool src = S != nullptr;
+    if constexpr (std::is_same<T, float>::value) {
+        if (mode == 2) {
+            if (order == 2) { if (src) CMCG_END(2, true, 2); else CMCG_END(2, false, 2); }
+            else { if (src) CMCG_END(4, true, 2); else CMCG_END(4, false, 2); }
+            return;
+        }
+    }
     if (order == 2) {
         if (mode == 0) { if (src) CMCG_END(2, true, 0); else CMCG_END(2, false, 0); }
         else { if (src) CMCG_END(2, true, 1); else CMCG_END(2, false, 1); }
@@ -965,14 +990,14 @@ void launch_adj_prep(const Geom& g, const double* b, const double* mass, const T
     k_adj_prep<T><<<plane_grid(g, zc), kThreads, 0, st>>>(b, mass, kap, t, g, zc);
 }
 
-template <typename T>
-void launch_adj_start(const Geom& g, int order, const double* a, const T* t, const double* mass, const T* kap,
+template <typename T, typename A>
+void launch_adj_start(const Geom& g, int order, const A* a, const T* t, const double* mass, const T* kap,
                       T* cur, T* prev, double dt, int zc, cudaStream_t st) {
     note_launch(1);
     if (order == 2)
-        k_adj_start<T, 2><<<plane_grid(g, zc), kThreads, 0, st>>>(a, t, mass, kap, cur, prev, g, dt, zc);
+        k_adj_start<T, 2, A><<<plane_grid(g, zc), kThreads, 0, st>>>(a, t, mass, kap, cur, prev, g, dt, zc);
     else
-        k_adj_start<T, 4><<<plane_grid(g, zc), kThreads, 0, st>>>(a, t, mass, kap, cur, prev, g, dt, zc);
+        k_adj_start<T, 4, A><<<plane_grid(g, zc), kThreads, 0, st>>>(a, t, mass, kap, cur, prev, g, dt, zc);
 }
 
 template <typename T>
@@ -984,6 +1009,12 @@ void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u
 #define CMCG_FIN(O, MODE)                                                                                        \
     k_adj_final<T, O, MODE><<<grid, kThreads, 0, st>>>(s, u1, mass, kap, minv, z0, z1, d0, d1, o0, o1, gt1, red, g, \
                                                        dt, zc)
+    if constexpr (std::is_same<T, float>::value) {
+        if (mode == 2) {
+            if (order == 2) CMCG_FIN(2, 2); else CMCG_FIN(4, 2);
+            return;
+        }
+    }
     if (order == 2) {
         if (mode == 0) CMCG_FIN(2, 0); else CMCG_FIN(2, 1);
     } else {
@@ -1012,14 +1043,16 @@ long long plane_blocks(const Geom& g, int zc) {
                                 const double*, const double*, double, double, double*, double*, Red, double,    \
                                 int, cudaStream_t);                                                            \
     template void launch_adj_prep<T>(const Geom&, const double*, const double*, const T*, T*, int, cudaStream_t); \
-    template void launch_adj_start<T>(const Geom&, int, const double*, const T*, const double*, const T*, T*,   \
-                                      T*, double, int, cudaStream_t);                                          \
+    template void launch_adj_start<T, double>(const Geom&, int, const double*, const T*, const double*, const T*, \
+                                              T*, T*, double, int, cudaStream_t);                               \
     template void launch_adj_final<T>(const Geom&, int, int, const T*, const T*, const double*, const T*,       \
                                       const double*, const double*, const double*, const double*, const double*, \
                                       double*, double*, double*, Red, double, int, cudaStream_t);
 CMCG_INST(float)
 CMCG_INST(double)
 #undef CMCG_INST
+template void launch_adj_start<float, float>(const Geom&, int, const float*, const float*, const double*,
+                                             const float*, float*, float*, double, int, cudaStream_t);
 
 }  // namespace cmcg
 
