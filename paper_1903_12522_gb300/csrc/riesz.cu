@@ -266,6 +266,178 @@ __global__ void __launch_bounds__(kT) k_residual(Geom g, const unsigned char* __
     }
 }
 
+// 3D Jacobi sweep (from a given x) and residual, two z-planes per loop trip: both planes' loads
+// (x with its x/y neighbours, b, the mask byte) are issued before either update, and the
+// z-neighbours come from registers.  The expressions are those of jacobi_node / residual_node
+// with the 7-point Laplacian summed in lap_t's order, so the results are bitwise equal to
+// k_jacobi / k_residual.
+struct Col3 {
+    long long sZ, oxm, oxp, oym, oyp;
+    int exy;  // axis ends of the column in x and y
+};
+
+__device__ __forceinline__ Col3 col3(const Geom& g, int ix, int iy) {
+    Col3 c;
+    c.sZ = (long long)g.sx * g.sy;
+    c.oxm = off_m1(ix, 1);
+    c.oxp = off_p1(ix, g.nx, 1);
+    c.oym = off_m1(iy, g.sx);
+    c.oyp = off_p1(iy, g.ny, g.sx);
+    c.exy = (ix == 0 || ix == g.nx) + (iy == 0 || iy == g.ny);
+    return c;
+}
+
+// MODE 0: Jacobi x_out = x + omega (cB s^-1 b - L / 6); MODE 1: residual r = b - cK s L.
+template <int MODE>
+__global__ void __launch_bounds__(kT) k_mg3_z2(Geom g, const unsigned char* __restrict__ mask,
+                                               const float* __restrict__ x, const float* __restrict__ b,
+                                               float* __restrict__ out, float omega, int zc) {
+    const PlaneIt m = plane_it(g, zc);
+    if (!m.valid || m.z0 >= m.z1) return;
+    const MGConst c = mg_const(g);
+    const Col3 o = col3(g, m.ix, m.iy);
+    const long long sZ = o.sZ;
+    auto update = [&](float xc, float xm, float xp, float sx, float sy, long long jj, int iz, float bj, bool dir) {
+        float acc = sx;
+        acc += sy;
+        acc += xm + xp;
+        const float L = 6.f * xc - acc;
+        const int e = o.exy + (iz == 0 || iz == g.nz);
+        float v;
+        if (MODE == 0) {
+            const float inv_s = (float)(1 << e);
+            v = xc + omega * (c.cB * inv_s * bj - c.inv2d * L);
+        } else {
+            const float s = 1.f / (float)(1 << e);
+            v = bj - c.cK * s * L;
+        }
+        out[jj] = dir ? 0.f : v;
+    };
+    long long j = node(g, m.ix, m.iy, m.z0);
+    float xm = x[j + (m.z0 > 0 ? -sZ : sZ)];
+    float xc = x[j];
+    int iz = m.z0;
+    for (; iz + 1 < m.z1; iz += 2) {
+        const long long j1 = j + sZ;
+        const float x1 = x[j1];                               // plane iz+1 (exists: iz+1 < z1 <= sz)
+        const float x2 = x[j1 + (iz + 1 < g.nz ? sZ : -sZ)];  // plane iz+2 (mirrored at the top)
+        const float sx0 = x[j + o.oxm] + x[j + o.oxp], sy0 = x[j + o.oym] + x[j + o.oyp];
+        const float sx1 = x[j1 + o.oxm] + x[j1 + o.oxp], sy1 = x[j1 + o.oym] + x[j1 + o.oyp];
+        const float b0 = b[j], b1 = b[j1];
+        const bool d0 = mask && mask[j], d1 = mask && mask[j1];
+        update(xc, xm, x1, sx0, sy0, j, iz, b0, d0);
+        update(x1, xc, x2, sx1, sy1, j1, iz + 1, b1, d1);
+        xm = x1;
+        xc = x2;
+        j += 2 * sZ;
+    }
+    if (iz < m.z1) {
+        const float xp = x[j + (iz < g.nz ? sZ : -sZ)];
+        const float sx0 = x[j + o.oxm] + x[j + o.oxp], sy0 = x[j + o.oym] + x[j + o.oyp];
+        update(xc, xm, xp, sx0, sy0, j, iz, b[j], mask && mask[j]);
+    }
+}
+
+// 3D prolongation x_f += P x_c along a thread's fine z-column.  Every fine plane blends the
+// xy-interpolated values of at most two coarse planes; those are kept in registers and
+// reused by the next fine plane (for 2:1 coarsening, one new coarse plane per two fine
+// planes).  Same expressions as prolong_node: bitwise equal to k_prolong_add.
+__global__ void __launch_bounds__(kT) k_prolong_add3(Geom gc, const float* __restrict__ xc, Geom gf,
+                                                     const unsigned char* __restrict__ maskf, float* __restrict__ xf,
+                                                     int zc) {
+    const PlaneIt m = plane_it(gf, zc);
+    if (!m.valid || m.z0 >= m.z1) return;
+    const Interp1 px = interp1_fast(m.ix, gf.nx, gc.nx), py = interp1_fast(m.iy, gf.ny, gc.ny);
+    const int x1 = px.t > 0.f ? px.j0 + 1 : px.j0, y1 = py.t > 0.f ? py.j0 + 1 : py.j0;
+    const float ax = 1.f - px.t, ay = 1.f - py.t;
+    const long long o00 = node(gc, px.j0, py.j0, 0), o10 = node(gc, x1, py.j0, 0);
+    const long long o01 = node(gc, px.j0, y1, 0), o11 = node(gc, x1, y1, 0);
+    const long long planeC = (long long)gc.sx * gc.sy;
+    auto pxy = [&](int J) {
+        const float* cp = xc + (long long)J * planeC;
+        return ay * (ax * cp[o00] + px.t * cp[o10]) + py.t * (ax * cp[o01] + px.t * cp[o11]);
+    };
+    int ja = -1, jb = -1;  // coarse planes held in va, vb
+    float va = 0.f, vb = 0.f;
+    for (int iz = m.z0; iz < m.z1; ++iz) {
+        const long long i = node(gf, m.ix, m.iy, iz);
+        const bool dir = maskf && maskf[i];  // tested at the store (see k_jacobi)
+        const float x0 = xf[i];
+        const Interp1 pz = interp1_fast(iz, gf.nz, gc.nz);  // the same for every thread of the block
+        const int z1 = pz.t > 0.f ? pz.j0 + 1 : pz.j0;
+        const float v0 = pz.j0 == jb ? vb : (pz.j0 == ja ? va : pxy(pz.j0));
+        const float v1 = z1 == pz.j0 ? v0 : (z1 == jb ? vb : pxy(z1));
+        ja = pz.j0;
+        va = v0;
+        jb = z1;
+        vb = v1;
+        const float v = (1.f - pz.t) * v0 + pz.t * v1;
+        if (!dir) xf[i] = x0 + v;
+    }
+}
+
+// 3D restriction for 2:1 coarsening along a thread's coarse z-column.  Coarse plane J gathers
+// fine planes 2J-1, 2J, 2J+1; the x-weighted row sums of plane 2J+1 are kept in registers
+// for plane J+1, so each coarse plane loads two fine planes.  Rows outside the grid are read
+// at a clamped address and left out of the sum, so every load is issued before the sums.  The
+// terms and their order are those of restrict_nested: bitwise equal to k_restrict.
+__global__ void __launch_bounds__(kT) k_restrict3_nested(Geom gf, const float* __restrict__ rf, Geom gc,
+                                                         const unsigned char* __restrict__ maskc,
+                                                         float* __restrict__ bc, int zc) {
+    const PlaneIt m = plane_it(gc, zc);
+    if (!m.valid || m.z0 >= m.z1) return;
+    const int cx = 2 * m.ix, cy = 2 * m.iy;
+    const bool xm = cx > 0, xp = cx < gf.nx;
+    const int xl = xm ? cx - 1 : cx, xr = xp ? cx + 1 : cx;
+    bool yok[3];
+    long long yoff[3];
+    for (int d = 0; d < 3; ++d) {
+        const int fy = cy + d - 1;
+        yok[d] = fy >= 0 && fy <= gf.ny;
+        yoff[d] = (long long)(yok[d] ? fy : cy) * gf.sx;
+    }
+    const long long sZ = (long long)gf.sx * gf.sy;
+    auto rows = [&](int fz, float* r) {  // row sums of fine plane fz (0 <= fz <= nz)
+        const float* pl = rf + (long long)fz * sZ;
+        float a[3], l[3], q[3];
+        for (int d = 0; d < 3; ++d) {
+            a[d] = pl[yoff[d] + cx];
+            l[d] = pl[yoff[d] + xl];
+            q[d] = pl[yoff[d] + xr];
+        }
+        for (int d = 0; d < 3; ++d) {
+            float racc = a[d];
+            if (xm) racc += 0.5f * l[d];
+            if (xp) racc += 0.5f * q[d];
+            r[d] = racc;
+        }
+    };
+    float lo[3] = {0.f, 0.f, 0.f};  // row sums of fine plane 2J - 1
+    bool have_lo = false;
+    for (int jz = m.z0; jz < m.z1; ++jz) {
+        const long long J = node(gc, m.ix, m.iy, jz);
+        const bool dir = maskc && maskc[J];
+        const int cz = 2 * jz;
+        const bool zlo = cz - 1 >= 0, zhi = cz + 1 <= gf.nz;
+        if (zlo && !have_lo) rows(cz - 1, lo);
+        float mid[3], hi[3] = {0.f, 0.f, 0.f};
+        rows(cz, mid);
+        if (zhi) rows(cz + 1, hi);
+        float acc = 0.f;
+        if (zlo)
+            for (int d = 0; d < 3; ++d)
+                if (yok[d]) acc += (d == 1 ? 1.f : 0.5f) * 0.5f * lo[d];
+        for (int d = 0; d < 3; ++d)
+            if (yok[d]) acc += (d == 1 ? 1.f : 0.5f) * 1.f * mid[d];
+        if (zhi)
+            for (int d = 0; d < 3; ++d)
+                if (yok[d]) acc += (d == 1 ? 1.f : 0.5f) * 0.5f * hi[d];
+        bc[J] = dir ? 0.f : acc;
+        for (int d = 0; d < 3; ++d) lo[d] = hi[d];
+        have_lo = zhi;
+    }
+}
+
 // b_c[J] = sum over fine nodes i with |i - 2J|_inf <= 1 of prod_a (1 or 1/2) r_f[i].
 __global__ void __launch_bounds__(kT) k_restrict(Geom gf, const float* __restrict__ rf, Geom gc,
                                                  const unsigned char* __restrict__ maskc, float* __restrict__ bc,
@@ -533,25 +705,39 @@ void launch_mg_jacobi(const MGLevel& L, const float* xin, float* xout, const flo
                       cudaStream_t st) {
     note_launch(1);
     const int zc = L.g.dim == 3 ? 8 : 1;
-    k_jacobi<<<mg_grid(L.g, zc), kT, 0, st>>>(L.g, L.mask, zero_init ? nullptr : xin, xout, b, omega, zc);
+    if (L.g.dim == 3 && !zero_init)
+        k_mg3_z2<0><<<mg_grid(L.g, zc), kT, 0, st>>>(L.g, L.mask, xin, b, xout, omega, zc);
+    else
+        k_jacobi<<<mg_grid(L.g, zc), kT, 0, st>>>(L.g, L.mask, zero_init ? nullptr : xin, xout, b, omega, zc);
 }
 
 void launch_mg_residual(const MGLevel& L, const float* x, const float* b, float* r, cudaStream_t st) {
     note_launch(1);
     const int zc = L.g.dim == 3 ? 8 : 1;
-    k_residual<<<mg_grid(L.g, zc), kT, 0, st>>>(L.g, L.mask, x, b, r, zc);
+    if (L.g.dim == 3)
+        k_mg3_z2<1><<<mg_grid(L.g, zc), kT, 0, st>>>(L.g, L.mask, x, b, r, 0.f, zc);
+    else
+        k_residual<<<mg_grid(L.g, zc), kT, 0, st>>>(L.g, L.mask, x, b, r, zc);
 }
 
 void launch_mg_restrict(const MGLevel& fine, const float* rf, const MGLevel& coarse, float* bc, cudaStream_t st) {
     note_launch(1);
     const int zc = coarse.g.dim == 3 ? 4 : 1;
-    k_restrict<<<mg_grid(coarse.g, zc), kT, 0, st>>>(fine.g, rf, coarse.g, coarse.mask, bc, zc);
+    const Geom& gf = fine.g;
+    const Geom& gc = coarse.g;
+    if (gf.dim == 3 && gf.nx == 2 * gc.nx && gf.ny == 2 * gc.ny && gf.nz == 2 * gc.nz)
+        k_restrict3_nested<<<mg_grid(gc, zc), kT, 0, st>>>(gf, rf, gc, coarse.mask, bc, zc);
+    else
+        k_restrict<<<mg_grid(gc, zc), kT, 0, st>>>(gf, rf, gc, coarse.mask, bc, zc);
 }
 
 void launch_mg_prolong_add(const MGLevel& coarse, const float* xc, const MGLevel& fine, float* xf, cudaStream_t st) {
     note_launch(1);
     const int zc = fine.g.dim == 3 ? 8 : 1;
-    k_prolong_add<<<mg_grid(fine.g, zc), kT, 0, st>>>(coarse.g, xc, fine.g, fine.mask, xf, zc);
+    if (fine.g.dim == 3)
+        k_prolong_add3<<<mg_grid(fine.g, zc), kT, 0, st>>>(coarse.g, xc, fine.g, fine.mask, xf, zc);
+    else
+        k_prolong_add<<<mg_grid(fine.g, zc), kT, 0, st>>>(coarse.g, xc, fine.g, fine.mask, xf, zc);
 }
 
 int mg_block_max_nodes() { return kBlockMaxNodes; }
