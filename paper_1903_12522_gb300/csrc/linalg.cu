@@ -473,12 +473,34 @@ void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double*
     k_fcg_update<<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, rh0, rh1, d0, d1, gh0, gh1, bf, red.sc);
 }
 
+// k_fcg_dots needs more than 32 registers, so fewer than the 8 blocks per SM that
+// kMaxBlocksReduce assumes are resident: its grid-stride grid is one full wave of what this
+// GPU holds at once (cached per device; deterministic for a given GPU and build).
+static unsigned fcg_dots_blocks(long long n) {
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int& c = cached[dev & 63];
+    if (c == 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fcg_dots, kT, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 ||
+            sms < 1) {
+            cudaGetLastError();
+            return vec_blocks(n);
+        }
+        c = per_sm * sms < kMaxBlocksReduce ? per_sm * sms : kMaxBlocksReduce;
+    }
+    const unsigned b = vec_blocks(n);
+    return b < (unsigned)c ? b : (unsigned)c;
+}
+
 void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, bool lowp, const double* rh0,
                      const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,
                      double* z1, Red red, bool first, cudaStream_t st) {
     note_launch(1);
-    k_fcg_dots<<<vec_blocks(g.np), kT, 0, st>>>(g, zf, 1.0 / volume, remove_mean ? 1 : 0, rh0, rh1, minv, gh0, gh1,
-                                                z0, z1, red, first ? 1 : 0, lowp ? 1 : 0);
+    k_fcg_dots<<<fcg_dots_blocks(g.np), kT, 0, st>>>(g, zf, 1.0 / volume, remove_mean ? 1 : 0, rh0, rh1, minv, gh0,
+                                                     gh1, z0, z1, red, first ? 1 : 0, lowp ? 1 : 0);
 }
 
 void launch_wsum_float(const Geom& g, const float* x, Red red, cudaStream_t st) {
