@@ -416,8 +416,9 @@ __global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, c
 // (FP32 periods inside a gradient) is MODE 0 with an FP32 hand-off to the adjoint period: out0
 // holds z0 and out1 holds t = e1 / (1 + beta) = D^-1 z1 (D = M (1 + beta)), both as floats,
 // which is what the adjoint start needs, so it has no separate D^-1 pass.
-// The FP32 instantiation is held to fewer registers for occupancy (the FP64 one would spill):
-// 384 -> 323 us per launch at 257^3.
+// The FP32 instantiations of k_end and k_adj_final are held to five resident blocks per SM
+// (48 registers) for occupancy; the FP64 ones would spill.  k_end: 384 -> 323 us per launch
+// at 257^3; k_adj_final with the hand-off would otherwise take 53 registers.
 template <typename T>
 constexpr int kEndMinBlocks = std::is_same<T, float>::value ? 5 : 1;
 
