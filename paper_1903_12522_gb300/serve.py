@@ -79,6 +79,7 @@ class Request:
         self.admitted = None
         self.finished = None
         self.stats = None
+        self.rejected = False
 
     def grid(self):
         return (self.n,) * self.dim
@@ -129,17 +130,24 @@ def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, 
     running = {}
     used = 0
     done = []
+    rejected = []
     t0 = time.perf_counter()
     updates = 0
     while queue or waiting or running:
         now = time.perf_counter() - t0
         while queue and queue[0].arrival <= now:
             waiting.append(queue.pop(0))
-        # admission: first fit in arrival order by workspace bytes and free slots
+        # admission: first fit in arrival order by workspace bytes and free slots; a request
+        # whose workspace alone exceeds the budget could never start and is rejected
         for req in list(waiting):
             if len(running) >= max_slots:
                 break
             nb = workspace_bytes(req, precision)
+            if nb > budget_bytes:
+                waiting.remove(req)
+                req.rejected = True
+                rejected.append(req)
+                continue
             if used + nb > budget_bytes:
                 continue
             c, f = req.build(device)
@@ -170,14 +178,17 @@ def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, 
     info = eng.info()
     eng.close()
     lat = np.array([r.finished - r.arrival for r in done])
+    latency = None if len(done) == 0 else {
+        "p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+        "mean": 1e3 * float(lat.mean())}
     return {
         "requests": len(done),
+        "rejected": len(rejected),
         "wall_s": wall,
         "solves_per_s": len(done) / wall,
         "updates_per_s": updates / wall,
-        "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
-                       "mean": 1e3 * float(lat.mean())},
-        "queue_ms_mean": 1e3 * float(np.mean([r.admitted - r.arrival for r in done])),
+        "latency_ms": latency,
+        "queue_ms_mean": None if len(done) == 0 else 1e3 * float(np.mean([r.admitted - r.arrival for r in done])),
         "status_ok": int(sum(1 for r in done if r.stats["status"] == cmcg.OK)),
         "ticks": info["ticks"],
         "graph_builds": info["graph_builds"],
