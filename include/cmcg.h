@@ -62,7 +62,9 @@ extern "C" {
 /* ---- option flags ------------------------------------------------------------------ */
 #define CMCG_FLAG_HOST_IO 1 /* reserve a staging buffer in the workspace for cmcg_solve_host */
 #define CMCG_FLAG_TIMING 2  /* time the leapfrog step kernels with CUDA events on the handle's
-                               stream; results in cmcg_stats.step_seconds_* / step_launches_* */
+                               stream; results in cmcg_stats.step_seconds_* / step_launches_*.
+                               Flexible-CG iterations are still replayed as CUDA graphs: the
+                               events are recorded by nodes of the captured iteration */
 #define CMCG_FLAG_INEXACT_RIESZ 4 /* apply the Riesz map of Eq. CMCG_PRECONDITIONIER approximately:
                                one multigrid V-cycle per CG iteration on the dual residual,
                                with flexible (Polak-Ribiere) CG; the fixed point is unchanged
