@@ -305,7 +305,11 @@ int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const do
  * finished in this tick, *n_finished their number. */
 int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_finished);
 /* Status and statistics of a finished slot (CMCG_OK, CMCG_NOT_CONVERGED or an error); frees
- * the slot.  CMCG_ERR_INVALID_ARG if the slot has not finished. */
+ * the slot.  CMCG_ERR_INVALID_ARG if the slot has not finished.  After it returns, the engine
+ * holds nothing of the solve (a cached tick graph that included the slot is dropped): the
+ * caller may destroy the handle and free its workspace, and a new solve admitted into the
+ * same slot, even with a handle at the same address, never replays the old solve's graph.
+ * A handle must not be destroyed while its slot is still active or unread. */
 int cmcg_engine_result(cmcg_engine* e, int slot, cmcg_stats* stats);
 /* Number of solves in progress. */
 int cmcg_engine_active(const cmcg_engine* e);
@@ -329,7 +333,9 @@ int cmcg_engine_barrier_selftest(cmcg_engine* e, long long spin_limit);
  * that loads the library holds until the process exits; grids above 262,144 nodes (for example
  * larger than 511^2 in 2D or 63^3 in 3D) are rejected with CMCG_ERR_WORKSPACE.  The first call
  * on a device looks up the array's device address with cudaGetSymbolAddress (make that first
- * call before any stream capture on that device).  Every call on a device shares the array and
+ * call before any stream capture on that device); the address is kept for the life of the
+ * process, so a device reset (cudaDeviceReset) on a device this entry point has used leaves
+ * it unusable on that device.  Every call on a device shares the array and
  * clears the parts that must start at zero; calls that overlap on the GPU (other streams or
  * threads) race.  Returns after the stream has finished the call's work. */
 int cmcg_wave_period_static(const cmcg_grid* grid, const double* c, double omega, const cmcg_bc* bc,

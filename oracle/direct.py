@@ -43,9 +43,3 @@ def periodic_state(dz: Discretization, U):
     """(v0, v1) = (Re U, wh Im U): the initial data of the discrete periodic solution."""
     return np.real(U) * dz.act, dz.omega_hat * np.imag(U) * dz.act
 
-
-def residual(dz: Discretization, U, F_hat) -> float:
-    """Relative residual ||(K - wt^2 M - i wh B) U - F^|| / ||F^||."""
-    A, ia = helmholtz_matrix(dz)
-    r = A @ np.asarray(U).ravel()[ia] - np.asarray(F_hat).ravel()[ia]
-    return float(np.linalg.norm(r) / max(np.linalg.norm(np.asarray(F_hat).ravel()[ia]), 1e-300))

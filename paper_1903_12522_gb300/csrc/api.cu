@@ -1108,6 +1108,7 @@ int wave_period_in_scratch(const cmcg_grid* grid, const double* c, double omega,
     H.g = make_geom(grid, abc);
     H.order = grid->order;
     H.opt.precision = CMCG_FP64;
+    fill_defaults(&H.opt);  // the same option defaults as a created handle
     H.st = st;
     H.omega = omega;
     H.T = 2.0 * kPi / omega;
@@ -1118,6 +1119,7 @@ int wave_period_in_scratch(const cmcg_grid* grid, const double* c, double omega,
     // the scratch keeps the previous call's contents: clear the reduction slots
     cudaMemsetAsync(H.tickets, 0, sizeof(unsigned) * kNumTickets, st);
     cudaMemsetAsync(H.sc, 0, sizeof(double) * SC_COUNT, st);
+    cudaMemsetAsync(H.sc + 6, 0xFF, sizeof(double), st);  // c_min starts at the largest key, as in cmcg_create
     launch_setup_coeffs(H.g, c, bc->dirichlet_mask, dir, 1.0, H.kap64, nullptr, H.mass, H.mask, H.red(), st);
     if (sync_read(&H) != CMCG_OK) return CMCG_ERR_CUDA;
     if (host_sc[3] != 0.0) return CMCG_ERR_INVALID_ARG;

@@ -9,9 +9,10 @@
 //   - INNER: one flexible-CG iteration with FP32 periods (Steps 5.1-5.7).
 // The FP32 leapfrog step loops of all INNER slots run in ONE batched persistent kernel per
 // period (forward, then adjoint); everything else is per-slot launches.  The tick is captured
-// as a CUDA graph and replayed while the set of (slot, unit) pairs stays the same.  After each
-// tick the host reads every slot's convergence word and moves slots between units; a finished
-// slot gets its recovery (Step (6)) and is released.
+// as a CUDA graph and replayed while the set of (slot, unit, submission number) triples stays
+// the same; releasing a slot drops a cached graph that includes it.  After each tick the host
+// reads every slot's convergence word and moves slots between units; a finished slot gets its
+// recovery (Step (6)) and is released.
 #include <string.h>
 
 #include <algorithm>
@@ -19,6 +20,7 @@
 #include <vector>
 
 #include "cmcg.h"
+#include "engine_sig.h"
 #include "solver.h"
 
 using namespace cmcg;
@@ -32,6 +34,7 @@ enum Unit { U_FREE = 0, U_INIT32, U_OUTER, U_INNER, U_DONE, U_RUNUP };
 
 struct EngineSlot {
     cmcg_handle* h = nullptr;
+    long long submission = 0;  // the engine's submission number of this solve (never reused)
     double* u = nullptr;
     double tol = 0;
     int unit = U_FREE;
@@ -60,8 +63,9 @@ struct cmcg_engine {
     bool use_graph = true;
     // graph cache
     cudaGraphExec_t exec = nullptr;
-    std::vector<long long> signature;       // configuration of the cached graph
-    std::vector<long long> last_signature;  // configuration of the previous tick
+    TickSignature signature;       // configuration of the cached graph
+    TickSignature last_signature;  // configuration of the previous tick
+    long long submissions = 0;     // solves submitted so far (the last submission number)
     long long graph_launches = 0;
     long long ticks = 0, graph_builds = 0;
     cudaError_t last_error = cudaSuccess;  // the CUDA error behind the last CMCG_ERR_CUDA
@@ -259,6 +263,17 @@ void upload_items(cmcg_engine* e, const std::vector<int>& act) {
     cudaStreamSynchronize(e->st);
 }
 
+// Drop the cached graph if it includes slot s: the graph holds that solve's device pointers
+// and its pinned status mirror, which the caller may free once the slot is released.
+void drop_graph_of_slot(cmcg_engine* e, int s) {
+    if (e->exec && e->signature.names_slot(s)) {
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+        e->signature.clear();
+    }
+    if (e->last_signature.names_slot(s)) e->last_signature.clear();
+}
+
 int finish_slot(cmcg_engine* e, int s) {
     EngineSlot& sl = e->slots[s];
     cmcg_handle* h = sl.h;
@@ -359,9 +374,11 @@ int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const do
         if (s < 0 && e->slots[i].unit == U_FREE) s = i;
     }
     if (s < 0) return CMCG_ERR_WORKSPACE;  // no free slot
+    drop_graph_of_slot(e, s);
     EngineSlot& sl = e->slots[s];
     sl = EngineSlot();
     sl.h = h;
+    sl.submission = ++e->submissions;
     sl.u = u;
     sl.tol = tol;
     sl.t0 = std::chrono::steady_clock::now();
@@ -395,13 +412,9 @@ int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_fin
         if (u == U_INIT32 || u == U_OUTER || u == U_INNER || u == U_RUNUP) act.push_back(i);
     }
     if (act.empty()) return CMCG_OK;
-    // configuration signature: (slot, unit, handle) of every active slot
-    std::vector<long long> sig;
-    for (int s : act) {
-        sig.push_back(s);
-        sig.push_back(e->slots[s].unit);
-        sig.push_back((long long)(uintptr_t)e->slots[s].h);
-    }
+    // configuration signature: (slot, unit, submission number) of every active slot
+    TickSignature sig;
+    for (int s : act) sig.add(s, e->slots[s].unit, e->slots[s].submission);
     // the batch descriptors follow the configuration of every tick (a cached graph reads them)
     const bool changed = sig != e->last_signature;
     if (changed) upload_items(e, act);
@@ -551,6 +564,9 @@ int cmcg_engine_result(cmcg_engine* e, int slot, cmcg_stats* stats) {
     if (stats) *stats = sl.st;
     const int status = sl.status;
     sl = EngineSlot();
+    // the caller may now destroy the handle and free its workspace: no cached graph may
+    // still point at them
+    drop_graph_of_slot(e, slot);
     return status;
 }
 

@@ -118,13 +118,51 @@ def workspace_bytes(req, precision):
                                     cmcg.make_options(precision, flags=cmcg.FLAG_INEXACT_RIESZ))
 
 
+class WallClock:
+    """Arrivals, admissions and completions on the wall clock (seconds since start)."""
+
+    def __init__(self):
+        self.t0 = time.perf_counter()
+
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def idle_until(self, t):
+        time.sleep(max(0.0, min(t - self.now(), 0.05)))
+
+    def ticked(self):
+        pass
+
+
+class TickClock:
+    """A simulated clock that advances by a fixed time per engine tick and jumps to the next
+    arrival when nothing runs.  Admission then depends only on the request stream and the
+    tick count, not on how fast the GPU or the host happens to be, so a run is repeatable."""
+
+    def __init__(self, tick_s):
+        self.tick_s = float(tick_s)
+        self.t = 0.0
+
+    def now(self):
+        return self.t
+
+    def idle_until(self, t):
+        self.t = max(self.t, t)
+
+    def ticked(self):
+        self.t += self.tick_s
+
+
 def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, device="cuda", log=None,
-          keep_results=False, stream=None, runup=0):
-    """Run the request stream in real time; returns per-request records and totals."""
+          keep_results=False, stream=None, runup=0, tick_s=None):
+    """Run the request stream; returns per-request records and totals.  Arrivals follow the
+    wall clock, or with tick_s a simulated clock that advances tick_s seconds per engine tick
+    (latencies are then in simulated time; wall_s and the rates stay on the wall clock)."""
     import torch
 
     eng = cmcg.Engine(max_slots=max_slots, stream=stream)
     stream = eng.stream
+    clock = TickClock(tick_s) if tick_s else WallClock()
     queue = list(requests)
     waiting = []
     running = {}
@@ -134,7 +172,7 @@ def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, 
     t0 = time.perf_counter()
     updates = 0
     while queue or waiting or running:
-        now = time.perf_counter() - t0
+        now = clock.now()
         while queue and queue[0].arrival <= now:
             waiting.append(queue.pop(0))
         # admission: first fit in arrival order by workspace bytes and free slots; a request
@@ -153,18 +191,20 @@ def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, 
             c, f = req.build(device)
             s = make_solver(req, c, precision, stream, runup)
             slot = eng.submit(s, f, None, tol)
-            req.admitted = time.perf_counter() - t0
+            req.admitted = clock.now()
             running[slot] = (req, s, nb)
             used += nb
             waiting.remove(req)
         if not running:
             if queue:
-                time.sleep(max(0.0, min(queue[0].arrival - (time.perf_counter() - t0), 0.05)))
+                clock.idle_until(queue[0].arrival)
             continue
-        for slot in eng.tick():
+        finished = eng.tick()
+        clock.ticked()
+        for slot in finished:
             req, s, nb = running.pop(slot)
             u, st = eng.result(slot)
-            req.finished = time.perf_counter() - t0
+            req.finished = clock.now()
             req.stats = st
             if keep_results:
                 req.result = u.clone()

@@ -164,9 +164,16 @@ def test_barrier_timeout_is_reported_and_engine_recovers():
 def test_serving_loop_results_match_alone():
     from paper_1903_12522_gb300 import serve
 
+    # arrivals on a simulated clock of 1 ms per tick: the admission pattern (who joins while
+    # whom is running, which slot a request lands in) is the same on every run
     reqs = serve.poisson_requests(8, rate=400.0, seed=9, two_d=(24, 48), three_d=(10, 16))
-    out = serve.serve(reqs, budget_bytes=int(4e9), max_slots=4, tol=1e-7, keep_results=True, stream=engine_stream())
+    out = serve.serve(reqs, budget_bytes=int(4e9), max_slots=4, tol=1e-7, keep_results=True, stream=engine_stream(),
+                      tick_s=1e-3)
     assert out["requests"] == 8 and out["status_ok"] == 8
+    # requests joined while others ran, and some were admitted into slots freed by others
+    assert any(r.admitted > min(q.admitted for q in reqs) and r.admitted < max(q.finished for q in reqs)
+               for r in reqs)
+    assert max(r.admitted for r in reqs) > min(r.finished for r in reqs)
     assert out["latency_ms"]["p50"] <= out["latency_ms"]["p99"]
     # a request solved alone gives the same field as inside the served mix
     stream = engine_stream()
@@ -190,4 +197,41 @@ def test_default_stream_runs_without_graphs():
     res = eng.run_all()
     assert eng.info()["graph_builds"] == 0
     assert all(st["status"] == cmcg.OK for _, st in res.values())
+    eng.close()
+
+
+def test_refilled_slot_builds_a_new_graph_and_matches_alone():
+    # A solve finishes in slot 0; its result is read, its handle destroyed and its workspace
+    # released; a new solve of the same shape is admitted and lands in slot 0 (possibly with a
+    # handle at the same address and the same workspace memory).  The engine must not replay
+    # the graph it captured for the old solve: it builds a new one, and the new solve's field
+    # equals its solve alone bit for bit.
+    stream = engine_stream()
+    w_long = small_random(7, 120)
+    w_short = wl.gaussian_2d(n=40)
+    w_new = small_random(3, 40)  # same grid as the short solve: same workspace size
+    alone_new, _ = run_engine([w_new], cmcg.MIXED, 1e-8)
+    eng = cmcg.Engine(max_slots=2, stream=stream)
+    s_short = solver(w_short, cmcg.MIXED, stream)
+    s_long = solver(w_long, cmcg.MIXED, stream)
+    assert eng.submit(s_short, w_short.f, w_short.g, 1e-6) == 0
+    assert eng.submit(s_long, w_long.f, w_long.g, 1e-10) == 1
+    finished = []
+    while 0 not in finished:
+        finished = eng.tick()
+        assert 1 not in finished, "the long solve must outlast the short one"
+    u0, st0 = eng.result(0)
+    assert st0["status"] == cmcg.OK
+    s_short.close()
+    del s_short
+    builds = eng.info()["graph_builds"]
+    assert builds >= 1
+    s_new = solver(w_new, cmcg.MIXED, stream)
+    assert eng.submit(s_new, w_new.f, w_new.g, 1e-8) == 0
+    res = eng.run_all()
+    assert eng.info()["graph_builds"] > builds
+    u_new, st_new = res[0]
+    assert st_new["status"] == cmcg.OK and res[1][1]["status"] == cmcg.OK
+    assert torch.equal(u_new, alone_new[0][0])
+    assert st_new["iterations"] == alone_new[0][1]["iterations"]
     eng.close()

@@ -138,13 +138,14 @@ def test_adjoint_period(case, precision, tol):
 
 @pytest.mark.parametrize("tile", [(0, 0, 0, 2), (0, 8, 8, 2), (0, 3, 16, 2), (16, 0, 0, 3), (3, 0, 0, 3),
                                   (0, 0, 0, 4), (3, 0, 0, 4), (0, 2, 0, 4), (5, 1, 0, 4), (16, 0, 4, 3), (5, 0, 4, 3)])
-def test_step_scheme_variants(case, tile):
+@pytest.mark.parametrize("name", ["odd3d_13x11x15", "sphere3d_24"])  # the 3D 7-point cases
+def test_step_scheme_variants(name, tile):
     # FP32 periods with the alternative step kernels: two steps per launch (temporal blocking,
     # scheme 2), two z-planes per thread iteration (scheme 3), and operands staged by bulk
     # copies into a shared-memory ring (scheme 4: tile[0] planes per CTA, tile[1] band rows)
-    name, w, dz = case
-    if w.dim != 3 or w.order != 2:
-        pytest.skip("the two-step kernel covers 3D 7-point grids")
+    w = CASES[name]()
+    dz = dz_of(w)
+    assert w.dim == 3 and w.order == 2
     s = solver_of(w, cmcg.FP32, tile=tile)
     y0, v0 = rand_state(dz, 6)
     yT, vT = wave.period(dz, y0, v0, None)

@@ -199,6 +199,41 @@ def test_cmcg_matches_direct(case):
 
 
 # ----------------------------------------------------------------------------------------
+# P7 on the functional itself (Eq. cost_functional_J): J = 1/2 ||Pi(v) - v||_E^2 vanishes at
+# the periodic state of the direct solve; it is exactly quadratic about that state,
+# J(v* + t d) = t^2 J_hom(d); and its central difference along d equals <J'(v), d> with the
+# gradient J' = P^T E e - E e of the CMCG Algorithm's step (2).  A dropped 1/2, a mismatch
+# taken as Pi(v) + v, a source applied to the homogeneous part or a wrong transpose fails one.
+@pytest.mark.parametrize("case", ["2d_mixed_faces", "3d_sphere"])
+def test_functional_J(case):
+    rng = np.random.default_rng(11)
+    if case == "3d_sphere":
+        w = wl.sphere_3d(n=8)
+        dz = make(w)
+        F = dz.load(w.f, w.g)
+    else:
+        n = (10, 8)
+        c = 1.0 + rng.random((9, 11))
+        dz = box(n, c=c, faces=(ABC, DIRICHLET, NEUMANN, ABC, ABC, ABC), omega=7.0)
+        F = dz.load(rng.standard_normal(dz.shape) + 1j * rng.standard_normal(dz.shape), None)
+    U = direct.solve(dz, F)
+    v0s, v1s = direct.periodic_state(dz, U)
+    J0 = wave.functional_J(dz, 0 * v0s, 0 * v1s, F)
+    assert J0 > 0
+    assert wave.functional_J(dz, v0s, v1s, F) <= 1e-22 * J0
+    d0, d1 = rng.standard_normal(dz.shape) * dz.act, rng.standard_normal(dz.shape) * dz.act
+    Jh = wave.functional_J(dz, d0, d1, None)
+    for t in (0.5, -2.0):
+        assert wave.functional_J(dz, v0s + t * d0, v1s + t * d1, F) == pytest.approx(t * t * Jh, rel=1e-9)
+    w0, w1 = rng.standard_normal(dz.shape) * dz.act, rng.standard_normal(dz.shape) * dz.act
+    g0, g1, _, _ = cmcg.gradient(dz, w0, w1, F)
+    eps = 1e-3
+    fd = (wave.functional_J(dz, w0 + eps * d0, w1 + eps * d1, F)
+          - wave.functional_J(dz, w0 - eps * d0, w1 - eps * d1, F)) / (2 * eps)
+    assert fd == pytest.approx(float(np.sum(g0 * d0) + np.sum(g1 * d1)), rel=1e-8)
+
+
+# ----------------------------------------------------------------------------------------
 # P3: manufactured discrete plane wave U = exp(i kt x) with (2c/h) sin(kt h/2) = wt.
 # The time-discrete Helmholtz residual is zero at every interior node (closed form of the
 # 5-point dispersion relation), and CMCG given the boundary residual returns U.
