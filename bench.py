@@ -63,10 +63,29 @@ def parse():
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-comparators", action="store_true")
+    # profiling entry points (instead of the benchmark line): pieces of the solver timed with
+    # CUDA events on a workload, for ncu captures and the measurements quoted in the design notes
+    ap.add_argument("--profile", default=None,
+                    choices=["period", "adjoint", "solve", "riesz", "fo-period", "fo-adjoint", "fo-solve", "stream",
+                             "obstacles"],
+                    help="period/adjoint/riesz/solve/fo-*: time that call --reps times; stream: copy and "
+                         "3-read/1-write bandwidth of PyTorch's own kernels; obstacles: CMCG against the "
+                         "do-nothing solver on the square obstacle and the cavity (Sec. 4.2)")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "layered", "gauss2d"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tile", type=int, nargs=4, default=None, help="cmcg_options.tile (default: autotuned)")
+    ap.add_argument("--inner-tol", type=float, default=0.0)
+    ap.add_argument("--filter", action="store_true", help="recover U by the fundamental-frequency filter")
+    ap.add_argument("--fp64-plain-tol", type=float, default=5e-10,
+                    help="tolerance of the plain FP64 comparator (chosen so that its error is about 1e-6)")
+    ap.add_argument("--fp64-tuned-tol", type=float, default=1e-10,
+                    help="tolerance of the tuned FP64 comparator (chosen so that its error is about 1e-6)")
     return ap.parse_args()
 
 
-def workload_config(w, args):
+def workload_config(w):
+    """The workload itself (the same in both arms); how each arm computes is in "method"."""
     return {
         "workload": f"3d_sphere_scattering_{w.n[0]}^3",
         "nodes": int(w.num_nodes),
@@ -76,6 +95,13 @@ def workload_config(w, args):
         "obstacle": "sound-soft sphere r=0.1",
         "incidence": "plane wave d=(1/2,0,sqrt(3)/2) via absorbing BC",
         "dt": "0.4h -> T/N",
+        "l2": "inputs larger than L2 (136 MB per FP64 field > 129 MB)",
+    }
+
+
+def method_config(args):
+    return {
+        "step": "one complete CMCG solve (Steps (1)-(6) of the CMCG Algorithm)",
         "tol": args.tol,
         "precision": {"mixed": "fp32 stepping + fp64 CG + fp64 defect correction",
                       "fp32": "fp32 stepping + fp64 CG", "fp64": "fp64"}[args.precision],
@@ -84,7 +110,6 @@ def workload_config(w, args):
         "runup_periods": args.runup,
         "runup": (f"{-args.runup} domain crossings at c_min, ramped sources (Sec. 4.3)" if args.runup < 0
                   else f"{args.runup} periods" if args.runup > 0 else "none"),
-        "l2": "inputs larger than L2 (136 MB per FP64 field > 129 MB)",
     }
 
 
@@ -207,56 +232,204 @@ def kernel_src_hash(name="k_step3d7("):
 
 
 # ---------------------------------------------------------------------------------------
-def cpu_baseline(w, budget_s=15.0):
-    """The oracle's leapfrog period on the same grid, timed on the host cores for a bounded
-    number of steps; returns updates/s and a description of the sample."""
+# The oracle on the host cores: the plain FP64 CPU implementation (numpy/scipy, written from
+# the paper), timed as it stands.  It is single-threaded, so "all cores" means independent
+# replicas of the same bounded sample, one process per core (spawned: no CUDA state is
+# inherited), as many as the host memory holds.
+ORACLE_BYTES_PER_NODE = 600  # resident set of one oracle replica per grid node (9.6 GB at 257^3)
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if not model.isdigit():
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def host_mem_available():
+    avail = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    except (OSError, ValueError):
+        pass
+    try:
+        lim = open("/sys/fs/cgroup/memory.max").read().strip()
+        if lim.isdigit():
+            avail = min(avail or int(lim), int(lim))
+    except OSError:
+        pass
+    return avail
+
+
+def oracle_replica_count(num_nodes):
+    cores, _ = host_cpu()
+    mem = host_mem_available()
+    per = ORACLE_BYTES_PER_NODE * num_nodes
+    by_mem = cores if mem is None else int(0.6 * mem // per)
+    return max(1, min(cores, by_mem))
+
+
+def _oracle_replica(conn, n):
+    """Spawned child: build the workload and the oracle's discretisation, then answer each
+    request of the parent with (steps, seconds) of leapfrog steps run for that many seconds."""
     from oracle import wave as owave
     from oracle.grid import Discretization
+    from paper_1903_12522_gb300 import workloads as wl
 
-    t0 = time.perf_counter()
+    w = wl.sphere_3d(n=n)
     dz = Discretization(w.n, w.h, w.c, w.omega, w.faces, w.dt_target, order=w.order, mask=w.mask)
-    setup = time.perf_counter() - t0
     F = dz.load(w.f, w.g)
     y = np.zeros(dz.shape)
     v = np.zeros(dz.shape)
-    steps = 0
-    t0 = time.perf_counter()
+    k = 0
+    conn.send((dz.size, dz.N))
     while True:
-        y, v, _ = owave.step(dz, y, v, steps, F)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or steps >= dz.N:
+        budget = conn.recv()
+        if budget is None:
             break
-    ups = steps * dz.size / el
-    return {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} of {dz.N} leapfrog steps of one period on the full {w.shape[0]}^3 grid "
-                      f"(numpy/scipy, single thread; setup {setup:.1f}s not timed)"}, steps, el
+        steps = 0
+        t0 = time.perf_counter()
+        while True:
+            y, v, _ = owave.step(dz, y, v, k, F)
+            k += 1
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= budget:
+                break
+        conn.send((steps, el))
+    conn.close()
+
+
+class OracleReplicas:
+    """P spawned oracle replicas of the full workload; each round runs every replica for a
+    bounded time at once and returns (updates, seconds) with seconds = the slowest replica."""
+
+    def __init__(self, n, procs):
+        import multiprocessing as mp
+
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"  # one thread per replica
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for _ in range(procs):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_replica, args=(b, n), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        t0 = time.perf_counter()
+        ready = [c.recv() for c in self.conns]
+        self.setup_s = time.perf_counter() - t0
+        self.size, self.N = ready[0]
+
+    def round(self, budget_s):
+        for c in self.conns:
+            c.send(float(budget_s))
+        res = [c.recv() for c in self.conns]
+        return sum(st for st, _ in res) * self.size, max(el for _, el in res), [st for st, _ in res]
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(None)
+            except (OSError, BrokenPipeError):
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def oracle_description(procs, budget_s, size, N, setup_s):
+    cores, model = host_cpu()
+    return (f"{procs} independent replica(s) of the oracle (plain FP64 numpy/scipy leapfrog, single-threaded "
+            f"each, one per core) on the full {size:,}-node grid; each timed round runs every replica's "
+            f"leapfrog steps for {budget_s:.0f} s (a bounded sample of the {N}-step period); host: {cores} "
+            f"logical cores, {model}; setup {setup_s:.0f} s not timed")
+
+
+def cpu_baseline(w, budget_s=5.0, rounds=2):
+    """The oracle's leapfrog steps on the same grid, on all host cores (replicas)."""
+    procs = oracle_replica_count(w.num_nodes)
+    rep = OracleReplicas(w.n[0], procs)
+    try:
+        rep.round(1.0)  # warm-up
+        upd, el = 0.0, 0.0
+        for _ in range(rounds):
+            u, e, _ = rep.round(budget_s)
+            upd += u
+            el += e
+    finally:
+        rep.close()
+    cores, model = host_cpu()
+    return {"value": upd / el, "unit": UNIT, "cores": procs, "kind": "oracle", "cpu": model, "nproc": cores,
+            "per_core_value": upd / el / procs,
+            "sample": oracle_description(procs, budget_s, rep.size, rep.N, rep.setup_s) + f"; {rounds} rounds"}
 
 
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, on the host cores (no GPU).  Each step is
+    one bounded round of every replica; ms_per_step is the time of that round."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     from paper_1903_12522_gb300 import workloads as wl
 
     w = wl.sphere_3d(n=args.n)
-    vals = []
-    desc = None
-    for i in range(args.warmup + args.steps):
-        cb, steps, el = cpu_baseline(w, budget_s=5.0)
-        if i >= args.warmup:
-            vals.append(cb["value"])
-            desc = cb
-    value = statistics.median(vals)
-    ms = 1e3 * (w.num_nodes * 36) / value
+    procs = oracle_replica_count(w.num_nodes)
+    budget = 4.0
+    rep = OracleReplicas(args.n, procs)
+    try:
+        for _ in range(args.warmup):
+            rep.round(budget)
+        upd, el, steps = 0.0, 0.0, []
+        for _ in range(args.steps):
+            u, e, st = rep.round(budget)
+            upd += u
+            el += e
+            steps.append(st)
+    finally:
+        rep.close()
+    value = upd / el
+    cores, model = host_cpu()
+    desc = oracle_description(procs, budget, rep.size, rep.N, rep.setup_s)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": desc["cores"], "kind": "oracle",
-                             "sample": desc["sample"] + "; each step is this bounded sample, ms_per_step scaled to one period"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w),
+            "method": {"step": "one bounded round of oracle leapfrog steps (FP64, CPU) on every replica",
+                       "leapfrog_steps_per_replica_per_step": steps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "cpu": model,
+                             "nproc": cores, "per_core_value": value / procs, "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def target_comparison(comparators, solves_per_s, err):
+    """Solves/s of this solve against the FP64 GPU solves at (about) the same accuracy."""
+    if not comparators:
+        return None
+    out = {"target_rel_err": 1e-6, "this_solve": {"solves_per_s": solves_per_s, "rel_err_vs_fp64_gpu": err}}
+    for key, c in comparators.items():
+        out[key] = c
+        out[f"speedup_vs_{key}"] = solves_per_s / c["solves_per_s"]
+    return out
 
 
 # ---------------------------------------------------------------------------------------
@@ -297,22 +470,48 @@ def run_ours(args):
         one_solve()
     torch.cuda.synchronize()
 
-    # reference: plain FP64 GPU solve to tol 1e-10 (not timed)
-    err = None
-    u_ref = None
-    ref_info = None
-    if not args.no_error_check:
+    # The plain FP64 GPU CMCG (FP64 stepping and CG, exact MG-PCG Riesz map, zero initial
+    # guess): to tol 1e-10 it is the accuracy reference; at a looser tolerance, and in its best
+    # FP64 form (one V-cycle Riesz map, the run-up), it is the comparator of the solves/s target
+    # at relative error 1e-6.  Each is one solve, timed on its own (outside the timed region).
+    def fp64_solve(tol, flags, runup):
         sref = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, precision=cmcg.FP64, dt=w.dt_target,
-                           device=dev)
-        t0 = time.perf_counter()
-        u_ref, st_ref = sref.solve(None, g_dev, tol=1e-10)
+                           flags=flags, runup_periods=runup, device=dev)
         torch.cuda.synchronize()
-        ref_info = {"precision": "fp64 (stepping, CG, exact MG-PCG Riesz to 1e-12)", "tol": 1e-10,
-                    "seconds": time.perf_counter() - t0, "cg_iterations": st_ref["iterations"],
-                    "updates_per_s": st_ref["point_updates"] / max(time.perf_counter() - t0, 1e-9)}
+        t0 = time.perf_counter()
+        u_c, st_c = sref.solve(None, g_dev, tol=tol)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
         sref.close()
         del sref
         torch.cuda.empty_cache()
+        return u_c, st_c, el
+
+    def rel_err(a, b):
+        return (torch.linalg.vector_norm(a.reshape(-1) - b.reshape(-1)) / torch.linalg.vector_norm(b)).item()
+
+    err = None
+    u_ref = None
+    ref_info = None
+    comparators = {}
+    if not args.no_error_check:
+        u_ref, st_ref, el = fp64_solve(1e-10, 0, 0)
+        ref_info = {"precision": "fp64 (stepping, CG, exact MG-PCG Riesz to 1e-12), no run-up", "tol": 1e-10,
+                    "seconds": el, "cg_iterations": st_ref["iterations"],
+                    "updates_per_s": st_ref["point_updates"] / el}
+        if not args.no_fp64_comparators:
+            for key, tol, fl, ru, desc in (
+                    ("fp64_plain", args.fp64_plain_tol, 0, 0,
+                     "plain FP64 GPU CMCG: FP64 stepping and CG, exact MG-PCG Riesz map, no run-up"),
+                    ("fp64_tuned", args.fp64_tuned_tol, cmcg.FLAG_INEXACT_RIESZ, args.runup,
+                     "FP64 GPU CMCG with this solver's other speed-ups: one V-cycle Riesz map (flexible CG) "
+                     "and the same run-up")):
+                u_c, st_c, el = fp64_solve(tol, fl, ru)
+                comparators[key] = {"what": desc, "tol": tol, "seconds_per_solve": el, "solves_per_s": 1.0 / el,
+                                    "rel_err_vs_fp64_gpu": rel_err(u_c, u_ref), "cg_iterations": st_c["iterations"],
+                                    "runup_periods": st_c["runup_periods"]}
+                del u_c
+                torch.cuda.empty_cache()
 
     clocks = ClockSampler(local)
     if ws > 1:
@@ -425,16 +624,17 @@ def run_ours(args):
         return
     cb = None
     if not args.no_cpu_baseline and ws == 1:
-        cb, _, _ = cpu_baseline(w)
+        cb = cpu_baseline(w)
     ms_per_step = 1e3 * elapsed / args.steps
     line = {
         "metric": METRIC, "value": updates / elapsed, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp32": "f32+f64", "fp64": "f64"}[args.precision],
-        "data": "synthetic", "config": {**workload_config(w, args), **tile_cfg},
+        "data": "synthetic", "config": workload_config(w), "method": {**method_config(args), **tile_cfg},
         "solves_per_s": ws * args.steps / elapsed,
         "rel_err_vs_fp64_gpu": err,
         "plain_fp64_gpu_reference": ref_info,
+        "vs_fp64_at_equal_accuracy": target_comparison(comparators, ws * args.steps / elapsed, err),
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
         "cg_iterations": [st.iterations for st in stats],
         "runup_periods_done": [st.runup_periods for st in stats],
@@ -452,9 +652,140 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------------------
+# Profiling entry points (--profile): not part of the benchmark line.
+def run_profile(a):
+    import torch
+
+    from paper_1903_12522_gb300 import cmcg
+    from paper_1903_12522_gb300 import workloads as wl
+
+    if a.profile == "obstacles":
+        return profile_obstacles(a.n)
+    if a.profile == "stream":
+        return profile_stream(a.n, a.reps)
+    prec = {"fp32": cmcg.FP32, "fp64": cmcg.FP64, "mixed": cmcg.MIXED}[a.precision]
+    w = {"sphere": wl.sphere_3d, "layered": wl.layered_3d, "gauss2d": wl.gaussian_2d}[a.workload](n=a.n)
+    fo = a.profile.startswith("fo-")
+    flags = cmcg.FLAG_FIRST_ORDER if fo else (cmcg.FLAG_INEXACT_RIESZ if a.riesz == "vcycle" else 0)
+    if a.filter:
+        flags |= cmcg.FLAG_FILTER
+    s = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, order=w.order, precision=prec, dt=w.dt_target,
+                    max_iter=a.max_iter, flags=flags, runup_periods=a.runup, tile=None if fo else a.tile,
+                    inner_tol=a.inner_tol)
+    act = 1.0 if w.mask is None else 1.0 - w.mask.astype(np.float64)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    y0, v0 = [torch.randn(w.num_nodes, generator=gen, device="cuda", dtype=torch.float64) for _ in range(2)]
+    if w.mask is not None:
+        m = torch.as_tensor(act, device="cuda").reshape(-1)
+        y0, v0 = y0 * m, v0 * m
+    g = None if w.g is None else torch.as_tensor(w.g, device="cuda").reshape(-1)
+    f = None if w.f is None else torch.as_tensor(w.f, device="cuda").reshape(-1)
+    N = s.info["steps_per_period"]
+    if fo:
+        x = torch.randn((w.dim + 1) * w.num_nodes, generator=gen, device="cuda", dtype=torch.float64)
+    for r in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        if a.profile == "period":
+            s.wave_period(y0, v0, f, g)
+        elif a.profile == "adjoint":
+            s.adjoint_period(y0, v0)
+        elif a.profile == "riesz":
+            s.riesz(y0)
+        elif a.profile == "fo-period":
+            s.fo_period(x)
+        elif a.profile == "fo-adjoint":
+            s.fo_adjoint_period(x)
+        else:
+            _, st = s.solve(f, g, tol=a.tol)
+            print(f"  solve: iterations={st['iterations']} periods={st['periods']} runup={st['runup_periods']} "
+                  f"rel={st['rel_residual']:.2e} status={st['status']}", flush=True)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ups = (N * w.num_nodes / (ms * 1e-3)) if a.profile in ("period", "adjoint", "fo-period", "fo-adjoint") \
+            else float("nan")
+        print(f"{a.profile} n={a.n} {a.precision} rep={r} ms={ms:.3f} updates/s={ups:.4g}", flush=True)
+
+
+def _axis_weights(n):
+    # trapezoidal weights of the node-based L2 norm along one axis (1/2 at both ends)
+    a = np.ones(n + 1)
+    a[0] = a[-1] = 0.5
+    return a
+
+
+def profile_obstacles(n, ells=(10, 25, 50, 100, 200, 400)):
+    """Sec. 4.2 on the GPU: for each l, the error of the do-nothing state after l ramped periods
+    (Eq. AP_SOLUTION) and of the CMCG iterate after l iterations from zero, both against a
+    converged FP64 CMCG solve, with each one's relative periodicity misfit sqrt(J) / ||g_S||."""
+    import torch
+
+    from paper_1903_12522_gb300 import cmcg
+    from paper_1903_12522_gb300 import workloads as wl
+
+    for cavity in (False, True):
+        w = wl.square_obstacle_2d(n=n, cavity=cavity)
+        wts = torch.as_tensor(np.outer(_axis_weights(n), _axis_weights(n)) * w.h ** 2, device="cuda").reshape(-1)
+
+        def solver(**kw):
+            return cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, precision=cmcg.FP64, dt=w.dt_target,
+                               **kw)
+
+        ref, st = solver().solve(None, w.g, tol=1e-12)
+        norm = math.sqrt(float(torch.sum(wts * ref.reshape(-1).abs() ** 2)))
+        g2 = np.abs(w.g) ** 2  # ||g_S||_{L2(Gamma_S)}: trapezoidal rule along each absorbing side
+        t = _axis_weights(n) * w.h
+        fnorm = math.sqrt(float(t @ g2[0] + t @ g2[-1] + t @ g2[:, 0] + t @ g2[:, -1]))
+
+        def err(u):
+            return math.sqrt(float(torch.sum(wts * (u.reshape(-1) - ref.reshape(-1)).abs() ** 2))) / norm
+
+        rows = []
+        for ell in ells:
+            u_dn, s_dn = solver(flags=cmcg.FLAG_NO_CG, runup_periods=ell).solve(None, w.g, tol=1e-6)
+            u_cg, s_cg = solver(max_iter=ell).solve(None, w.g, tol=1e-14)
+            rows.append({"l": ell, "do_nothing_err": err(u_dn), "cmcg_err": err(u_cg),
+                         "do_nothing_misfit": math.sqrt(max(s_dn["J_final"], 0.0)) / fnorm,
+                         "cmcg_misfit": math.sqrt(max(s_cg["J_final"], 0.0)) / fnorm})
+        print(json.dumps({"workload": w.name, "reference_cg_iterations": st["iterations"], "rows": rows}), flush=True)
+
+
+def profile_stream(n, reps):
+    """Bandwidth calibration with PyTorch's own elementwise kernels on (n+1)^3 FP32 arrays: a
+    copy (1 read + 1 write) and p += a * b in place (3 reads + 1 write, the access mix of the
+    one-step leapfrog kernel without its neighbour loads).  Prints GB/s per pattern."""
+    import torch
+
+    m = (n + 1) ** 3
+    a, b, p, q = [torch.rand(m, device="cuda", dtype=torch.float32) for _ in range(4)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    out = {}
+    for name, fn, nbytes in (("copy_1r1w", lambda: q.copy_(a), 8 * m),
+                             ("addcmul_3r1w", lambda: p.addcmul_(a, b), 16 * m)):
+        for _ in range(3):
+            fn()
+        times = []
+        for _ in range(max(reps, 5)):
+            flush.zero_()  # evict L2 between runs
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+        t = sorted(times)[len(times) // 2]
+        out[name] = {"us": t * 1e6, "GB_s": nbytes / t / 1e9}
+    print(json.dumps({"n": n, "nodes": m, "median": out}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

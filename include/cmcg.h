@@ -153,8 +153,14 @@ typedef struct {
                                most 16); 3 = one step per launch with [2] = 2 (default) or 4
                                z-planes per loop iteration, [0] z-planes per thread; 4 = FP32
                                steps with operands staged by TMA bulk copies, [0] z-planes per
-                               CTA and [1] rows per band (0 = automatic).  Chosen per grid
-                               class by the autotuner (paper_1903_12522_gb300/autotune.py). */
+                               CTA and [1] rows per band (0 = automatic); 5 = FP32 steps in
+                               vector form, one aligned float4 of the flat node index per
+                               thread, also for 2D 5-point steps (FP64 steps: scheme 1);
+                               6 = FP32 steps with operands staged in shared memory by
+                               asynchronous copies several planes ahead, [0] z-planes per
+                               CTA, [1] rows per band, [2] planes in flight (2 or 3; 0 =
+                               automatic).  Chosen per grid class by the autotuner
+                               (paper_1903_12522_gb300/autotune.py). */
 } cmcg_options;
 
 typedef struct {
@@ -211,6 +217,15 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
 int cmcg_destroy(cmcg_handle* h);
 
 int cmcg_get_info(const cmcg_handle* h, cmcg_info* info);
+
+/* Residual history of the last cmcg_solve / cmcg_solve_host on this handle (the quantity the
+ * stopping criterion of the CMCG Algorithm, Step 5.8, tests, studied along the iterations in
+ * Sec. 4.2): entry k is sqrt(gamma_k / gamma_0) after CG iteration k (k = 0: the start),
+ * relative to the zero initial guess (also with a run-up).  CMCG_MIXED: the inner FP32
+ * iterations' estimates scaled by the FP64 residual they started from, and at the end of each
+ * inner solve the recomputed FP64 residual.  First-order solves record none.  rel_host: host,
+ * capacity doubles; *count receives the number of entries (copies min(count, capacity)). */
+int cmcg_get_history(const cmcg_handle* h, double* rel_host, int capacity, int* count);
 
 /* One period of the forced wave equation (Eq. WE) by leapfrog: from y(0) = u0, y_t(0) = v0
  * to (uT, vT) = (y(T), y_t(T)).  f: interior source amplitude, g: boundary datum g_S on
@@ -296,6 +311,11 @@ size_t cmcg_engine_workspace_size(int max_slots);
 int cmcg_engine_create(int max_slots, void* workspace, size_t ws_bytes, void* stream, int flags,
                        cmcg_engine** out);
 int cmcg_engine_destroy(cmcg_engine* e);
+/* Launch shape of the batched step kernel (tuned per workload class by the autotuner):
+ * blocks_per_sm resident blocks per SM (0 = as many as fit, the default; larger values are
+ * capped there), z_planes = z-planes per work item on 3D grids (0 = 16, at most 256).  Only
+ * while no solve is active (else CMCG_ERR_INVALID_ARG). */
+int cmcg_engine_set_shape(cmcg_engine* e, int blocks_per_sm, int z_planes);
 /* Admit a solve: f, g sources as in cmcg_solve (device, nullable, read now); tol as in
  * cmcg_solve; u: device complex double[N_p] written when the solve finishes.  Returns the slot
  * (>= 0), or CMCG_ERR_WORKSPACE when no slot is free, CMCG_ERR_INVALID_ARG when h is already

@@ -33,10 +33,10 @@ ERR_DEVICE_TIMEOUT = -7
 ENGINE_NO_GRAPH = 1
 
 EXPORTED = (
-    "cmcg_workspace_size", "cmcg_create", "cmcg_destroy", "cmcg_get_info", "cmcg_wave_period",
+    "cmcg_workspace_size", "cmcg_create", "cmcg_destroy", "cmcg_get_info", "cmcg_get_history", "cmcg_wave_period",
     "cmcg_adjoint_period", "cmcg_riesz", "cmcg_solve", "cmcg_solve_host", "cmcg_status_string",
     "cmcg_engine_workspace_size", "cmcg_engine_create", "cmcg_engine_destroy", "cmcg_engine_submit",
-    "cmcg_engine_tick", "cmcg_engine_result", "cmcg_engine_active", "cmcg_engine_info",
+    "cmcg_engine_tick", "cmcg_engine_result", "cmcg_engine_active", "cmcg_engine_info", "cmcg_engine_set_shape",
     "cmcg_engine_barrier_selftest", "cmcg_engine_cuda_error", "cmcg_fo_period", "cmcg_fo_adjoint_period",
     "cmcg_bulk_wait_selftest",
 )
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
     lib.cmcg_destroy.restype = I
     lib.cmcg_get_info.argtypes = [P, C.POINTER(Info)]
     lib.cmcg_get_info.restype = I
+    lib.cmcg_get_history.argtypes = [P, P, I, C.POINTER(I)]
+    lib.cmcg_get_history.restype = I
     lib.cmcg_wave_period.argtypes = [P, P, P, P, P, P, P]
     lib.cmcg_wave_period.restype = I
     lib.cmcg_adjoint_period.argtypes = [P, P, P, P, P]
@@ -120,6 +122,8 @@ def load(path: str = LIB_PATH):
     lib.cmcg_engine_create.restype = I
     lib.cmcg_engine_destroy.argtypes = [P]
     lib.cmcg_engine_destroy.restype = I
+    lib.cmcg_engine_set_shape.argtypes = [P, I, I]
+    lib.cmcg_engine_set_shape.restype = I
     lib.cmcg_engine_submit.argtypes = [P, P, P, P, D, P]
     lib.cmcg_engine_submit.restype = I
     lib.cmcg_engine_tick.argtypes = [P, C.POINTER(I), I, C.POINTER(I)]
@@ -197,6 +201,16 @@ def cmcg_get_info(h) -> dict:
     info = Info()
     _check(load().cmcg_get_info(h, C.byref(info)), "cmcg_get_info")
     return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def cmcg_get_history(h) -> np.ndarray:
+    """Relative residual per CG iteration of the handle's last solve (see include/cmcg.h)."""
+    n = C.c_int(0)
+    _check(load().cmcg_get_history(h, None, 0, C.byref(n)), "cmcg_get_history")
+    out = np.zeros(n.value, dtype=np.float64)
+    if n.value:
+        _check(load().cmcg_get_history(h, out.ctypes.data, n.value, C.byref(n)), "cmcg_get_history")
+    return out
 
 
 def cmcg_wave_period(h, u0, v0, f, g, uT, vT) -> None:
@@ -380,6 +394,10 @@ class Solver:
         self._before_caller()
         return s.reshape(self.shape), code
 
+    def history(self):
+        """Relative residual per CG iteration of the last solve."""
+        return cmcg_get_history(self.handle)
+
     def solve(self, f=None, g=None, tol=1e-6):
         torch = self.torch
         f, g = self._dev(f, torch.complex128), self._dev(g, torch.complex128)
@@ -400,7 +418,7 @@ class Engine:
     stream argument the engine creates its own (CUDA graphs need a created stream); pass
     engine.stream to the solvers."""
 
-    def __init__(self, max_slots, stream=None, flags=0, device="cuda"):
+    def __init__(self, max_slots, stream=None, flags=0, device="cuda", shape=None):
         import torch
 
         lib = load()
@@ -416,6 +434,13 @@ class Engine:
                                       int(flags), C.byref(self.handle)), "cmcg_engine_create")
         self.max_slots = int(max_slots)
         self._pending = {}
+        if shape is not None:
+            self.set_shape(*shape)
+
+    def set_shape(self, blocks_per_sm=0, z_planes=0):
+        """Launch shape of the batched step kernel (cmcg_engine_set_shape); only while idle."""
+        _check(load().cmcg_engine_set_shape(self.handle, int(blocks_per_sm), int(z_planes)),
+               "cmcg_engine_set_shape")
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

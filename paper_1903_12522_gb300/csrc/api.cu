@@ -114,6 +114,9 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
     H->mask = c.take<unsigned char>(np);
     H->kap32 = o.precision != CMCG_FP64 ? c.take<float>(np + 4) : nullptr;  // + 16 B for bulk copies
     H->S = c.take<double>(2 * np);
+    // FP32 steps read the source in FP32 (GB300 runs FP64 arithmetic at a small fraction of the
+    // FP32 rate: an FP64 source term would make a forced FP32 step ALU-bound)
+    H->S32 = o.precision != CMCG_FP64 && !(o.flags & CMCG_FLAG_FIRST_ORDER) ? c.take<float>(2 * np + 4) : nullptr;
     if (o.flags & CMCG_FLAG_FIRST_ORDER) {
         // first-order state (p, v): CG vectors and the two stepping buffers; no Riesz map
         const size_t ns = (size_t)(g.dim + 1) * np;
@@ -165,6 +168,10 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
 }
 
 int cuda_status() { return cudaGetLastError() == cudaSuccess ? CMCG_OK : CMCG_ERR_CUDA; }
+
+void source_updated(cmcg_handle* H) {
+    if (H->S32) launch_to_float(2 * H->g.np, H->S, H->S32, H->st);
+}
 
 // Fold completed event pairs into the per-precision step times.
 // A pair without an elapsed time is skipped, and the error it raised is cleared unless an
@@ -254,8 +261,9 @@ PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool
 }
 
 // z-planes per thread of the one-step kernels; negative selects the variant that processes two
-// planes per loop iteration (tile[3] == 3)
+// planes per loop iteration (tile[3] == 3), kZcFlat the FP32 vector form (tile[3] == 5)
 int step_zc(const cmcg_handle* H) {
+    if (H->order == 2 && H->opt.tile[3] == 5) return kZcFlat;
     if (H->g.dim != 3) return 1;
     const int zc = H->opt.tile[0] > 0 ? H->opt.tile[0] : kZcStep3D;
     if (H->order != 2 || H->opt.tile[3] != 3) return zc;
@@ -272,8 +280,16 @@ bool use_pairs(const cmcg_handle* H, bool src) {
 // One leapfrog step cur -> prev (in place).  FP32 3D 7-point steps without a source go through
 // the bulk-copy kernel when tile[3] == 4 (tile[1] = band rows, tile[0] = planes per CTA).
 template <typename T>
-void step_one(cmcg_handle* H, const T* cur, T* prev, const T* kap, const double* S, double cs, double sn, int flags,
+void step_one(cmcg_handle* H, const T* cur, T* prev, const T* kap, const T* S, double cs, double sn, int flags,
               int zc) {
+    if (std::is_same<T, float>::value && H->opt.tile[3] == 6 && H->order == 2 && H->g.dim == 3) {
+        // operands staged by asynchronous copies: tile[1] rows per band, tile[0] planes per CTA,
+        // tile[2] planes in flight (any step, forced or not)
+        if (launch_step_async(H->g, (const float*)cur, (float*)prev, (const float*)kap, (const float*)S, cs, sn, flags,
+                              H->opt.tile[1], H->opt.tile[0], H->opt.tile[2], H->st) == cudaSuccess)
+            return;
+        cudaGetLastError();
+    }
     if (std::is_same<T, float>::value && H->opt.tile[3] == 4 && H->order == 2 && !(flags & kStepSrc)) {
         int ty = 0, zb = 0;
         if (step_bulk_plan(H->g, H->opt.tile[1], H->opt.tile[0], &ty, &zb)) {
@@ -323,18 +339,17 @@ void plain_steps(cmcg_handle* H, PeriodBuffers& b, int count) {
 
 template <typename T>
 void fwd_steps(cmcg_handle* H, PeriodBuffers& b, bool src) {
-    const Geom& g = H->g;
     const int zc = step_zc(H);
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     if (!src) {
         plain_steps<T>(H, b, H->N - 1);
         return;
     }
-    const double* S = H->S;
+    const T* S = step_source<T>(H);
     const int tp = timing_begin(H, std::is_same<T, float>::value, H->N - 1);
     for (int n = 1; n < H->N; ++n) {
         const double th = H->omega * n * H->dt;
-        launch_step<T>(g, H->order, (const T*)b.cur, (T*)b.prev, kap, S, cos(th), sin(th), kStepSrc, zc, H->st);
+        step_one<T>(H, (const T*)b.cur, (T*)b.prev, kap, S, cos(th), sin(th), kStepSrc, zc);
         std::swap(b.cur, b.prev);
     }
     timing_end(H, tp);
@@ -458,7 +473,7 @@ double ramp(double t, double ttr) {
 template <typename T>
 void runup(cmcg_handle* H, int periods, double* w0, double* w1) {
     const Geom& g = H->g;
-    const int zc = g.dim == 3 ? kZcStep3D : 1;
+    const int zc = step_zc(H);
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     T* cur = (T*)H->yb;
@@ -471,8 +486,8 @@ void runup(cmcg_handle* H, int periods, double* w0, double* w1) {
     for (long long n = 1; n < total; ++n) {
         const double t = n * H->dt;
         const double th = ramp(t, ttr);
-        launch_step<T>(g, H->order, cur, prev, kap, H->S, th * cos(H->omega * t), th * sin(H->omega * t), kStepSrc,
-                       zc, H->st);
+        step_one<T>(H, cur, prev, kap, step_source<T>(H), th * cos(H->omega * t), th * sin(H->omega * t), kStepSrc,
+                    zc);
         std::swap(cur, prev);
     }
     const double tN = total * H->dt;
@@ -708,6 +723,7 @@ int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_o
     if (rc != CMCG_OK) return rc;
     if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
     double rel = H->hsc[SC_REL];
+    H->hist.push_back(rel * H->hist_scale);
     int it = 0;
     // FP32 periods read float(d0); the direction update writes it for the next iteration, and
     // the dual-residual update writes float(rhat0) for the V-cycle
@@ -732,6 +748,7 @@ int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_o
             if (rc != CMCG_OK) return rc;
             if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
             rel = H->hsc[SC_REL];
+            H->hist.push_back(rel * H->hist_scale);
             if (rel <= tol) break;
         }
         if (it > max_iter) it = max_iter;
@@ -790,6 +807,7 @@ int cg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_ou
     if (rc != CMCG_OK) return rc;
     if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
     double rel = H->hsc[SC_REL];
+    H->hist.push_back(rel * H->hist_scale);
     int it = 0;
     if (rel > tol) {
         for (it = 1; it <= max_iter; ++it) {
@@ -806,6 +824,7 @@ int cg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_ou
             if (rc != CMCG_OK) return rc;
             if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
             rel = H->hsc[SC_REL];
+            H->hist.push_back(rel * H->hist_scale);
             if (rel <= tol) break;
         }
         if (it > max_iter) it = max_iter;
@@ -837,10 +856,12 @@ int solve_plain(cmcg_handle* H, double tol, cmcg_stats* stats) {
     int iters = 0;
     double rel = 1.0;
     if (scale <= tol) {
+        H->hist.push_back(scale);
         stats->iterations = 0;
         stats->rel_residual = scale;
         return CMCG_OK;
     }
+    H->hist_scale = scale;
     rc = cg_loop<T>(H, tol / scale, H->opt.max_iter, &iters, &rel);
     stats->iterations = iters;
     stats->rel_residual = rel * scale;
@@ -879,6 +900,9 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
             stats->J0 = H->hsc[SC_J];
         }
         rel = gamma_ref > 0 ? sqrt(gam / gamma_ref) : 0.0;
+        // the FP64 residual replaces the inner solve's last estimate
+        if (H->hist.empty()) H->hist.push_back(rel);
+        else H->hist.back() = rel;
         if (rel <= tol || total >= H->opt.max_iter) break;
         // inner solve: relative tolerance inner_tol, but not below what the outer needs
         const double inner = std::max(H->opt.inner_tol, 0.5 * tol / std::max(rel, 1e-300));
@@ -886,6 +910,8 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
         launch_fill(H->w1, n, 0.0, H->st);
         int it = 0;
         double irel = 1.0;
+        H->hist_scale = rel;
+        H->hist.pop_back();  // the inner loop records its start, which is this FP64 residual
         rc = cg_loop<float>(H, std::min(inner, 0.5), H->opt.max_iter - total, &it, &irel);
         if (rc < 0) return rc;
         total += it;
@@ -972,6 +998,8 @@ int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool w
     h->riesz_iters = 0;
     h->periods = 0;
     h->graph_replays = 0;
+    h->hist.clear();
+    h->hist_scale = 1.0;
     const long long n = h->g.np;
     int rc;
     if (h->first_order) {
@@ -1237,7 +1265,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     if (H->has_dir && H->sumW <= 0) return fail(CMCG_ERR_INVALID_ARG);
     if (o.runup_periods < -64 || o.runup_periods > 100000) return fail(CMCG_ERR_INVALID_ARG);
     if (o.tile[0] < 0 || o.tile[0] > 512 || o.tile[1] < 0 || o.tile[1] > 512 || o.tile[2] < 0 || o.tile[2] > 16 ||
-        o.tile[3] < 0 || o.tile[3] > 4)
+        o.tile[3] < 0 || o.tile[3] > 6)
         return fail(CMCG_ERR_INVALID_ARG);
     // time step: N = ceil(T / dt_target - 1e-9), dt = T / N
     const double dt_target = o.dt > 0 ? o.dt : 0.5 * grid->h / (sqrt((double)grid->dim) * cmax);
@@ -1283,6 +1311,14 @@ int cmcg_destroy(cmcg_handle* h) {
     return CMCG_OK;
 }
 
+int cmcg_get_history(const cmcg_handle* h, double* rel_host, int capacity, int* count) {
+    if (!h || !count || capacity < 0 || (capacity > 0 && !rel_host)) return CMCG_ERR_INVALID_ARG;
+    const int n = (int)std::min<size_t>(h->hist.size(), (size_t)INT32_MAX);
+    for (int k = 0; k < n && k < capacity; ++k) rel_host[k] = h->hist[k];
+    *count = n;
+    return CMCG_OK;
+}
+
 int cmcg_get_info(const cmcg_handle* h, cmcg_info* info) {
     if (!h || !info) return CMCG_ERR_INVALID_ARG;
     info->steps_per_period = h->N;
@@ -1301,6 +1337,7 @@ int cmcg_wave_period(cmcg_handle* h, const double* u0, const double* v0, const d
     if (h->first_order) return CMCG_ERR_UNSUPPORTED;
     const bool src = f || g;
     if (src) launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
+    if (src) source_updated(h);
     launch_mask_copy(h->g, u0, h->kap64, h->z0, h->st);
     launch_mask_copy(h->g, v0, h->kap64, h->z1, h->st);
     if (h->opt.precision == CMCG_FP32)
@@ -1342,6 +1379,7 @@ int cmcg_fo_period(cmcg_handle* h, const double* s0, const double* f, const doub
     if (!h->first_order) return CMCG_ERR_UNSUPPORTED;
     const bool src = f || g;
     if (src) launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
+    if (src) source_updated(h);
     if (fo_period(h, s0, src, sT) != CMCG_OK) return CMCG_ERR_CUDA;
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return CMCG_ERR_CUDA;
     return cuda_status();
@@ -1362,6 +1400,7 @@ int cmcg_solve(cmcg_handle* h, const double* f, const double* g, double tol, dou
         launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
     else
         launch_fill(h->S, 2 * h->g.np, 0.0, h->st);
+    source_updated(h);
     cmcg_stats local{};
     cmcg_stats* st = stats ? stats : &local;
     const int rc = solve_prepared(h, tol, u, st, stats != nullptr);
@@ -1386,6 +1425,7 @@ int cmcg_solve_host(cmcg_handle* h, const double* f_host, const double* g_host, 
         cudaMemcpyAsync(h->stage, g_host, bytes, cudaMemcpyHostToDevice, h->st);
         launch_make_source(h->g, nullptr, h->stage, h->kap64, h->S, zce, true, h->st);
     }
+    source_updated(h);
     if (cuda_status() != CMCG_OK) return CMCG_ERR_CUDA;
     cmcg_stats local{};
     cmcg_stats* st = stats ? stats : &local;

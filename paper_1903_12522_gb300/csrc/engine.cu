@@ -59,7 +59,9 @@ struct cmcg_engine {
     unsigned* bar = nullptr;         // barrier counter + generation
     int* err = nullptr;              // barrier time-out flag
     int* err_host = nullptr;         // pinned
-    int grid = 0;
+    int grid = 0;      // blocks of the batched step kernel (at most the co-resident maximum)
+    int grid_max = 0;  // co-resident maximum
+    int zc3 = kZcStep3D;  // z-planes per work item of 3D grids in the batched kernel
     bool use_graph = true;
     // graph cache
     cudaGraphExec_t exec = nullptr;
@@ -97,7 +99,7 @@ size_t engine_layout(cmcg_engine* e, int max_slots, char* base) {
     return off + 256;
 }
 
-BatchItem make_item(cmcg_handle* h, const PeriodBuffers& b, bool adjoint) {
+BatchItem make_item(cmcg_handle* h, const PeriodBuffers& b, bool adjoint, int zc3) {
     BatchItem it{};
     it.g = h->g;
     it.kap = h->kap32;
@@ -106,7 +108,7 @@ BatchItem make_item(cmcg_handle* h, const PeriodBuffers& b, bool adjoint) {
     it.order = h->order;
     it.nsteps = h->N - 1;
     it.adjoint = adjoint ? 1 : 0;
-    it.zc = h->g.dim == 3 ? kZcStep3D : 1;
+    it.zc = h->g.dim == 3 ? zc3 : 1;
     const long long plane = (long long)h->g.sx * h->g.sy;
     it.blocks_xy = (int)((plane + 255) / 256);
     it.blocks = it.blocks_xy * ((h->g.sz + it.zc - 1) / it.zc);
@@ -191,7 +193,7 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
         for (int i = 0; i < m; ++i) {
             cmcg_handle* h = e->slots[inner[i]].h;
             on_side(e, h, lane + i, [&](cmcg_handle* hh) { fb[i] = fwd_begin<float>(hh, hh->d0, hh->d1, false); });
-            items[i] = make_item(h, fb[i], false);
+            items[i] = make_item(h, fb[i], false, e->zc3);
             items[i].offset = total;
             total += items[i].blocks;
             maxs = std::max(maxs, items[i].nsteps);
@@ -207,7 +209,7 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
                 fwd_end<float>(hh, after_steps(fb[i], hh->N - 1), hh->d1, false, 0, hh->z0, hh->z1);
                 ab[i] = adj_begin<float>(hh, hh->z0, hh->z1, 0);
             });
-            items[m + i] = make_item(h, ab[i], true);
+            items[m + i] = make_item(h, ab[i], true, e->zc3);
             items[m + i].offset = total_a;
             total_a += items[m + i].blocks;
             maxa = std::max(maxa, items[m + i].nsteps);
@@ -250,10 +252,10 @@ void upload_items(cmcg_engine* e, const std::vector<int>& act) {
         if (sl.unit != U_INNER) continue;
         cmcg_handle* h = sl.h;
         PeriodBuffers f{h->yb, h->ya, nullptr}, a{h->ya, h->yb, nullptr};
-        items[m] = make_item(h, f, false);
+        items[m] = make_item(h, f, false, e->zc3);
         items[m].offset = tf;
         tf += items[m].blocks;
-        items[e->max_slots + m] = make_item(h, a, true);
+        items[e->max_slots + m] = make_item(h, a, true, e->zc3);
         items[e->max_slots + m].offset = ta;
         ta += items[e->max_slots + m].blocks;
         ++m;
@@ -327,7 +329,7 @@ int cmcg_engine_create(int max_slots, void* workspace, size_t ws_bytes, void* st
     }
     cudaMemsetAsync(e->bar, 0, sizeof(unsigned) * 4, e->st);
     cudaMemsetAsync(e->err, 0, sizeof(int) * 4, e->st);
-    e->grid = batch_steps_max_blocks();
+    e->grid = e->grid_max = batch_steps_max_blocks();
     bool ok = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; k < cmcg_engine::kSide; ++k) {
         ok = ok && cudaStreamCreateWithFlags(&e->side[k], cudaStreamNonBlocking) == cudaSuccess;
@@ -344,6 +346,25 @@ int cmcg_engine_create(int max_slots, void* workspace, size_t ws_bytes, void* st
         return CMCG_ERR_CUDA;
     }
     *out = e;
+    return CMCG_OK;
+}
+
+int cmcg_engine_set_shape(cmcg_engine* e, int blocks_per_sm, int z_planes) {
+    if (!e || blocks_per_sm < 0 || z_planes < 0 || z_planes > 256) return CMCG_ERR_INVALID_ARG;
+    for (const EngineSlot& sl : e->slots)
+        if (sl.unit != U_FREE && sl.unit != U_DONE) return CMCG_ERR_INVALID_ARG;  // only while idle
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return CMCG_ERR_CUDA;
+    e->grid = blocks_per_sm == 0 ? e->grid_max : std::min(e->grid_max, blocks_per_sm * sms);
+    e->zc3 = z_planes == 0 ? kZcStep3D : z_planes;
+    if (e->exec) {
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+    }
+    e->signature.clear();
+    e->last_signature.clear();
     return CMCG_OK;
 }
 
@@ -390,6 +411,7 @@ int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const do
         launch_make_source(h->g, f, g, h->kap64, h->S, h->g.dim == 3 ? kZcEnds : 1, false, h->st);
     else
         launch_fill(h->S, 2 * h->g.np, 0.0, h->st);
+    source_updated(h);
     if (h->opt.precision == CMCG_MIXED) {
         launch_fill(h->wo0, h->g.np, 0.0, h->st);
         launch_fill(h->wo1, h->g.np, 0.0, h->st);

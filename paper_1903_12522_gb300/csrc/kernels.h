@@ -18,6 +18,9 @@ struct Red {
 enum StepFlags { kStepSrc = 1, kStepPrevScaled = 2, kStepNoDiv = 4 };
 // Added to the (negated) planes-per-thread of a step launch: four z-planes per loop iteration.
 constexpr int kZk4 = 1 << 12;
+// Planes-per-thread value that selects the FP32 3D 7-point step in vector form (one aligned
+// float4 of the flat node index per thread; FP64 and other stencils take their default kernel).
+constexpr int kZcFlat = 1 << 20;
 
 // Process-wide count of kernels launched by this library (every launcher records its launches).
 void note_launch(long long k);
@@ -25,7 +28,8 @@ long long launch_count();
 
 // ---- wave.cu --------------------------------------------------------------------------
 template <typename T>
-void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, const double* S, double cs,
+// S: the source dt^2 M^-1 F^ (complex interleaved) in the stepping precision T
+void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, const T* S, double cs,
                  double sn, int flags, int zc, cudaStream_t st);
 template <typename T>
 void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y0, T* y1, const T* kap,
@@ -90,6 +94,13 @@ int step_bulk_smem(int sx, int ty);
 // CMCG_ERR_DEVICE_TIMEOUT when the wait runs out as it must (CMCG_OK would mean it did not).
 int bulk_wait_selftest(int spin_limit, cudaStream_t st);
 bool step_bulk_plan(const Geom& g, int ty_req, int zc_req, int* ty, int* zc);
+// FP32 3D 7-point step with its operands staged in shared memory by asynchronous copies
+// (step_async.cu): ty rows per band, zc planes per CTA (0 = automatic), depth = planes in
+// flight (2 or 3).  Any step flags.  cudaErrorInvalidValue if the grid does not suit it.
+cudaError_t launch_step_async(const Geom& g, const float* cur, float* prev, const float* kap, const float* S,
+                              double cs, double sn, int flags, int ty, int zc, int depth, cudaStream_t st);
+bool step_async_plan(const Geom& g, int ty_req, int zc_req, int depth, int* ty, int* zc, size_t* smem, int* cap_c,
+                     int* cap_p);
 void launch_step_bulk(const Geom& g, const float* cur, float* prev, const float* kap, int flags, int ty, int zc,
                       double* sc, cudaStream_t st);
 

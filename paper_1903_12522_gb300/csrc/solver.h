@@ -2,6 +2,7 @@
 // points (api.cu) and the multi-solve engine (engine.cu).
 #pragma once
 #include <type_traits>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -31,6 +32,7 @@ struct cmcg_handle {
     // coefficients
     double *kap64 = nullptr, *mass = nullptr, *minv = nullptr, *S = nullptr;
     float* kap32 = nullptr;
+    float* S32 = nullptr;  // FP32 copy of S, the source of FP32 leapfrog steps (FP32 / mixed)
     unsigned char* mask = nullptr;
     // wave buffers (sized for double; FP32 stepping uses the first half) + FP64 temp
     void *ya = nullptr, *yb = nullptr;
@@ -57,6 +59,10 @@ struct cmcg_handle {
     unsigned* tickets = nullptr;
     double* sc = nullptr;
     double* hsc = nullptr;  // pinned host mirror of sc
+    // residual history of the last solve: sqrt(gamma_k / gamma_0) per CG iteration, relative to
+    // the zero initial guess (hist_scale converts a loop's own relative residual)
+    std::vector<double> hist;
+    double hist_scale = 1.0;
     // counters of the current call
     long long riesz_iters = 0;
     long long periods = 0;
@@ -84,6 +90,14 @@ struct PeriodBuffers {
 };
 
 int cuda_status();
+// After every change of S: refresh its FP32 copy (FP32 and mixed-precision handles).
+void source_updated(cmcg_handle* H);
+// The source array of leapfrog steps in precision T.
+template <typename T>
+const T* step_source(const cmcg_handle* H) {
+    if constexpr (std::is_same<T, float>::value) return H->S32;
+    else return H->S;
+}
 int sync_read(cmcg_handle* H);
 bool inexact(const cmcg_handle* H);
 // b_ready: the finest level's right-hand side already holds float(rhat0) (written by the

@@ -71,7 +71,7 @@ struct DiffT {  // a[i] - b[i] in T
 // Leapfrog step, generic (any dim / order): one thread per (x, y) column, marching z.
 template <typename T, int ORDER, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step(const T* __restrict__ cur, T* __restrict__ prev_out,
-                                                   const T* __restrict__ kap, const double* __restrict__ S,
+                                                   const T* __restrict__ kap, const T* __restrict__ S,
                                                    double cs, double sn, Geom g, int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid) return;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const T* __restrict__ cur, T*
         const T k = kap[j];
         const T yp = prev_out[j];
         T rhs = T(2) * cur[j] - k * L;
-        if (FLAGS & kStepSrc) rhs += (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
+        if (FLAGS & kStepSrc) rhs += S[2 * j] * (T)cs + S[2 * j + 1] * (T)sn;
         const int nb = num_abc(g, m.ix, m.iy, iz);
         T out;
         if (nb == 0) {
@@ -150,7 +150,7 @@ __global__ void k_scale_complex(long long n, double* __restrict__ u, double s) {
 // Leapfrog step, 3D 2nd order: z-neighbours carried in registers along the march.
 template <typename T, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur, T* __restrict__ prev_out,
-                                                      const T* __restrict__ kap, const double* __restrict__ S,
+                                                      const T* __restrict__ kap, const T* __restrict__ S,
                                                       double cs, double sn, Geom g, int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid || m.z0 >= m.z1) return;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
         const T k = __ldcs(kap + j);  // streamed: keep L2 for the two wave fields reused next step
         const T yp = prev_out[j];
         T rhs = T(2) * yc - k * L;
-        if (FLAGS & kStepSrc) rhs += (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
+        if (FLAGS & kStepSrc) rhs += S[2 * j] * (T)cs + S[2 * j + 1] * (T)sn;
         const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         T out;
         if (nb == 0) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
 // issued before either update (more loads in flight per thread).
 template <typename T, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ cur, T* __restrict__ prev_out,
-                                                         const T* __restrict__ kap, const double* __restrict__ S,
+                                                         const T* __restrict__ kap, const T* __restrict__ S,
                                                          double cs, double sn, Geom g, int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid || m.z0 >= m.z1) return;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ c
     auto update = [&](T yc, T ym, T yz, long long jj, int iz, T sxy, T k, T yp) {
         const T L = T(6) * yc - (sxy + (ym + yz));
         T rhs = T(2) * yc - k * L;
-        if (FLAGS & kStepSrc) rhs += (T)(S[2 * jj] * cs + S[2 * jj + 1] * sn);
+        if (FLAGS & kStepSrc) rhs += S[2 * jj] * (T)cs + S[2 * jj + 1] * (T)sn;
         const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         T out;
         if (nb == 0) {
@@ -244,11 +244,157 @@ __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ c
     }
 }
 
+// Leapfrog step, 2D 5-point or 3D 7-point, FP32, vector form.  Each thread owns one aligned float4 chunk of
+// the flat node index, nodes 4c .. 4c+3 (which may straddle a row or a plane), and reads y^n,
+// y^{n-1} and kappa and writes y^{n+1} with 16-byte accesses.  The neighbours at a flat offset
+// d = 4a + r (0 <= r < 4) of the four nodes are positions r .. r+3 of chunks c+a and c+a+1;
+// the x-neighbours of the chunk's two end nodes are single loads.  Every load is issued before
+// any arithmetic.  At a face the neighbour outside is replaced by the mirror value afterwards
+// (ghost-point Neumann, as in the other step kernels), so a chunk index is clamped into range
+// only where all of its values are discarded.  Same expression, in the same order, as
+// k_step / k_step3d7.  The last chunk may extend past the last node: its loads read the slack behind
+// every FP32 field (at least 16 bytes), and only its real nodes are stored.
+struct Win4 {
+    float v[4];
+};
+
+__device__ __forceinline__ float4 ld4g(const float* __restrict__ f, long long ch) {
+    return __ldg(reinterpret_cast<const float4*>(f) + ch);
+}
+
+__device__ __forceinline__ long long clamp_ch(long long ch, long long nch) {
+    return ch < 0 ? 0 : (ch >= nch ? nch - 1 : ch);
+}
+
+// w.v[e] = f[4 ca + r + e] (e = 0..3), r the same for every thread of the grid.
+__device__ __forceinline__ Win4 window4(const float* __restrict__ f, long long ca, int r, long long nch) {
+    const long long c0 = clamp_ch(ca, nch), c1 = clamp_ch(ca + 1, nch);
+    Win4 w;
+    if (r == 0) {
+        const float4 a = ld4g(f, c0);
+        w.v[0] = a.x, w.v[1] = a.y, w.v[2] = a.z, w.v[3] = a.w;
+    } else if (r == 1) {
+        const float4 a = ld4g(f, c0);
+        const float b = __ldg(f + 4 * c1);
+        w.v[0] = a.y, w.v[1] = a.z, w.v[2] = a.w, w.v[3] = b;
+    } else if (r == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(f + 4 * c0 + 2));
+        const float2 b = __ldg(reinterpret_cast<const float2*>(f + 4 * c1));
+        w.v[0] = a.x, w.v[1] = a.y, w.v[2] = b.x, w.v[3] = b.y;
+    } else {
+        const float a = __ldg(f + 4 * c0 + 3);
+        const float4 b = ld4g(f, c1);
+        w.v[0] = a, w.v[1] = b.x, w.v[2] = b.y, w.v[3] = b.z;
+    }
+    return w;
+}
+
+template <int DIM, int FLAGS>
+__global__ void __launch_bounds__(kThreads) k_step_v4(const float* __restrict__ cur, float* __restrict__ prev_out,
+                                                      const float* __restrict__ kap, const float* __restrict__ S,
+                                                      double cs, double sn, Geom g) {
+    const long long nch = (g.np + 3) >> 2;
+    const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+    if (c >= nch) return;
+    const long long sY = g.sx, sZ = (long long)g.sx * g.sy;
+    const long long i0 = 4 * c;
+    const float4 yc4 = ld4g(cur, c);
+    const float xl = __ldg(cur + (i0 > 0 ? i0 - 1 : 0));
+    const float xr = __ldg(cur + (i0 + 4 < g.np ? i0 + 4 : g.np - 1));
+    const Win4 yP = window4(cur, c + (sY >> 2), (int)(sY & 3), nch);
+    const Win4 yM = window4(cur, c + ((-sY) >> 2), (int)((-sY) & 3), nch);
+    Win4 zP{}, zM{};
+    if (DIM == 3) {
+        zP = window4(cur, c + (sZ >> 2), (int)(sZ & 3), nch);
+        zM = window4(cur, c + ((-sZ) >> 2), (int)((-sZ) & 3), nch);
+    }
+    const float4 k4 = __ldcs(reinterpret_cast<const float4*>(kap) + c);  // streamed, as in k_step3d7
+    const float4 p4 = reinterpret_cast<const float4*>(prev_out)[c];
+    float2 s2[4];
+    if (FLAGS & kStepSrc) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const long long j = i0 + e < g.np ? i0 + e : g.np - 1;
+            s2[e] = __ldg(reinterpret_cast<const float2*>(S) + j);
+        }
+    }
+    // coordinates of node i0 (the flat index is below 2^31 for this kernel)
+    const unsigned u0 = (unsigned)i0;
+    int iz = (int)(u0 / (unsigned)sZ);
+    const unsigned rem = u0 - (unsigned)iz * (unsigned)sZ;
+    int iy = (int)(rem / (unsigned)g.sx);
+    int ix = (int)(rem - (unsigned)iy * (unsigned)g.sx);
+    const float yc[4] = {yc4.x, yc4.y, yc4.z, yc4.w};
+    const float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+    const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
+    float out[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float xm = e == 0 ? xl : yc[e - 1];
+        float xp = e == 3 ? xr : yc[e + 1];
+        if (ix == 0) xm = xp;
+        if (ix == g.nx) xp = xm;
+        float ym = yM.v[e], yp = yP.v[e];
+        if (iy == 0) ym = yp;
+        if (iy == g.ny) yp = ym;
+        float L;
+        if (DIM == 3) {
+            float zm = zM.v[e], zp = zP.v[e];
+            if (iz == 0) zm = zp;
+            if (iz == g.nz) zp = zm;
+            L = 6.f * yc[e] - (((xm + xp) + (ym + yp)) + (zm + zp));
+        } else {
+            L = 4.f * yc[e] - ((xm + xp) + (ym + yp));
+        }
+        const float k = kk[e];
+        float rhs = 2.f * yc[e] - k * L;
+        if (FLAGS & kStepSrc) rhs += s2[e].x * (float)cs + s2[e].y * (float)sn;
+        int nb = 0;
+        nb += (ix == 0) & (int)(g.abc & 1u);
+        nb += (ix == g.nx) & (int)((g.abc >> 1) & 1u);
+        nb += (iy == 0) & (int)((g.abc >> 2) & 1u);
+        nb += (iy == g.ny) & (int)((g.abc >> 3) & 1u);
+        if (DIM == 3) {
+            nb += (iz == 0) & (int)((g.abc >> 4) & 1u);
+            nb += (iz == g.nz) & (int)((g.abc >> 5) & 1u);
+        }
+        const float yq = pp[e];
+        if (nb == 0) {
+            out[e] = rhs - yq;
+        } else {
+            const float beta = (float)nb * sqrtf(k);
+            const float v = rhs - ((FLAGS & kStepPrevScaled) ? yq : (1.f - beta) * yq);
+            out[e] = (FLAGS & kStepNoDiv) ? v : v / (1.f + beta);
+        }
+        if (++ix == g.sx) {
+            ix = 0;
+            if (++iy == g.sy) {
+                iy = 0;
+                ++iz;
+            }
+        }
+    }
+    if (i0 + 3 < g.np) {
+        reinterpret_cast<float4*>(prev_out)[c] = make_float4(out[0], out[1], out[2], out[3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (i0 + e < g.np) prev_out[i0 + e] = out[e];
+    }
+}
+
+// Can the vector-form step run on these fields?  16-byte aligned fields (each carries at
+// least 16 bytes of slack behind its last node) and a flat index below 2^31.
+inline bool step_v4_ok(const Geom& g, const void* cur, const void* prev, const void* kap) {
+    const uintptr_t a = (uintptr_t)cur | (uintptr_t)prev | (uintptr_t)kap;
+    return (a & 15u) == 0 && g.np + 4 < (1ll << 31);
+}
+
 // Leapfrog step, 3D 2nd order, K z-planes per loop iteration (K >= 2): all K planes' loads are
 // issued before any update.  Same expression, in the same order, as k_step3d7.
 template <typename T, int FLAGS, int K>
 __global__ void __launch_bounds__(kThreads) k_step3d7_zk(const T* __restrict__ cur, T* __restrict__ prev_out,
-                                                         const T* __restrict__ kap, const double* __restrict__ S,
+                                                         const T* __restrict__ kap, const T* __restrict__ S,
                                                          double cs, double sn, Geom g, int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid || m.z0 >= m.z1) return;
@@ -264,7 +410,7 @@ __global__ void __launch_bounds__(kThreads) k_step3d7_zk(const T* __restrict__ c
     auto update = [&](T yc, T ym, T yz, long long jj, int iz, T sxy, T k, T yp) {
         const T L = T(6) * yc - (sxy + (ym + yz));
         T rhs = T(2) * yc - k * L;
-        if (FLAGS & kStepSrc) rhs += (T)(S[2 * jj] * cs + S[2 * jj + 1] * sn);
+        if (FLAGS & kStepSrc) rhs += S[2 * jj] * (T)cs + S[2 * jj + 1] * (T)sn;
         const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         T out;
         if (nb == 0) {
@@ -321,7 +467,7 @@ __device__ __forceinline__ int refl(int i, int n) { return i < 0 ? -i : (i > n ?
 
 template <typename T, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step3d13(const T* __restrict__ cur, T* __restrict__ prev_out,
-                                                       const T* __restrict__ kap, const double* __restrict__ S,
+                                                       const T* __restrict__ kap, const T* __restrict__ S,
                                                        double cs, double sn, Geom g, int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid || m.z0 >= m.z1) return;
@@ -350,7 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_step3d13(const T* __restrict__ cur
         const T k = kap[j];
         const T yp = prev_out[j];
         T rhs = T(2) * zc0 - k * L;
-        if (FLAGS & kStepSrc) rhs += (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
+        if (FLAGS & kStepSrc) rhs += S[2 * j] * (T)cs + S[2 * j + 1] * (T)sn;
         const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         T out;
         if (nb == 0) {
@@ -897,10 +1043,25 @@ inline dim3 plane_grid(const Geom& g, int zc) {
 }
 
 template <typename T, int ORDER, int FLAGS>
-void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const double* S, double cs, double sn,
+void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const T* S, double cs, double sn,
                    int zc, cudaStream_t st) {
     // zc < 0 selects the variants of the 3D 7-point kernel with several z-planes per loop
-    // iteration: -zc = planes per thread, plus kZk4 for four planes per iteration (else two)
+    // iteration: -zc = planes per thread, plus kZk4 for four planes per iteration (else two);
+    // kZcFlat the FP32 vector form (other types and stencils: their default kernel)
+    if (zc == kZcFlat) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (ORDER == 2 && step_v4_ok(g, cur, prev, kap)) {
+                const long long nch = (g.np + 3) >> 2;
+                const unsigned blocks = (unsigned)((nch + kThreads - 1) / kThreads);
+                if (g.dim == 3)
+                    k_step_v4<3, FLAGS><<<blocks, kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g);
+                else
+                    k_step_v4<2, FLAGS><<<blocks, kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g);
+                return;
+            }
+        }
+        zc = g.dim == 3 ? 16 : 1;
+    }
     if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZk4) {
         const int z = -zc - kZk4;
         k_step3d7_zk<T, FLAGS, 4><<<plane_grid(g, z), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z);
@@ -916,7 +1077,7 @@ void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const dou
 }
 
 template <typename T, int ORDER>
-void step_flags(const Geom& g, const T* cur, T* prev, const T* kap, const double* S, double cs, double sn,
+void step_flags(const Geom& g, const T* cur, T* prev, const T* kap, const T* S, double cs, double sn,
                 int flags, int zc, cudaStream_t st) {
     switch (flags) {
         case 0: step_dispatch<T, ORDER, 0>(g, cur, prev, kap, S, cs, sn, zc, st); break;
@@ -934,7 +1095,7 @@ void step_flags(const Geom& g, const T* cur, T* prev, const T* kap, const double
 
 // ---- launchers ------------------------------------------------------------------------
 template <typename T>
-void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, const double* S, double cs,
+void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, const T* S, double cs,
                  double sn, int flags, int zc, cudaStream_t st) {
     note_launch(1);
     if (order == 2)
@@ -1036,7 +1197,7 @@ long long plane_blocks(const Geom& g, int zc) {
 }
 
 #define CMCG_INST(T)                                                                                           \
-    template void launch_step<T>(const Geom&, int, const T*, T*, const T*, const double*, double, double, int,   \
+    template void launch_step<T>(const Geom&, int, const T*, T*, const T*, const T*, double, double, int,        \
                                  int, cudaStream_t);                                                           \
     template void launch_start<T>(const Geom&, int, const T*, const double*, T*, T*, const T*, const double*,   \
                                   double, int, cudaStream_t);                                                  \

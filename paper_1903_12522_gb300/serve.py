@@ -2,10 +2,13 @@
 
   python -m paper_1903_12522_gb300.serve batch [--count 64] [--max-n 1024]
   python -m paper_1903_12522_gb300.serve serve [--requests 40] [--rate 50] [--budget-gb 120]
+  python -m paper_1903_12522_gb300.serve batch-compare [--tol 5e-10] [--fp64-tol 5e-10]
 
 batch: the uneven 2D batch -- instances seeded 1000+i, n ~ U{96..1024}, 8-20 points per
   wavelength, smooth random c(x) in [1, 2], one Gaussian source each -- admitted together and
   stepped by one persistent kernel per period; reports solves/s and grid-point updates/s.
+batch-compare: the same batch at equal accuracy against FP64 solves of each instance one after
+  another (plain, and with the V-cycle Riesz map and the run-up), errors against FP64 to 1e-10.
 serve: Poisson arrivals (seeded) of a 70 % 2D (n ~ U{128..512}) / 30 % 3D (n ~ U{64..256})
   request mix, 10-16 points per wavelength, smooth random c, one random source, tol 1e-6.
   A request is admitted when its workspace (cmcg_workspace_size) fits the memory budget and a
@@ -30,6 +33,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 if os.path.dirname(HERE) not in sys.path:
     sys.path.insert(0, os.path.dirname(HERE))
 
+from paper_1903_12522_gb300 import autotune  # noqa: E402
 from paper_1903_12522_gb300 import cmcg  # noqa: E402
 from paper_1903_12522_gb300 import workloads as wl  # noqa: E402
 
@@ -160,7 +164,7 @@ def serve(requests, budget_bytes, max_slots=64, precision=cmcg.MIXED, tol=1e-6, 
     (latencies are then in simulated time; wall_s and the rates stay on the wall clock)."""
     import torch
 
-    eng = cmcg.Engine(max_slots=max_slots, stream=stream)
+    eng = cmcg.Engine(max_slots=max_slots, stream=stream, shape=autotune.lookup_engine("mix"))
     stream = eng.stream
     clock = TickClock(tick_s) if tick_s else WallClock()
     queue = list(requests)
@@ -239,14 +243,9 @@ def batch(count=64, max_n=None, precision=cmcg.MIXED, tol=1e-6, device="cuda", r
     """The uneven 2D batch solved together; returns totals."""
     import torch
 
-    eng = cmcg.Engine(max_slots=count)
+    eng = cmcg.Engine(max_slots=count, shape=autotune.lookup_engine("batch2d"))
     stream = eng.stream
-    ws = []
-    for i in range(count):
-        w = wl.random_2d_instance(i)
-        if max_n is not None and w.n[0] > max_n:
-            w = wl.random_2d_instance(i, n=max_n)
-        ws.append(w)
+    ws = batch_instances(count, max_n)
     solvers = [cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, precision=precision, dt=w.dt_target,
                            flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream, runup_periods=runup) for w in ws]
     torch.cuda.synchronize()
@@ -272,9 +271,72 @@ def batch(count=64, max_n=None, precision=cmcg.MIXED, tol=1e-6, device="cuda", r
     }
 
 
+def batch_instances(count, max_n=None):
+    ws = []
+    for i in range(count):
+        w = wl.random_2d_instance(i)
+        if max_n is not None and w.n[0] > max_n:
+            w = wl.random_2d_instance(i, n=max_n)
+        ws.append(w)
+    return ws
+
+
+def batch_compare(count=64, max_n=None, tol=5e-10, fp64_tol=5e-10, fp64_tuned_tol=1e-10, runup=-2, device="cuda"):
+    """The uneven 2D batch at equal accuracy: the mixed-precision engine batch against the same
+    instances solved one after another by the plain FP64 GPU CMCG (FP64 stepping, exact Riesz
+    map, no run-up) and by the FP64 solver with the V-cycle Riesz map and the run-up; every
+    field's error against a plain FP64 solve to tol 1e-10 (not timed)."""
+    import torch
+
+    ws = batch_instances(count, max_n)
+
+    def rel(u, r):
+        return float(torch.linalg.vector_norm(u.reshape(-1) - r.reshape(-1)) / torch.linalg.vector_norm(r))
+
+    def fp64_solve(w, tol_, flags=0, ru=0):
+        s = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, precision=cmcg.FP64, dt=w.dt_target, flags=flags,
+                        runup_periods=ru)
+        u, st = s.solve(w.f, None, tol=tol_)
+        s.close()
+        return u, st
+
+    refs = [fp64_solve(w, 1e-10)[0] for w in ws]
+    out = {"instances": count, "nodes_total": int(sum(w.num_nodes for w in ws)), "tol_reference": 1e-10}
+    for key, tol_, flags, ru in (("fp64_plain", fp64_tol, 0, 0),
+                                 ("fp64_tuned", fp64_tuned_tol, cmcg.FLAG_INEXACT_RIESZ, runup)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        errs = []
+        for w, r in zip(ws, refs):
+            u, st = fp64_solve(w, tol_, flags, ru)
+            errs.append(rel(u, r))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[key] = {"tol": tol_, "wall_s": wall, "solves_per_s": count / wall, "max_rel_err": max(errs),
+                    "median_rel_err": float(np.median(errs))}
+    eng = cmcg.Engine(max_slots=count, shape=autotune.lookup_engine("batch2d"))
+    stream = eng.stream
+    solvers = [cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, precision=cmcg.MIXED, dt=w.dt_target,
+                           flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream, runup_periods=runup) for w in ws]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    slots = [eng.submit(s, w.f, None, tol) for s, w in zip(solvers, ws)]
+    res = eng.run_all()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    eng.close()
+    errs = [rel(res[sl][0], r) for sl, r in zip(slots, refs)]
+    out["mixed_batch"] = {"tol": tol, "wall_s": wall, "solves_per_s": count / wall, "max_rel_err": max(errs),
+                          "median_rel_err": float(np.median(errs)),
+                          "status_ok": sum(1 for sl in slots if res[sl][1]["status"] == cmcg.OK)}
+    for key in ("fp64_plain", "fp64_tuned"):
+        out[f"speedup_vs_{key}"] = out["mixed_batch"]["solves_per_s"] / out[key]["solves_per_s"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["batch", "serve"])
+    ap.add_argument("mode", choices=["batch", "serve", "batch-compare"])
     ap.add_argument("--count", type=int, default=64)
     ap.add_argument("--max-n", type=int, default=None)
     ap.add_argument("--requests", type=int, default=40)
@@ -285,13 +347,20 @@ def main():
     ap.add_argument("--runup", type=int, default=-2,
                     help="run-up periods per solve (Sec. 4.3; -k = k domain crossings; mixed precision only)")
     ap.add_argument("--max-3d", type=int, default=256)
+    ap.add_argument("--fp64-tol", type=float, default=5e-10, help="batch-compare: tolerance of the plain FP64 solves")
+    ap.add_argument("--fp64-tuned-tol", type=float, default=1e-10,
+                    help="batch-compare: tolerance of the FP64 solves with the V-cycle Riesz map and the run-up")
+    ap.add_argument("--tick-s", type=float, default=None,
+                    help="serve: arrivals on a simulated clock advancing this much per tick (repeatable runs)")
     a = ap.parse_args()
     prec = cmcg.MIXED if a.precision == "mixed" else cmcg.FP32
     if a.mode == "batch":
         out = batch(a.count, a.max_n, prec, a.tol, runup=a.runup)
+    elif a.mode == "batch-compare":
+        out = batch_compare(a.count, a.max_n, a.tol, a.fp64_tol, a.fp64_tuned_tol, runup=a.runup)
     else:
         reqs = poisson_requests(a.requests, a.rate, three_d=(64, a.max_3d))
-        out = serve(reqs, int(a.budget_gb * 1e9), precision=prec, tol=a.tol, runup=a.runup)
+        out = serve(reqs, int(a.budget_gb * 1e9), precision=prec, tol=a.tol, runup=a.runup, tick_s=a.tick_s)
     print(json.dumps(out), flush=True)
 
 

@@ -92,6 +92,28 @@ def test_alone_equals_in_the_mix(precision):
         assert alone[0][1]["iterations"] == mixed[k][1]["iterations"]
 
 
+def test_engine_launch_shapes_agree():
+    # the batched kernel's launch shape (resident blocks per SM, z-planes per 3D work item) only
+    # changes how the nodes are split over blocks: the same bits for every shape
+    ws = mix()[:3]
+    stream = engine_stream()
+    outs = []
+    for shape in (None, (1, 4), (2, 32)):
+        eng = cmcg.Engine(max_slots=len(ws), stream=stream, shape=shape)
+        solvers = [solver(w, cmcg.FP32, stream) for w in ws]
+        slots = [eng.submit(s, w.f, w.g, 1e-6) for s, w in zip(solvers, ws)]
+        res = eng.run_all()
+        outs.append([res[sl][0] for sl in slots])
+        with pytest.raises(cmcg.CMCGError):  # a solve is active: no shape change
+            s2 = solver(ws[0], cmcg.FP32, stream)
+            eng.submit(s2, ws[0].f, ws[0].g, 1e-6)
+            eng.set_shape(2, 8)
+        eng.run_all()
+        eng.close()
+    for o in outs[1:]:
+        assert all(torch.equal(a, b) for a, b in zip(o, outs[0]))
+
+
 def test_graph_and_plain_launches_agree():
     ws = mix()[:3]
     a, _ = run_engine(ws, cmcg.MIXED, 1e-8)

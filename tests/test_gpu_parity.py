@@ -137,12 +137,16 @@ def test_adjoint_period(case, precision, tol):
 
 
 @pytest.mark.parametrize("tile", [(0, 0, 0, 2), (0, 8, 8, 2), (0, 3, 16, 2), (16, 0, 0, 3), (3, 0, 0, 3),
-                                  (0, 0, 0, 4), (3, 0, 0, 4), (0, 2, 0, 4), (5, 1, 0, 4), (16, 0, 4, 3), (5, 0, 4, 3)])
+                                  (0, 0, 0, 4), (3, 0, 0, 4), (0, 2, 0, 4), (5, 1, 0, 4), (16, 0, 4, 3), (5, 0, 4, 3),
+                                  (0, 0, 0, 5), (0, 0, 0, 6), (3, 1, 3, 6), (5, 2, 2, 6)])
 @pytest.mark.parametrize("name", ["odd3d_13x11x15", "sphere3d_24"])  # the 3D 7-point cases
 def test_step_scheme_variants(name, tile):
     # FP32 periods with the alternative step kernels: two steps per launch (temporal blocking,
-    # scheme 2), two z-planes per thread iteration (scheme 3), and operands staged by bulk
-    # copies into a shared-memory ring (scheme 4: tile[0] planes per CTA, tile[1] band rows)
+    # scheme 2), two z-planes per thread iteration (scheme 3), operands staged by bulk copies
+    # into a shared-memory ring (scheme 4: tile[0] planes per CTA, tile[1] band rows), and one
+    # aligned float4 of the flat node index per thread (scheme 5), and operands staged by
+    # asynchronous copies (scheme 6: tile[0] planes per CTA, tile[1] band rows, tile[2] depth);
+    # schemes 5 and 6 also run forced steps
     w = CASES[name]()
     dz = dz_of(w)
     assert w.dim == 3 and w.order == 2
@@ -154,6 +158,27 @@ def test_step_scheme_variants(name, tile):
     q0, q1 = wave.transposed_period(dz, y0, v0)
     g0, g1 = s.adjoint_period(y0, v0)
     assert rel(g0.cpu().numpy(), q0) <= 2e-5 and rel(g1.cpu().numpy(), q1) <= 2e-5
+    if tile[3] in (5, 6):
+        yF, vF = wave.period(dz, y0, v0, dz.load(w.f, w.g))
+        uF, uVF = s.wave_period(y0, v0, w.f, w.g)
+        assert rel(uF.cpu().numpy(), yF) <= 2e-5 and rel(uVF.cpu().numpy(), vF) <= 2e-5
+
+
+@pytest.mark.parametrize("name", ["gauss2d_40", "odd2d_37x29", "mixed2d"])
+def test_vector_step_2d(name):
+    # the vector-form step (scheme 5) on 2D 5-point grids: forced and homogeneous FP32 periods
+    # and the adjoint period against the oracle
+    w = CASES[name]()
+    dz = dz_of(w)
+    s = solver_of(w, cmcg.FP32, tile=(0, 0, 0, 5))
+    y0, v0 = rand_state(dz, 8)
+    for F, f, g in ((dz.load(w.f, w.g), w.f, w.g), (None, None, None)):
+        yT, vT = wave.period(dz, y0, v0, F)
+        uT, uV = s.wave_period(y0, v0, f, g)
+        assert rel(uT.cpu().numpy(), yT) <= 2e-5 and rel(uV.cpu().numpy(), vT) <= 2e-5, name
+    q0, q1 = wave.transposed_period(dz, y0, v0)
+    g0, g1 = s.adjoint_period(y0, v0)
+    assert rel(g0.cpu().numpy(), q0) <= 2e-5 and rel(g1.cpu().numpy(), q1) <= 2e-5, name
 
 
 def test_adjoint_dot_product_on_device(case):
@@ -278,6 +303,12 @@ def test_fp64_iterations_and_shift_match_oracle(case):
     assert abs(st["iterations"] - ref.iterations) <= 2, (st["iterations"], ref.iterations)
     assert abs(st["lambda_re"] - ref.lam.real) <= 1e-8 * max(abs(ref.lam), 1e-12)
     assert abs(st["J0"] - ref.J_history[0]) <= 1e-10 * ref.J_history[0]
+    # the residual history (Step 5.8's quantity per iteration) follows the oracle's
+    hist = s.history()
+    assert len(hist) == st["iterations"] + 1 and hist[0] == pytest.approx(1.0, rel=1e-12)
+    assert hist[-1] == pytest.approx(st["rel_residual"], rel=1e-12) and hist[-1] <= 1e-10
+    k = min(10, len(hist), len(ref.residual_history))  # the early iterations, before rounding drifts
+    assert np.allclose(hist[:k], ref.residual_history[:k], rtol=1e-6, atol=0), name
 
 
 @pytest.mark.parametrize("precision,tol", [(cmcg.FP64, 1e-9), (cmcg.MIXED, 1e-9), (cmcg.FP32, 1e-6)])
@@ -291,6 +322,8 @@ def test_graph_replayed_iterations_match_plain_launches(precision, tol):
         out[name] = s.solve(w.f, w.g, tol=tol)
     (ug, sg), (up, sp) = out["graph"], out["plain"]
     assert torch.equal(ug, up)
+    # the history of a mixed solve ends at the FP64 residual it stopped on
+    assert len(s.history()) >= 1 and s.history()[-1] == pytest.approx(sp["rel_residual"], rel=1e-12)
     for k in ("iterations", "periods", "riesz_iterations", "kernel_launches", "outer_iterations"):
         assert sg[k] == sp[k], (k, sg[k], sp[k])
     assert sp["graph_replays"] == 0
@@ -310,6 +343,8 @@ def test_step_timing_inside_replayed_graphs(precision):
         out[name] = s.solve(w.f, w.g, tol=1e-9)
     (ug, sg), (up, sp) = out["graph"], out["plain"]
     assert torch.equal(ug, up)
+    # the history of a mixed solve ends at the FP64 residual it stopped on
+    assert len(s.history()) >= 1 and s.history()[-1] == pytest.approx(sp["rel_residual"], rel=1e-12)
     assert sg["graph_replays"] >= sg["iterations"] - 2 > 0, (sg["graph_replays"], sg["iterations"])
     assert sp["graph_replays"] == 0
     for k in ("step_launches_fp32", "step_launches_fp64", "kernel_launches", "periods"):
@@ -443,11 +478,12 @@ def full_size():
 
 @pytest.mark.parametrize("precision,tol,tile", [(cmcg.FP64, 1e-11, None), (cmcg.FP32, 1e-4, None),
                                                (cmcg.FP32, 1e-4, (0, 0, 0, 2)), (cmcg.FP32, 1e-4, (16, 0, 0, 3)),
-                                               (cmcg.FP32, 1e-4, (0, 0, 0, 4))])
+                                               (cmcg.FP32, 1e-4, (0, 0, 0, 4)), (cmcg.FP32, 1e-4, (0, 0, 0, 5)),
+                                               (cmcg.FP32, 1e-4, (0, 0, 0, 6))])
 def test_full_size_period_sampled(full_size, precision, tol, tile):
     w, y0, v0 = full_size
     s = solver_of(w, precision, tile=tile)
-    if tile is not None:  # the two-step kernel runs homogeneous steps only: no source here
+    if tile is not None and tile[3] not in (5, 6):  # schemes 2-4 run homogeneous steps only: no source here
         uT, vT = [t.cpu().numpy() for t in s.wave_period(y0, v0, None, None)]
     else:
         uT, vT = [t.cpu().numpy() for t in s.wave_period(y0, v0, None, w.g)]
@@ -457,17 +493,18 @@ def test_full_size_period_sampled(full_size, precision, tol, tile):
         sub, sl, local = crop(w, cidx, N + 3)
         dz = dz_of(sub)
         assert dz.N == N
-        yT, vTo = wave.period(dz, y0[sl], v0[sl], None if tile is not None else dz.load(sub.f, sub.g))
+        yT, vTo = wave.period(dz, y0[sl], v0[sl],
+                              None if tile is not None and tile[3] not in (5, 6) else dz.load(sub.f, sub.g))
         scale = max(np.abs(yT).max(), 1e-30)
         assert abs(uT[sl][local] - yT[local]) <= tol * scale, (cidx, uT[sl][local], yT[local])
         scale_v = max(np.abs(vTo).max(), 1e-30)
         assert abs(vT[sl][local] - vTo[local]) <= tol * scale_v, cidx
 
 
-@pytest.mark.parametrize("tile", [(0, 0, 0, 3), (0, 0, 0, 4), (16, 0, 4, 3)])
+@pytest.mark.parametrize("tile", [(0, 0, 0, 3), (0, 0, 0, 4), (16, 0, 4, 3), (0, 0, 0, 5), (0, 0, 0, 6), (0, 0, 3, 6)])
 def test_full_size_step_kernels_agree(full_size, tile):
-    # the z-pair and bulk-copy kernels evaluate the single-step kernel's expression in the same
-    # order; their FP32 periods agree with it to rounding
+    # the z-pair, bulk-copy and vector-form kernels evaluate the single-step kernel's expression
+    # in the same order; their FP32 periods agree with it to rounding
     w, y0, v0 = full_size
     ref = [t.reshape(-1) for t in solver_of(w, cmcg.FP32, tile=(0, 0, 0, 1)).wave_period(y0, v0)]
     out = [t.reshape(-1) for t in solver_of(w, cmcg.FP32, tile=tile).wave_period(y0, v0)]

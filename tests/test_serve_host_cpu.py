@@ -38,7 +38,7 @@ class FakeSolver:
 class FakeEngine:
     last = None
 
-    def __init__(self, max_slots, stream=None):
+    def __init__(self, max_slots, stream=None, shape=None):
         self.max_slots = max_slots
         self.stream = stream if stream is not None else object()
         self.running = {}  # slot -> [solver, ticks left, bytes, admission tick]
@@ -94,7 +94,8 @@ def test_admission_respects_budget_and_slots(fakes):
     reqs = serve.poisson_requests(30, rate=2000.0, seed=3, two_d=(64, 256), three_d=(16, 48))
     sizes = [serve.workspace_bytes(r, cmcg.MIXED) for r in reqs]
     budget = 3 * max(sizes)  # only a few fit at once
-    out = serve.serve(reqs, budget_bytes=budget, max_slots=4, device="cpu")
+    # a simulated clock of 1 ms per tick: the admission pattern does not depend on host speed
+    out = serve.serve(reqs, budget_bytes=budget, max_slots=4, device="cpu", tick_s=1e-3)
     eng = FakeEngine.last
     assert out["requests"] == 30 and out["status_ok"] == 30 and out["rejected"] == 0
     assert eng.peak_slots <= 4
@@ -116,7 +117,7 @@ def test_first_fit_lets_a_small_request_pass_a_large_one(fakes):
     b_first, b_big, b_small = (serve.workspace_bytes(r, cmcg.MIXED) for r in (first, big, small))
     budget = b_first + max(b_small, b_big - 1)
     assert b_first + b_big > budget >= b_first + b_small and b_big <= budget
-    out = serve.serve([first, big, small], budget_bytes=budget, max_slots=8, device="cpu")
+    out = serve.serve([first, big, small], budget_bytes=budget, max_slots=8, device="cpu", tick_s=1e-3)
     assert out["requests"] == 3 and out["rejected"] == 0
     assert small.admitted < big.admitted
     assert big.admitted >= first.finished  # it waited for the memory of the first
