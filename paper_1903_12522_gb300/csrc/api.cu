@@ -117,6 +117,7 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
     // FP32 steps read the source in FP32 (GB300 runs FP64 arithmetic at a small fraction of the
     // FP32 rate: an FP64 source term would make a forced FP32 step ALU-bound)
     H->S32 = o.precision != CMCG_FP64 && !(o.flags & CMCG_FLAG_FIRST_ORDER) ? c.take<float>(2 * np + 4) : nullptr;
+    H->scol = g.dim == 3 && !(o.flags & CMCG_FLAG_FIRST_ORDER) ? c.take<unsigned char>((size_t)g.sx * g.sy) : nullptr;
     if (o.flags & CMCG_FLAG_FIRST_ORDER) {
         // first-order state (p, v): CG vectors and the two stepping buffers; no Riesz map
         const size_t ns = (size_t)(g.dim + 1) * np;
@@ -171,6 +172,7 @@ int cuda_status() { return cudaGetLastError() == cudaSuccess ? CMCG_OK : CMCG_ER
 
 void source_updated(cmcg_handle* H) {
     if (H->S32) launch_to_float(2 * H->g.np, H->S, H->S32, H->st);
+    if (H->scol) launch_source_columns(H->g, H->S, H->scol, H->st);
 }
 
 // Fold completed event pairs into the per-precision step times.
@@ -297,7 +299,7 @@ void step_one(cmcg_handle* H, const T* cur, T* prev, const T* kap, const T* S, d
             return;
         }
     }
-    launch_step<T>(H->g, H->order, cur, prev, kap, S, cs, sn, flags, zc, H->st);
+    launch_step<T>(H->g, H->order, cur, prev, kap, S, cs, sn, flags, zc, H->st, H->scol);
 }
 
 // `count` homogeneous steps from b (in pairs where possible, else one by one).

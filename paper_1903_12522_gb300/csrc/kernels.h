@@ -28,9 +28,13 @@ long long launch_count();
 
 // ---- wave.cu --------------------------------------------------------------------------
 template <typename T>
-// S: the source dt^2 M^-1 F^ (complex interleaved) in the stepping precision T
+// S: the source dt^2 M^-1 F^ (complex interleaved) in the stepping precision T; scol (3D,
+// nullable): per (x, y) column, nonzero if S is nonzero at some node with 0 < z < nz (the
+// 3D 7-point kernels then read S on the other columns' z-faces only)
 void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, const T* S, double cs,
-                 double sn, int flags, int zc, cudaStream_t st);
+                 double sn, int flags, int zc, cudaStream_t st, const unsigned char* scol = nullptr);
+// scol of S (3D): one byte per (x, y) column
+void launch_source_columns(const Geom& g, const double* S, unsigned char* scol, cudaStream_t st);
 template <typename T>
 void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y0, T* y1, const T* kap,
                   const double* S, double dt, int zc, cudaStream_t st);

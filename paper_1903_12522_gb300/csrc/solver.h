@@ -33,6 +33,7 @@ struct cmcg_handle {
     double *kap64 = nullptr, *mass = nullptr, *minv = nullptr, *S = nullptr;
     float* kap32 = nullptr;
     float* S32 = nullptr;  // FP32 copy of S, the source of FP32 leapfrog steps (FP32 / mixed)
+    unsigned char* scol = nullptr;  // 3D: columns with source inside the grid (launch_source_columns)
     unsigned char* mask = nullptr;
     // wave buffers (sized for double; FP32 stepping uses the first half) + FP64 temp
     void *ya = nullptr, *yb = nullptr;

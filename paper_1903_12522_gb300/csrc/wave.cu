@@ -131,6 +131,21 @@ __global__ void __launch_bounds__(kThreads) k_step_filter(const double* __restri
     }
 }
 
+// Source columns: scol[x + sx y] = 1 if S != 0 at some node (x, y, z) with 0 < z < nz.  A
+// boundary datum on the six faces of a box leaves only the x- and y-face columns flagged.
+__global__ void k_source_columns(Geom g, const double* __restrict__ S, unsigned char* __restrict__ scol) {
+    const long long plane = (long long)g.sx * g.sy;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < plane; c += stride) {
+        bool any = false;
+        for (int z = 1; z < g.nz && !any; ++z) {
+            const long long j = c + plane * z;
+            any = S[2 * j] != 0.0 || S[2 * j + 1] != 0.0;
+        }
+        scol[c] = any ? 1 : 0;
+    }
+}
+
 // acc = w0 + i w1 / wh (the n = 0 term; zero on Dirichlet nodes).
 __global__ void k_filter_init(long long n, const double* __restrict__ w0, const double* __restrict__ w1,
                               const double* __restrict__ kap64, double inv_wh, double* __restrict__ acc) {
@@ -151,7 +166,8 @@ __global__ void k_scale_complex(long long n, double* __restrict__ u, double s) {
 template <typename T, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur, T* __restrict__ prev_out,
                                                       const T* __restrict__ kap, const T* __restrict__ S,
-                                                      double cs, double sn, Geom g, int zc) {
+                                                      double cs, double sn, Geom g, int zc,
+                                                      const unsigned char* __restrict__ scol) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid || m.z0 >= m.z1) return;
     const long long sZ = (long long)g.sx * g.sy;
@@ -163,6 +179,8 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
     nbxy += (m.ix == g.nx) & (int)((g.abc >> 1) & 1u);
     nbxy += (m.iy == 0) & (int)((g.abc >> 2) & 1u);
     nbxy += (m.iy == g.ny) & (int)((g.abc >> 3) & 1u);
+    // a column without source inside the grid (0 < z < nz) reads S only on its two z-faces
+    const bool col_src = !(FLAGS & kStepSrc) || !scol || scol[m.ix + (long long)g.sx * m.iy];
     T ym = cur[j + (m.z0 > 0 ? -sZ : sZ)];
     T yc = cur[j];
     for (int iz = m.z0; iz < m.z1; ++iz) {
@@ -171,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
         const T k = __ldcs(kap + j);  // streamed: keep L2 for the two wave fields reused next step
         const T yp = prev_out[j];
         T rhs = T(2) * yc - k * L;
-        if (FLAGS & kStepSrc) rhs += S[2 * j] * (T)cs + S[2 * j + 1] * (T)sn;
+        if ((FLAGS & kStepSrc) && (col_src || iz == 0 || iz == g.nz)) rhs += S[2 * j] * (T)cs + S[2 * j + 1] * (T)sn;
         const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         T out;
         if (nb == 0) {
@@ -193,7 +211,8 @@ __global__ void __launch_bounds__(kThreads) k_step3d7(const T* __restrict__ cur,
 template <typename T, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ cur, T* __restrict__ prev_out,
                                                          const T* __restrict__ kap, const T* __restrict__ S,
-                                                         double cs, double sn, Geom g, int zc) {
+                                                         double cs, double sn, Geom g, int zc,
+                                                         const unsigned char* __restrict__ scol) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid || m.z0 >= m.z1) return;
     const long long sZ = (long long)g.sx * g.sy;
@@ -205,10 +224,13 @@ __global__ void __launch_bounds__(kThreads) k_step3d7_z2(const T* __restrict__ c
     nbxy += (m.ix == g.nx) & (int)((g.abc >> 1) & 1u);
     nbxy += (m.iy == 0) & (int)((g.abc >> 2) & 1u);
     nbxy += (m.iy == g.ny) & (int)((g.abc >> 3) & 1u);
+    // a column without source inside the grid (0 < z < nz) reads S only on its two z-faces
+    const bool col_src = !(FLAGS & kStepSrc) || !scol || scol[m.ix + (long long)g.sx * m.iy];
     auto update = [&](T yc, T ym, T yz, long long jj, int iz, T sxy, T k, T yp) {
         const T L = T(6) * yc - (sxy + (ym + yz));
         T rhs = T(2) * yc - k * L;
-        if (FLAGS & kStepSrc) rhs += S[2 * jj] * (T)cs + S[2 * jj + 1] * (T)sn;
+        if ((FLAGS & kStepSrc) && (col_src || iz == 0 || iz == g.nz))
+            rhs += S[2 * jj] * (T)cs + S[2 * jj + 1] * (T)sn;
         const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         T out;
         if (nb == 0) {
@@ -395,7 +417,8 @@ inline bool step_v4_ok(const Geom& g, const void* cur, const void* prev, const v
 template <typename T, int FLAGS, int K>
 __global__ void __launch_bounds__(kThreads) k_step3d7_zk(const T* __restrict__ cur, T* __restrict__ prev_out,
                                                          const T* __restrict__ kap, const T* __restrict__ S,
-                                                         double cs, double sn, Geom g, int zc) {
+                                                         double cs, double sn, Geom g, int zc,
+                                                         const unsigned char* __restrict__ scol) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid || m.z0 >= m.z1) return;
     const long long sZ = (long long)g.sx * g.sy;
@@ -407,10 +430,13 @@ __global__ void __launch_bounds__(kThreads) k_step3d7_zk(const T* __restrict__ c
     nbxy += (m.ix == g.nx) & (int)((g.abc >> 1) & 1u);
     nbxy += (m.iy == 0) & (int)((g.abc >> 2) & 1u);
     nbxy += (m.iy == g.ny) & (int)((g.abc >> 3) & 1u);
+    // a column without source inside the grid (0 < z < nz) reads S only on its two z-faces
+    const bool col_src = !(FLAGS & kStepSrc) || !scol || scol[m.ix + (long long)g.sx * m.iy];
     auto update = [&](T yc, T ym, T yz, long long jj, int iz, T sxy, T k, T yp) {
         const T L = T(6) * yc - (sxy + (ym + yz));
         T rhs = T(2) * yc - k * L;
-        if (FLAGS & kStepSrc) rhs += S[2 * jj] * (T)cs + S[2 * jj + 1] * (T)sn;
+        if ((FLAGS & kStepSrc) && (col_src || iz == 0 || iz == g.nz))
+            rhs += S[2 * jj] * (T)cs + S[2 * jj + 1] * (T)sn;
         const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         T out;
         if (nb == 0) {
@@ -1044,7 +1070,7 @@ inline dim3 plane_grid(const Geom& g, int zc) {
 
 template <typename T, int ORDER, int FLAGS>
 void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const T* S, double cs, double sn,
-                   int zc, cudaStream_t st) {
+                   int zc, const unsigned char* scol, cudaStream_t st) {
     // zc < 0 selects the variants of the 3D 7-point kernel with several z-planes per loop
     // iteration: -zc = planes per thread, plus kZk4 for four planes per iteration (else two);
     // kZcFlat the FP32 vector form (other types and stencils: their default kernel)
@@ -1064,11 +1090,11 @@ void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const T* 
     }
     if (ORDER == 2 && g.dim == 3 && zc < 0 && (-zc) >= kZk4) {
         const int z = -zc - kZk4;
-        k_step3d7_zk<T, FLAGS, 4><<<plane_grid(g, z), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z);
+        k_step3d7_zk<T, FLAGS, 4><<<plane_grid(g, z), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, z, scol);
     } else if (ORDER == 2 && g.dim == 3 && zc < 0) {
-        k_step3d7_z2<T, FLAGS><<<plane_grid(g, -zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, -zc);
+        k_step3d7_z2<T, FLAGS><<<plane_grid(g, -zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, -zc, scol);
     } else if (ORDER == 2 && g.dim == 3) {
-        k_step3d7<T, FLAGS><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, zc);
+        k_step3d7<T, FLAGS><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, zc, scol);
     } else if (ORDER == 4 && g.dim == 3) {
         k_step3d13<T, FLAGS><<<plane_grid(g, zc), kThreads, 0, st>>>(cur, prev, kap, S, cs, sn, g, zc);
     } else {
@@ -1078,14 +1104,14 @@ void step_dispatch(const Geom& g, const T* cur, T* prev, const T* kap, const T* 
 
 template <typename T, int ORDER>
 void step_flags(const Geom& g, const T* cur, T* prev, const T* kap, const T* S, double cs, double sn,
-                int flags, int zc, cudaStream_t st) {
+                int flags, int zc, const unsigned char* scol, cudaStream_t st) {
     switch (flags) {
-        case 0: step_dispatch<T, ORDER, 0>(g, cur, prev, kap, S, cs, sn, zc, st); break;
-        case kStepSrc: step_dispatch<T, ORDER, kStepSrc>(g, cur, prev, kap, S, cs, sn, zc, st); break;
-        case kStepPrevScaled: step_dispatch<T, ORDER, kStepPrevScaled>(g, cur, prev, kap, S, cs, sn, zc, st); break;
-        case kStepNoDiv: step_dispatch<T, ORDER, kStepNoDiv>(g, cur, prev, kap, S, cs, sn, zc, st); break;
+        case 0: step_dispatch<T, ORDER, 0>(g, cur, prev, kap, S, cs, sn, zc, scol, st); break;
+        case kStepSrc: step_dispatch<T, ORDER, kStepSrc>(g, cur, prev, kap, S, cs, sn, zc, scol, st); break;
+        case kStepPrevScaled: step_dispatch<T, ORDER, kStepPrevScaled>(g, cur, prev, kap, S, cs, sn, zc, scol, st); break;
+        case kStepNoDiv: step_dispatch<T, ORDER, kStepNoDiv>(g, cur, prev, kap, S, cs, sn, zc, scol, st); break;
         case kStepPrevScaled | kStepNoDiv:
-            step_dispatch<T, ORDER, kStepPrevScaled | kStepNoDiv>(g, cur, prev, kap, S, cs, sn, zc, st);
+            step_dispatch<T, ORDER, kStepPrevScaled | kStepNoDiv>(g, cur, prev, kap, S, cs, sn, zc, scol, st);
             break;
         default: break;
     }
@@ -1096,12 +1122,19 @@ void step_flags(const Geom& g, const T* cur, T* prev, const T* kap, const T* S, 
 // ---- launchers ------------------------------------------------------------------------
 template <typename T>
 void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, const T* S, double cs,
-                 double sn, int flags, int zc, cudaStream_t st) {
+                 double sn, int flags, int zc, cudaStream_t st, const unsigned char* scol) {
     note_launch(1);
     if (order == 2)
-        step_flags<T, 2>(g, cur, prev, kap, S, cs, sn, flags, zc, st);
+        step_flags<T, 2>(g, cur, prev, kap, S, cs, sn, flags, zc, scol, st);
     else
-        step_flags<T, 4>(g, cur, prev, kap, S, cs, sn, flags, zc, st);
+        step_flags<T, 4>(g, cur, prev, kap, S, cs, sn, flags, zc, scol, st);
+}
+
+void launch_source_columns(const Geom& g, const double* S, unsigned char* scol, cudaStream_t st) {
+    note_launch(1);
+    const long long plane = (long long)g.sx * g.sy;
+    const unsigned blocks = (unsigned)std::min<long long>((plane + kThreads - 1) / kThreads, 4096);
+    k_source_columns<<<blocks, kThreads, 0, st>>>(g, S, scol);
 }
 
 template <typename T>
@@ -1198,7 +1231,7 @@ long long plane_blocks(const Geom& g, int zc) {
 
 #define CMCG_INST(T)                                                                                           \
     template void launch_step<T>(const Geom&, int, const T*, T*, const T*, const T*, double, double, int,        \
-                                 int, cudaStream_t);                                                           \
+                                 int, cudaStream_t, const unsigned char*);                                     \
     template void launch_start<T>(const Geom&, int, const T*, const double*, T*, T*, const T*, const double*,   \
                                   double, int, cudaStream_t);                                                  \
     template void launch_end<T>(const Geom&, int, int, const T*, const T*, const T*, const double*, const T*,   \
