@@ -252,13 +252,14 @@ PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool
     // T-precision copy of w0 for the endpoint stencils (FP32: in the temp buffer, which the
     // forward period does not otherwise use)
     b.w0t = w0;
-    if (std::is_same<T, float>::value) {
+    const bool v32 = std::is_same<T, float>::value && H->vec32_active;  // w0, w1 hold floats
+    if (std::is_same<T, float>::value && !v32) {
         float* w0f = (float*)H->tmp;
         if (!w0f_ready) launch_to_float(g.np, w0, w0f, H->st);
         b.w0t = w0f;
     }
     launch_start<T>(g, H->order, (const T*)b.w0t, w1, (T*)b.prev, (T*)b.cur, kap, src ? H->S : nullptr, H->dt,
-                    zce, H->st);
+                    zce, H->st, v32);
     return b;
 }
 
@@ -365,8 +366,8 @@ void fwd_end(cmcg_handle* H, const PeriodBuffers& b, const double* w1, bool src,
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     const double thN = H->omega * H->N * H->dt;
-    launch_end<T>(g, H->order, fp32_handoff<T>(mode) ? 2 : mode, (const T*)b.cur, (const T*)b.prev,
-                  (const T*)b.w0t, w1, kap, H->mass,
+    const int m = fp32_handoff<T>(mode) ? (H->vec32_active ? 3 : 2) : mode;
+    launch_end<T>(g, H->order, m, (const T*)b.cur, (const T*)b.prev, (const T*)b.w0t, w1, kap, H->mass,
                   src ? H->S : nullptr, cos(thN), sin(thN), out0, out1, H->red(), H->dt, zce, H->st);
     H->periods += 1;
 }
@@ -438,8 +439,9 @@ void adj_end(cmcg_handle* H, const PeriodBuffers& b, const double* a, const doub
     const Geom& g = H->g;
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
-    launch_adj_final<T>(g, H->order, fp32_handoff<T>(mode) ? 2 : mode, (const T*)b.cur, (const T*)b.prev, H->mass,
-                        kap, H->minv, a, bb, d0, d1, o0, o1, gt1, H->red(), H->dt, zce, H->st);
+    const int m = fp32_handoff<T>(mode) ? (H->vec32_active ? 3 : 2) : mode;
+    launch_adj_final<T>(g, H->order, m, (const T*)b.cur, (const T*)b.prev, H->mass, kap, H->minv, a, bb, d0, d1, o0,
+                        o1, gt1, H->red(), H->dt, zce, H->st);
     H->periods += 1;
 }
 
@@ -614,12 +616,40 @@ bool inexact(const cmcg_handle* H) { return (H->opt.flags & CMCG_FLAG_INEXACT_RI
 void apply_B(cmcg_handle* H, bool first, bool lowp, bool b_ready) {
     const Geom& g = H->g;
     Red red = H->red();
-    if (!b_ready) launch_to_float(g.np, H->rh0, H->lv[0].b, H->st);
+    const bool v32 = H->vec32_active;  // rhat, ghat and z are FP32 vectors
+    if (!b_ready) {
+        if (v32) cudaMemcpyAsync(H->lv[0].b, H->rh0, sizeof(float) * g.np, cudaMemcpyDeviceToDevice, H->st);
+        else launch_to_float(g.np, H->rh0, H->lv[0].b, H->st);
+    }
     vcycle(H, 0);
     if (!H->has_dir) launch_wsum_float(g, H->lv[0].x, red, H->st);
-    launch_fcg_dots(g, H->lv[0].x, H->volume, !H->has_dir, lowp, H->rh0, H->rh1, H->minv, H->gh0, H->gh1, H->r0, H->r1,
-                    red, first, H->st);
+    launch_fcg_dots(g, H->lv[0].x, H->volume, !H->has_dir, lowp || v32, H->rh0, H->rh1, H->minv, H->gh0, H->gh1, H->r0,
+                    H->r1, red, first, H->st, v32);
     H->riesz_iters += 1;
+}
+
+// Start of an inner solve on FP32 CG vectors: rhat = float(ghat) from the FP64 gradient,
+// z = B rhat and gamma0 (apply_B), d = z; leaves vec32_active set.
+void begin_vec32_inner(cmcg_handle* H) {
+    const long long n = H->g.np;
+    launch_to_float(n, H->gh0, (float*)H->rh0, H->st);
+    launch_to_float(n, H->gh1, (float*)H->rh1, H->st);
+    H->vec32_active = true;
+    apply_B(H, true, true);
+    cudaMemcpyAsync(H->d0, H->r0, sizeof(float) * n, cudaMemcpyDeviceToDevice, H->st);
+    cudaMemcpyAsync(H->d1, H->r1, sizeof(float) * n, cudaMemcpyDeviceToDevice, H->st);
+}
+
+// W += w: the inner correction (FP32 vectors on a vec32 handle) into the FP64 iterate.
+void add_correction(cmcg_handle* H, double* W0, double* W1) {
+    const long long n = H->g.np;
+    if (H->vec32) {
+        launch_add_float(n, (const float*)H->w0, W0, H->st);
+        launch_add_float(n, (const float*)H->w1, W1, H->st);
+    } else {
+        launch_axpy(n, 1.0, H->w0, W0, H->st);
+        launch_axpy(n, 1.0, H->w1, W1, H->st);
+    }
 }
 
 // One CG iteration captured as a CUDA graph.  Capture needs a created stream that is not
@@ -716,27 +746,37 @@ template <typename T>
 int fcg_loop(cmcg_handle* H, double tol, int max_iter, int* iters, double* rel_out) {
     const long long n = H->g.np;
     Red red = H->red();
-    cudaMemcpyAsync(H->rh0, H->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
-    cudaMemcpyAsync(H->rh1, H->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
-    apply_B(H, true, std::is_same<T, float>::value);
-    cudaMemcpyAsync(H->d0, H->r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
-    cudaMemcpyAsync(H->d1, H->r1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+    const bool f32 = std::is_same<T, float>::value;
+    const bool v32 = f32 && H->vec32;  // the inner solve of mixed precision: FP32 CG vectors
+    struct Reset {  // vec32_active holds only while this loop enqueues work
+        cmcg_handle* h;
+        ~Reset() { h->vec32_active = false; }
+    } reset{H};
+    if (v32) {
+        begin_vec32_inner(H);
+    } else {
+        cudaMemcpyAsync(H->rh0, H->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+        cudaMemcpyAsync(H->rh1, H->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+        apply_B(H, true, f32);
+        cudaMemcpyAsync(H->d0, H->r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+        cudaMemcpyAsync(H->d1, H->r1, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
+    }
     int rc = sync_read(H);
     if (rc != CMCG_OK) return rc;
     if (H->hsc[SC_STATUS] != 0.0) return CMCG_ERR_DIVERGED;
     double rel = H->hsc[SC_REL];
     H->hist.push_back(rel * H->hist_scale);
     int it = 0;
-    // FP32 periods read float(d0); the direction update writes it for the next iteration, and
-    // the dual-residual update writes float(rhat0) for the V-cycle
-    const bool f32 = std::is_same<T, float>::value;
-    float* d0f = f32 ? (float*)H->tmp : nullptr;
-    if (f32) launch_to_float(n, H->d0, d0f, H->st);
+    // FP32 periods read float(d0) (with FP32 vectors d0 itself); the direction update writes it
+    // for the next iteration, and the dual-residual update writes float(rhat0) for the V-cycle
+    float* d0f = f32 && !v32 ? (float*)H->tmp : nullptr;
+    if (d0f) launch_to_float(n, H->d0, d0f, H->st);
     auto body = [&]() {
         gradient<T>(H, H->d0, H->d1, false, H->d0, H->d1, false, f32);  // 5.1: ghat_d = H d
-        launch_fcg_update(n, H->w0, H->w1, H->rh0, H->rh1, H->d0, H->d1, H->gh0, H->gh1, red, H->st, H->lv[0].b);
+        launch_fcg_update(n, H->w0, H->w1, H->rh0, H->rh1, H->d0, H->d1, H->gh0, H->gh1, red, H->st, H->lv[0].b,
+                          v32);
         apply_B(H, false, f32, true);                                      // 5.2 on the residual
-        launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st, d0f);  // 5.7
+        launch_cg_direction(n, H->r0, H->r1, H->d0, H->d1, red, H->st, d0f, v32);  // 5.7
     };
     // The iteration's launches and arguments do not change (its scalars live on the device), so
     // it is captured once as a CUDA graph and replayed: on small grids the host's launch rate,
@@ -917,8 +957,7 @@ int solve_mixed(cmcg_handle* H, double tol, cmcg_stats* stats) {
         rc = cg_loop<float>(H, std::min(inner, 0.5), H->opt.max_iter - total, &it, &irel);
         if (rc < 0) return rc;
         total += it;
-        launch_axpy(n, 1.0, H->w0, H->wo0, H->st);
-        launch_axpy(n, 1.0, H->w1, H->wo1, H->st);
+        add_correction(H, H->wo0, H->wo1);
     }
     // the returned iterate lives in (w0, w1)
     cudaMemcpyAsync(H->w0, H->wo0, sizeof(double) * n, cudaMemcpyDeviceToDevice, H->st);
@@ -1237,6 +1276,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
         return CMCG_ERR_CUDA;
     }
     H->timing = (o.flags & CMCG_FLAG_TIMING) != 0;
+    H->vec32 = o.precision == CMCG_MIXED && (o.flags & CMCG_FLAG_INEXACT_RIESZ) && !(o.flags & CMCG_FLAG_FIRST_ORDER);
     if (H->timing)
         for (int e = 0; e < 8; ++e) cudaEventCreate(&H->ev[e]);
     auto fail = [&](int code) {

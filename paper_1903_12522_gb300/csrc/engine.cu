@@ -120,9 +120,17 @@ PeriodBuffers after_steps(PeriodBuffers b, int nsteps) {
     return b;
 }
 
-// The per-slot prologue of a unit that ends with "z = B rhat, d = z" (OUTER, INIT32).
+// The per-slot prologue of a unit that ends with "z = B rhat, d = z" (OUTER, INIT32).  On a
+// handle with FP32 CG vectors (mixed precision) the inner vectors start as floats; gamma0, the
+// outer residual, is then reduced in FP32 from float(rhat) (rhat is the current residual, so
+// its rounding is relative to its own size).
 void reset_direction(cmcg_handle* h) {
     const long long n = h->g.np;
+    if (h->vec32) {
+        begin_vec32_inner(h);
+        h->vec32_active = false;
+        return;
+    }
     cudaMemcpyAsync(h->rh0, h->gh0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
     cudaMemcpyAsync(h->rh1, h->gh1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st);
     apply_B(h, true, false);
@@ -162,8 +170,7 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
         if (sl.unit == U_OUTER) {
             on_side(e, sl.h, lane++, [](cmcg_handle* h) {
                 const long long n = h->g.np;
-                launch_axpy(n, 1.0, h->w0, h->wo0, h->st);
-                launch_axpy(n, 1.0, h->w1, h->wo1, h->st);
+                add_correction(h, h->wo0, h->wo1);
                 gradient<double>(h, h->wo0, h->wo1, true, h->wo0, h->wo1, false);
                 launch_fill(h->w0, n, 0.0, h->st);
                 launch_fill(h->w1, n, 0.0, h->st);
@@ -192,7 +199,11 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
         std::vector<BatchItem> items(2 * (size_t)m);
         for (int i = 0; i < m; ++i) {
             cmcg_handle* h = e->slots[inner[i]].h;
-            on_side(e, h, lane + i, [&](cmcg_handle* hh) { fb[i] = fwd_begin<float>(hh, hh->d0, hh->d1, false); });
+            on_side(e, h, lane + i, [&](cmcg_handle* hh) {
+                hh->vec32_active = hh->vec32;
+                fb[i] = fwd_begin<float>(hh, hh->d0, hh->d1, false);
+                hh->vec32_active = false;
+            });
             items[i] = make_item(h, fb[i], false, e->zc3);
             items[i].offset = total;
             total += items[i].blocks;
@@ -206,8 +217,10 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
         for (int i = 0; i < m; ++i) {
             cmcg_handle* h = e->slots[inner[i]].h;
             on_side(e, h, lane + i, [&](cmcg_handle* hh) {
+                hh->vec32_active = hh->vec32;
                 fwd_end<float>(hh, after_steps(fb[i], hh->N - 1), hh->d1, false, 0, hh->z0, hh->z1);
                 ab[i] = adj_begin<float>(hh, hh->z0, hh->z1, 0);
+                hh->vec32_active = false;
             });
             items[m + i] = make_item(h, ab[i], true, e->zc3);
             items[m + i].offset = total_a;
@@ -222,12 +235,14 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
             cmcg_handle* h = e->slots[inner[i]].h;
             on_side(e, h, lane + i, [&](cmcg_handle* hh) {
                 const long long n = hh->g.np;
+                hh->vec32_active = hh->vec32;
                 adj_end<float>(hh, after_steps(ab[i], hh->N - 1), hh->z0, hh->z1, 0, hh->d0, hh->d1, hh->gh0, hh->gh1,
                                nullptr);
                 launch_fcg_update(n, hh->w0, hh->w1, hh->rh0, hh->rh1, hh->d0, hh->d1, hh->gh0, hh->gh1, hh->red(),
-                                  hh->st, hh->lv[0].b);
+                                  hh->st, hh->lv[0].b, hh->vec32);
                 apply_B(hh, false, true, true);
-                launch_cg_direction(n, hh->r0, hh->r1, hh->d0, hh->d1, hh->red(), hh->st);
+                launch_cg_direction(n, hh->r0, hh->r1, hh->d0, hh->d1, hh->red(), hh->st, nullptr, hh->vec32);
+                hh->vec32_active = false;
             });
         }
         // the descriptors are uploaded before the tick (upload_items)

@@ -36,11 +36,13 @@ void launch_step(const Geom& g, int order, const T* cur, T* prev, const T* kap, 
 // scol of S (3D): one byte per (x, y) column
 void launch_source_columns(const Geom& g, const double* S, unsigned char* scol, cudaStream_t st);
 template <typename T>
+// w1_float (T = float): w1 points to floats (the FP32 CG vectors of a mixed-precision inner solve)
 void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y0, T* y1, const T* kap,
-                  const double* S, double dt, int zc, cudaStream_t st);
+                  const double* S, double dt, int zc, cudaStream_t st, bool w1_float = false);
 // mode 0: z = E (Pi(w) - w) and J; mode 1: (y(T), y_t(T)); mode 2 (T = float only): mode 0
 // with z0 and t = D^-1 z1 written as floats into out0 and out1 (the FP32 hand-off to the
-// adjoint period: launch_adj_start with a = z0 and t, then launch_adj_final mode 2).
+// adjoint period: launch_adj_start with a = z0 and t, then launch_adj_final mode 2); mode 3
+// (T = float only): mode 2 with w1 pointing to floats (FP32 CG vectors).
 template <typename T>
 void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const T* w0t, const double* w1,
                 const T* kap, const double* mass, const double* S, double cs, double sn, double* out0, double* out1,
@@ -53,7 +55,8 @@ template <typename T, typename A>
 void launch_adj_start(const Geom& g, int order, const A* a, const T* t, const double* mass, const T* kap,
                       T* cur, T* prev, double dt, int zc, cudaStream_t st);
 // mode 0: gradient (gt1 may be null); mode 1: q; mode 2 (T = float only): mode 0 reading the
-// FP32 hand-off (z0, t) through z0 and z1.
+// FP32 hand-off (z0, t) through z0 and z1; mode 3 (T = float only): mode 2 with d0, d1, o0, o1
+// pointing to floats (FP32 CG vectors).
 template <typename T>
 void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass, const T* kap,
                       const double* minv, const double* z0, const double* z1, const double* d0, const double* d1,
@@ -125,9 +128,9 @@ void launch_cg_init(long long n, const double* gt0, const double* gt1, const dou
 void launch_cg_update(long long n, double* w0, double* w1, double* r0, double* r1, double* rh0, double* rh1,
                       const double* d0, const double* d1, const double* gt0, const double* gt1, const double* gh0,
                       const double* gh1, double sign, Red red, cudaStream_t st);
-// d0f (optional): also float(d0).
+// d0f (optional): also float(d0).  f32vec: r and d point to floats (FP32 CG vectors).
 void launch_cg_direction(long long n, const double* r0, const double* r1, double* d0, double* d1, Red red,
-                         cudaStream_t st, float* d0f = nullptr);
+                         cudaStream_t st, float* d0f = nullptr, bool f32vec = false);
 // Reductions on the solution for the compatibility-condition shift: sums of
 // (F re, F im, (M u) re, (M u) im, (B u) re, (B u) im) into sc[SC_R0..SC_R5].
 void launch_recover(const Geom& g, const double* w0, const double* w1, double omega_hat, const double* S,
@@ -136,13 +139,17 @@ void launch_axpy(long long n, double a, const double* x, double* y, cudaStream_t
 void launch_reciprocal(long long n, const double* m, double* out, cudaStream_t st);
 // Flexible CG with an approximate Riesz map (one multigrid V-cycle).
 // bf (optional): also float(rhat0), the V-cycle's right-hand side.
+// f32vec: every vector argument points to floats (FP32 CG vectors of a mixed-precision inner solve).
 void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double* rh1, const double* d0,
                        const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st,
-                       float* bf = nullptr);
-// lowp: FP32 arithmetic with compensated FP32 partial sums (inside an FP32-period solve).
+                       float* bf = nullptr, bool f32vec = false);
+// y += x, x in FP32.
+void launch_add_float(long long n, const float* x, double* y, cudaStream_t st);
+// lowp: FP32 arithmetic with compensated FP32 partial sums (inside an FP32-period solve);
+// f32vec: rh, gh, z point to floats (implies lowp).
 void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, bool lowp, const double* rh0,
                      const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,
-                     double* z1, Red red, bool first, cudaStream_t st);
+                     double* z1, Red red, bool first, cudaStream_t st, bool f32vec = false);
 void launch_wsum_float(const Geom& g, const float* x, Red red, cudaStream_t st);
 void launch_shift(long long n, double* u, const double* kap64, double lre, double lim, cudaStream_t st);
 // Sums of the compatibility condition for a complex field u: 1.F^, 1.M u, 1.B u -> sc[SC_R0..+5].

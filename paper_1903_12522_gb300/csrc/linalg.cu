@@ -167,15 +167,17 @@ __global__ void __launch_bounds__(kT) k_cg_update(long long n, double* __restric
     }
 }
 
-// Step 5.7: d = r + beta d; with d0f, also float(d0) (what FP32 periods read).
-__global__ void __launch_bounds__(kT) k_cg_direction(long long n, const double* __restrict__ r0,
-                                                     const double* __restrict__ r1, double* __restrict__ d0,
-                                                     double* __restrict__ d1, float* __restrict__ d0f,
+// Step 5.7: d = r + beta d; with d0f, also float(d0) (what FP32 periods read).  V: the CG
+// vectors' type (float: the inner solve of mixed precision, whose periods read d0 directly).
+template <typename V>
+__global__ void __launch_bounds__(kT) k_cg_direction(long long n, const V* __restrict__ r0,
+                                                     const V* __restrict__ r1, V* __restrict__ d0,
+                                                     V* __restrict__ d1, float* __restrict__ d0f,
                                                      const double* __restrict__ sc) {
-    const double beta = sc[SC_BETA];
+    const V beta = (V)sc[SC_BETA];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const double v = r0[j] + beta * d0[j];
+        const V v = r0[j] + beta * d0[j];
         d0[j] = v;
         d1[j] = r1[j] + beta * d1[j];
         if (d0f) d0f[j] = (float)v;
@@ -295,32 +297,40 @@ __global__ void k_reciprocal(long long n, const double* __restrict__ m, double* 
 // Step 5.3-5.5 with the dual residual: alpha = gamma / (ghat_d . d); v -= alpha d;
 // rhat -= alpha ghat_d.  The primal residual z = B rhat is formed afterwards (k_fcg_dots); with
 // bf, float(rhat0) is written for its V-cycle.
-__global__ void __launch_bounds__(kT) k_fcg_update(long long n, double* __restrict__ w0, double* __restrict__ w1,
-                                                   double* __restrict__ rh0, double* __restrict__ rh1,
-                                                   const double* __restrict__ d0, const double* __restrict__ d1,
-                                                   const double* __restrict__ gh0, const double* __restrict__ gh1,
+template <typename V>
+__global__ void __launch_bounds__(kT) k_fcg_update(long long n, V* __restrict__ w0, V* __restrict__ w1,
+                                                   V* __restrict__ rh0, V* __restrict__ rh1,
+                                                   const V* __restrict__ d0, const V* __restrict__ d1,
+                                                   const V* __restrict__ gh0, const V* __restrict__ gh1,
                                                    float* __restrict__ bf, double* __restrict__ sc) {
-    const double alpha = sc[SC_GAMMA] / sc[SC_GD];
+    const V alpha = (V)(sc[SC_GAMMA] / sc[SC_GD]);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         w0[j] -= alpha * d0[j];
         w1[j] -= alpha * d1[j];
-        const double r = rh0[j] - alpha * gh0[j];
+        const V r = rh0[j] - alpha * gh0[j];
         rh0[j] = r;
         rh1[j] -= alpha * gh1[j];
         if (bf) bf[j] = (float)r;
     }
 }
 
+// y += x with x in FP32 (the inner correction of mixed precision added to the FP64 iterate).
+__global__ void k_add_float(long long n, const float* __restrict__ x, double* __restrict__ y) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) y[j] += (double)x[j];
+}
+
 // z0 from the FP32 V-cycle output with the W-weighted mean removed when K is singular,
 // z1 = M^-1 rhat1; gamma' = z . rhat; for the Polak-Ribiere update also z . ghat_d:
 // beta = -alpha (z . ghat_d) / gamma (= gamma'/gamma when B is exactly E^-1).  first != 0:
 // Step (4), gamma0 = gamma', no beta.
+template <typename V>
 __global__ void __launch_bounds__(kT) k_fcg_dots(Geom g, const float* __restrict__ zf, double inv_volume,
-                                                 int remove_mean, const double* __restrict__ rh0,
-                                                 const double* __restrict__ rh1, const double* __restrict__ minv,
-                                                 const double* __restrict__ gh0, const double* __restrict__ gh1,
-                                                 double* __restrict__ z0, double* __restrict__ z1, Red red,
+                                                 int remove_mean, const V* __restrict__ rh0,
+                                                 const V* __restrict__ rh1, const double* __restrict__ minv,
+                                                 const V* __restrict__ gh0, const V* __restrict__ gh1,
+                                                 V* __restrict__ z0, V* __restrict__ z1, Red red,
                                                  int first, int lowp) {
     const double mu = remove_mean ? red.sc[SC_P_XW] * inv_volume : 0.0;
     double acc[2] = {0.0, 0.0};
@@ -335,8 +345,8 @@ __global__ void __launch_bounds__(kT) k_fcg_dots(Geom g, const float* __restrict
             const float a0 = m != 0.0f ? zf[j] - muf : 0.0f;
             const float r1 = (float)rh1[j];
             const float a1 = r1 * m;
-            z0[j] = (double)a0;
-            z1[j] = (double)a1;
+            z0[j] = (V)a0;
+            z1[j] = (V)a1;
             s0.add(a0 * (float)rh0[j] + a1 * r1);
             if (!first) s1.add(a0 * (float)gh0[j] + a1 * (float)gh1[j]);
         }
@@ -346,11 +356,11 @@ __global__ void __launch_bounds__(kT) k_fcg_dots(Geom g, const float* __restrict
         for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.np; j += stride) {
             const double m = minv[j];
             const double a0 = m != 0.0 ? (double)zf[j] - mu : 0.0;
-            const double a1 = rh1[j] * m;
-            z0[j] = a0;
-            z1[j] = a1;
-            acc[0] += a0 * rh0[j] + a1 * rh1[j];
-            if (!first) acc[1] += a0 * gh0[j] + a1 * gh1[j];
+            const double a1 = (double)rh1[j] * m;
+            z0[j] = (V)a0;
+            z1[j] = (V)a1;
+            acc[0] += a0 * (double)rh0[j] + a1 * (double)rh1[j];
+            if (!first) acc[1] += a0 * (double)gh0[j] + a1 * (double)gh1[j];
         }
     }
     if (grid_sum<2>(acc, red.partials, red.ticket) && threadIdx.x == 0) {
@@ -425,9 +435,13 @@ void launch_cg_update(long long n, double* w0, double* w1, double* r0, double* r
 }
 
 void launch_cg_direction(long long n, const double* r0, const double* r1, double* d0, double* d1, Red red,
-                         cudaStream_t st, float* d0f) {
+                         cudaStream_t st, float* d0f, bool f32vec) {
     note_launch(1);
-    k_cg_direction<<<vec_blocks(n), kT, 0, st>>>(n, r0, r1, d0, d1, d0f, red.sc);
+    if (f32vec)
+        k_cg_direction<float><<<vec_blocks(n), kT, 0, st>>>(n, (const float*)r0, (const float*)r1, (float*)d0,
+                                                            (float*)d1, d0f, red.sc);
+    else
+        k_cg_direction<double><<<vec_blocks(n), kT, 0, st>>>(n, r0, r1, d0, d1, d0f, red.sc);
 }
 
 void launch_scalar_residual(long long n, const double* r0, const double* r1, const double* rh0,
@@ -468,14 +482,26 @@ void launch_reciprocal(long long n, const double* m, double* out, cudaStream_t s
 }
 
 void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double* rh1, const double* d0,
-                       const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st, float* bf) {
+                       const double* d1, const double* gh0, const double* gh1, Red red, cudaStream_t st, float* bf,
+                       bool f32vec) {
     note_launch(1);
-    k_fcg_update<<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, rh0, rh1, d0, d1, gh0, gh1, bf, red.sc);
+    if (f32vec)
+        k_fcg_update<float><<<vec_blocks(n), kT, 0, st>>>(n, (float*)w0, (float*)w1, (float*)rh0, (float*)rh1,
+                                                          (const float*)d0, (const float*)d1, (const float*)gh0,
+                                                          (const float*)gh1, bf, red.sc);
+    else
+        k_fcg_update<double><<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, rh0, rh1, d0, d1, gh0, gh1, bf, red.sc);
+}
+
+void launch_add_float(long long n, const float* x, double* y, cudaStream_t st) {
+    note_launch(1);
+    k_add_float<<<vec_blocks(n), kT, 0, st>>>(n, x, y);
 }
 
 // k_fcg_dots needs more than 32 registers, so fewer than the 8 blocks per SM that
 // kMaxBlocksReduce assumes are resident: its grid-stride grid is one full wave of what this
 // GPU holds at once (cached per device; deterministic for a given GPU and build).
+template <typename V>
 static unsigned fcg_dots_blocks(long long n) {
     static int cached[64] = {};
     int dev = 0;
@@ -483,7 +509,7 @@ static unsigned fcg_dots_blocks(long long n) {
     int& c = cached[dev & 63];
     if (c == 0) {
         int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fcg_dots, kT, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fcg_dots<V>, kT, 0) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 ||
             sms < 1) {
             cudaGetLastError();
@@ -497,10 +523,16 @@ static unsigned fcg_dots_blocks(long long n) {
 
 void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, bool lowp, const double* rh0,
                      const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,
-                     double* z1, Red red, bool first, cudaStream_t st) {
+                     double* z1, Red red, bool first, cudaStream_t st, bool f32vec) {
     note_launch(1);
-    k_fcg_dots<<<fcg_dots_blocks(g.np), kT, 0, st>>>(g, zf, 1.0 / volume, remove_mean ? 1 : 0, rh0, rh1, minv, gh0,
-                                                     gh1, z0, z1, red, first ? 1 : 0, lowp ? 1 : 0);
+    if (f32vec)
+        k_fcg_dots<float><<<fcg_dots_blocks<float>(g.np), kT, 0, st>>>(
+            g, zf, 1.0 / volume, remove_mean ? 1 : 0, (const float*)rh0, (const float*)rh1, minv, (const float*)gh0,
+            (const float*)gh1, (float*)z0, (float*)z1, red, first ? 1 : 0, 1);
+    else
+        k_fcg_dots<double><<<fcg_dots_blocks<double>(g.np), kT, 0, st>>>(
+            g, zf, 1.0 / volume, remove_mean ? 1 : 0, rh0, rh1, minv, gh0, gh1, z0, z1, red, first ? 1 : 0,
+            lowp ? 1 : 0);
 }
 
 void launch_wsum_float(const Geom& g, const float* x, Red red, cudaStream_t st) {

@@ -60,6 +60,11 @@ struct cmcg_handle {
     unsigned* tickets = nullptr;
     double* sc = nullptr;
     double* hsc = nullptr;  // pinned host mirror of sc
+    // FP32 CG vectors: a mixed-precision handle with the V-cycle Riesz map keeps the vectors of
+    // its inner (FP32-period) flexible CG -- w, rhat, d, ghat, z -- as floats in the first half
+    // of their buffers; vec32_active is set while such an inner iteration is being enqueued
+    bool vec32 = false;
+    bool vec32_active = false;
     // residual history of the last solve: sqrt(gamma_k / gamma_0) per CG iteration, relative to
     // the zero initial guess (hist_scale converts a loop's own relative residual)
     std::vector<double> hist;
@@ -104,6 +109,10 @@ bool inexact(const cmcg_handle* H);
 // b_ready: the finest level's right-hand side already holds float(rhat0) (written by the
 // flexible-CG update), so the conversion pass is skipped.
 void apply_B(cmcg_handle* H, bool first, bool lowp, bool b_ready = false);
+// FP32 CG vectors (H->vec32): start of an inner solve from the FP64 gradient (rhat, z = B rhat,
+// gamma0, d = z as floats; sets vec32_active), and W += w of the finished inner solve.
+void begin_vec32_inner(cmcg_handle* H);
+void add_correction(cmcg_handle* H, double* W0, double* W1);
 int adj_step_flags(int k, int N);
 // Gradient periods (mode 0) in FP32 hand z from the forward end to the adjoint period as
 // floats in the z buffers: z0, and t = D^-1 z1 (D = M (1 + beta)) in place of z1.

@@ -555,8 +555,8 @@ __device__ __forceinline__ R weight_t(const Geom& g, int ix, int iy, int iz) {
 }
 
 // Period start: y0 = w0, y1 = w0 + dt (1 - beta) w1 + (S_re - kappa Lt w0) / 2.
-template <typename T, int ORDER, bool SRC>
-__global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, const double* __restrict__ w1,
+template <typename T, int ORDER, bool SRC, typename V = double>
+__global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, const V* __restrict__ w1,
                                                     T* __restrict__ y0, T* __restrict__ y1,
                                                     const T* __restrict__ kap, const double* __restrict__ S,
                                                     Geom g, double dt, int zc) {
@@ -594,9 +594,9 @@ __global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, c
 template <typename T>
 constexpr int kEndMinBlocks = std::is_same<T, float>::value ? 5 : 1;
 
-template <typename T, int ORDER, bool SRC, int MODE>
+template <typename T, int ORDER, bool SRC, int MODE, typename V = double>
 __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __restrict__ yN, const T* __restrict__ yNm1,
-                                                  const T* __restrict__ w0t, const double* __restrict__ w1,
+                                                  const T* __restrict__ w0t, const V* __restrict__ w1,
                                                   const T* __restrict__ kap, const double* __restrict__ mass,
                                                   const double* __restrict__ S, double cs, double sn,
                                                   double* __restrict__ out0, double* __restrict__ out1,
@@ -693,13 +693,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_start(const A* __restrict__ a,
 // is given: the exact Riesz map needs it, the V-cycle does not), and reduces
 // (ghat . d, sum ghat0).  MODE 2 (FP32) is MODE 0 on the FP32 hand-off of k_end: z0 in z0, and
 // z1 = M (1 + beta) t from t in z1.
-template <typename T, int ORDER, int MODE>
+template <typename T, int ORDER, int MODE, typename V = double>
 __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_adj_final(const T* __restrict__ s, const T* __restrict__ u1,
                                                         const double* __restrict__ mass, const T* __restrict__ kap,
                                                         const double* __restrict__ minv,
                                                         const double* __restrict__ z0, const double* __restrict__ z1,
-                                                        const double* __restrict__ d0, const double* __restrict__ d1,
-                                                        double* __restrict__ o0, double* __restrict__ o1,
+                                                        const V* __restrict__ d0, const V* __restrict__ d1,
+                                                        V* __restrict__ o0, V* __restrict__ o1,
                                                         double* __restrict__ gt1, Red red, Geom g, double dt, int zc) {
     const PlaneMap m = plane_map(g, zc);
     double acc[2] = {0.0, 0.0};
@@ -723,8 +723,8 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_adj_final(const 
             const T q0 = M * (sj - (T(1) - beta) * u1[j]) - T(0.5) * dtT * dtT * W * ih2 * L;
             const T q1 = dtT * M * (T(1) - beta) * sj;
             if (MODE == 1) {
-                o0[j] = dir ? 0.0 : (double)q0;
-                o1[j] = dir ? 0.0 : (double)q1;
+                o0[j] = dir ? V(0) : (V)q0;
+                o1[j] = dir ? V(0) : (V)q1;
             } else if (std::is_same<T, float>::value) {
                 // FP32 periods: z came from FP32 values, so the differences and products stay in
                 // FP32 (FP64 only holds the stored vectors)
@@ -739,17 +739,17 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_adj_final(const 
                 const float g0 = (float)q0 - zz0;
                 const float g1 = (float)q1 - zz1;
                 const float pd = g0 * (float)d0[j] + g1 * (float)d1[j];
-                o0[j] = dir ? 0.0 : (double)g0;
-                o1[j] = dir ? 0.0 : (double)g1;
+                o0[j] = dir ? V(0) : (V)g0;
+                o1[j] = dir ? V(0) : (V)g1;
                 if (gt1) gt1[j] = dir ? 0.0 : (double)(g1 * (float)minv[j]);
                 accf0.add(dir ? 0.0f : pd);
                 accf1.add(dir ? 0.0f : g0);
             } else {
                 const double g0 = (double)q0 - z0[j];
                 const double g1 = (double)q1 - z1[j];
-                const double pd = g0 * d0[j] + g1 * d1[j];
-                o0[j] = dir ? 0.0 : g0;
-                o1[j] = dir ? 0.0 : g1;
+                const double pd = g0 * (double)d0[j] + g1 * (double)d1[j];
+                o0[j] = dir ? V(0) : (V)g0;
+                o1[j] = dir ? V(0) : (V)g1;
                 if (gt1) gt1[j] = dir ? 0.0 : g1 * minv[j];
                 acc[0] += dir ? 0.0 : pd;
                 acc[1] += dir ? 0.0 : g0;
@@ -1139,9 +1139,22 @@ void launch_source_columns(const Geom& g, const double* S, unsigned char* scol, 
 
 template <typename T>
 void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y0, T* y1, const T* kap,
-                  const double* S, double dt, int zc, cudaStream_t st) {
+                  const double* S, double dt, int zc, cudaStream_t st, bool w1_float) {
     note_launch(1);
     const dim3 grid = plane_grid(g, zc);
+    if constexpr (std::is_same<T, float>::value) {
+        if (w1_float) {  // FP32 CG vectors: w1 holds floats
+            const float* w1f = (const float*)w1;
+            if (order == 2) {
+                if (S) k_start<T, 2, true, float><<<grid, kThreads, 0, st>>>(w0t, w1f, y0, y1, kap, S, g, dt, zc);
+                else k_start<T, 2, false, float><<<grid, kThreads, 0, st>>>(w0t, w1f, y0, y1, kap, S, g, dt, zc);
+            } else {
+                if (S) k_start<T, 4, true, float><<<grid, kThreads, 0, st>>>(w0t, w1f, y0, y1, kap, S, g, dt, zc);
+                else k_start<T, 4, false, float><<<grid, kThreads, 0, st>>>(w0t, w1f, y0, y1, kap, S, g, dt, zc);
+            }
+            return;
+        }
+    }
     if (order == 2) {
         if (S) k_start<T, 2, true><<<grid, kThreads, 0, st>>>(w0t, w1, y0, y1, kap, S, g, dt, zc);
         else k_start<T, 2, false><<<grid, kThreads, 0, st>>>(w0t, w1, y0, y1, kap, S, g, dt, zc);
@@ -1165,6 +1178,16 @@ void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, 
         if (mode == 2) {
             if (order == 2) { if (src) CMCG_END(2, true, 2); else CMCG_END(2, false, 2); }
             else { if (src) CMCG_END(4, true, 2); else CMCG_END(4, false, 2); }
+            return;
+        }
+        if (mode == 3) {  // mode 2 with FP32 CG vectors: w1 holds floats
+            const float* w1f = (const float*)w1;
+#define CMCG_END3(O, SRC)                                                                                      \
+    k_end<T, O, SRC, 2, float><<<grid, kThreads, 0, st>>>(yN, yNm1, w0t, w1f, kap, mass, S, cs, sn, out0, out1, \
+                                                          red, g, dt, zc)
+            if (order == 2) { if (src) CMCG_END3(2, true); else CMCG_END3(2, false); }
+            else { if (src) CMCG_END3(4, true); else CMCG_END3(4, false); }
+#undef CMCG_END3
             return;
         }
     }
@@ -1209,6 +1232,16 @@ void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u
             if (order == 2) CMCG_FIN(2, 2); else CMCG_FIN(4, 2);
             return;
         }
+        if (mode == 3) {  // mode 2 with FP32 CG vectors: d and the gradient are floats
+            const float *d0f = (const float*)d0, *d1f = (const float*)d1;
+            float *o0f = (float*)o0, *o1f = (float*)o1;
+#define CMCG_FIN3(O)                                                                                               \
+    k_adj_final<T, O, 2, float><<<grid, kThreads, 0, st>>>(s, u1, mass, kap, minv, z0, z1, d0f, d1f, o0f, o1f, gt1, \
+                                                           red, g, dt, zc)
+            if (order == 2) CMCG_FIN3(2); else CMCG_FIN3(4);
+#undef CMCG_FIN3
+            return;
+        }
     }
     if (order == 2) {
         if (mode == 0) CMCG_FIN(2, 0); else CMCG_FIN(2, 1);
@@ -1233,7 +1266,7 @@ long long plane_blocks(const Geom& g, int zc) {
     template void launch_step<T>(const Geom&, int, const T*, T*, const T*, const T*, double, double, int,        \
                                  int, cudaStream_t, const unsigned char*);                                     \
     template void launch_start<T>(const Geom&, int, const T*, const double*, T*, T*, const T*, const double*,   \
-                                  double, int, cudaStream_t);                                                  \
+                                  double, int, cudaStream_t, bool);                                            \
     template void launch_end<T>(const Geom&, int, int, const T*, const T*, const T*, const double*, const T*,   \
                                 const double*, const double*, double, double, double*, double*, Red, double,    \
                                 int, cudaStream_t);                                                            \
