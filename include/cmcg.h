@@ -147,7 +147,9 @@ typedef struct {
                                at a given tol does not depend on the run-up.                  */
     int tile[4];            /* launch shape of the leapfrog kernels, 0 = default.  [3] selects
                                the step scheme of 3D 7-point steps (the others keep one step per
-                               launch): 0 or 1 = one step per launch, [0] z-planes per thread
+                               launch): 0 = the default, scheme 3 on 3D 7-point grids and
+                               scheme 5 on 2D 5-point grids (the fastest measured); 1 = one
+                               step per launch, [0] z-planes per thread
                                (16); 2 = two FP32 steps per launch (temporal blocking), [1]
                                z-planes per block (24), [2] maximum interior tile height (16, at
                                most 16); 3 = one step per launch with [2] = 2 (default) or 4
