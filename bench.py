@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-comparators", action="store_true")
+    ap.add_argument("--no-l2-kappa", action="store_true", help="do not keep kappa resident in L2 (CMCG_FLAG_L2_KAPPA)")
     # profiling entry points (instead of the benchmark line): pieces of the solver timed with
     # CUDA events on a workload, for ncu captures and the measurements quoted in the design notes
     ap.add_argument("--profile", default=None,
@@ -110,6 +111,8 @@ def method_config(args):
         "runup_periods": args.runup,
         "runup": (f"{-args.runup} domain crossings at c_min, ramped sources (Sec. 4.3)" if args.runup < 0
                   else f"{args.runup} periods" if args.runup > 0 else "none"),
+        "l2_kappa": "off" if getattr(args, "no_l2_kappa", False) else
+                    "FP32 kappa kept in an L2 set-aside across steps (CMCG_FLAG_L2_KAPPA)",
     }
 
 
@@ -454,8 +457,10 @@ def run_ours(args):
     m_host = torch.from_numpy(np.ascontiguousarray(w.mask.ravel())).pin_memory()
     g_dev = g_host.to(dev).reshape(-1)
     rflag = cmcg.FLAG_INEXACT_RIESZ if args.riesz == "vcycle" else 0
+    l2flag = 0 if args.no_l2_kappa else cmcg.FLAG_L2_KAPPA
     s = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, precision=prec, dt=w.dt_target,
-                    flags=cmcg.FLAG_TIMING | rflag, max_iter=args.max_iter, device=dev, runup_periods=args.runup)
+                    flags=cmcg.FLAG_TIMING | rflag | l2flag, max_iter=args.max_iter, device=dev,
+                    runup_periods=args.runup)
     u = torch.empty(w.num_nodes, dtype=torch.complex128, device=dev)
     stream = s.stream
 
@@ -581,7 +586,8 @@ def run_ours(args):
         s.close()
         del s
         torch.cuda.empty_cache()
-        opts = cmcg.make_options(prec, dt=w.dt_target, flags=cmcg.FLAG_HOST_IO | rflag, runup_periods=args.runup)
+        opts = cmcg.make_options(prec, dt=w.dt_target, flags=cmcg.FLAG_HOST_IO | rflag | l2flag,
+                                 runup_periods=args.runup)
         grid = cmcg.make_grid(w.n, w.h)
         ws_t = torch.empty(cmcg.cmcg_workspace_size(grid, opts), dtype=torch.uint8, device=dev)
         c_dev = torch.empty_like(c_host, device=dev)

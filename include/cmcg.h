@@ -103,6 +103,16 @@ extern "C" {
                                CMCG_ERR_UNSUPPORTED.  cmcg_wave_period, cmcg_adjoint_period and
                                cmcg_riesz return CMCG_ERR_UNSUPPORTED on such a handle; use
                                cmcg_fo_period and cmcg_fo_adjoint_period. */
+#define CMCG_FLAG_L2_KAPPA 64 /* keep the FP32 coefficient kappa (4 bytes per node, read by
+                               every FP32 leapfrog step and never written) resident in the L2
+                               cache across steps: the handle's stream gets an access-policy
+                               window on it and the process's persisting-L2 set-aside is raised
+                               to its size (restored when the last such handle is destroyed).
+                               Applies to CMCG_FP32 / CMCG_MIXED handles on a created stream
+                               whose kappa fits the device's largest set-aside (84.7 MB on a
+                               GB300: grids up to 21 M nodes); otherwise ignored.  Side effects
+                               beyond the handle: the stream attribute (cleared at destroy) and
+                               the set-aside, which other work in the process shares. */
 
 /* ---- precision of the wave stepping ------------------------------------------------ */
 #define CMCG_FP64 0  /* every operation in FP64                                            */

@@ -28,6 +28,7 @@ FLAG_INEXACT_RIESZ = 4
 FLAG_FILTER = 8
 FLAG_NO_CG = 16
 FLAG_FIRST_ORDER = 32
+FLAG_L2_KAPPA = 64
 
 ERR_DEVICE_TIMEOUT = -7
 ENGINE_NO_GRAPH = 1

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <atomic>
 #include <chrono>
 #include <type_traits>
@@ -169,6 +170,65 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
 }
 
 int cuda_status() { return cudaGetLastError() == cudaSuccess ? CMCG_OK : CMCG_ERR_CUDA; }
+
+// ---- L2 residency of kappa (CMCG_FLAG_L2_KAPPA) ----------------------------------------------
+// The persisting-L2 set-aside is a per-process device limit: raised while any handle uses it,
+// restored (and the persisting lines released) when the last one is destroyed.
+static std::mutex g_l2_mu;
+static int g_l2_users = 0;
+static size_t g_l2_prev_limit = 0;
+
+void l2_kappa_begin(cmcg_handle* H) {
+    const cudaStream_t st = H->st;
+    if (!H->kap32 || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return;
+    int dev = 0, max_persist = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const size_t bytes = sizeof(float) * (size_t)H->g.np;
+    if (max_persist <= 0 || bytes > (size_t)max_persist) return;
+    std::lock_guard<std::mutex> lock(g_l2_mu);
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (g_l2_users == 0) g_l2_prev_limit = cur;
+    if (cur < bytes && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaStreamAttrValue attr = {};
+    attr.accessPolicyWindow.base_ptr = (void*)H->kap32;
+    attr.accessPolicyWindow.num_bytes = bytes;
+    attr.accessPolicyWindow.hitRatio = 1.0f;
+    attr.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    if (cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &attr) != cudaSuccess) {
+        cudaGetLastError();
+        if (g_l2_users == 0) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_prev_limit);
+        return;
+    }
+    g_l2_users += 1;
+    H->l2_kappa = true;
+}
+
+void l2_kappa_end(cmcg_handle* H) {
+    if (!H->l2_kappa) return;
+    cudaStreamSynchronize(H->st);
+    cudaStreamAttrValue attr = {};
+    attr.accessPolicyWindow.num_bytes = 0;  // no window
+    cudaStreamSetAttribute(H->st, cudaStreamAttributeAccessPolicyWindow, &attr);
+    std::lock_guard<std::mutex> lock(g_l2_mu);
+    if (--g_l2_users == 0) {
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_prev_limit);
+    }
+    cudaGetLastError();
+    H->l2_kappa = false;
+}
 
 void source_updated(cmcg_handle* H) {
     if (H->S32) launch_to_float(2 * H->g.np, H->S, H->S32, H->st);
@@ -1246,7 +1306,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     if (opts) o = *opts;
     if (o.precision < CMCG_FP64 || o.precision > CMCG_MIXED) return CMCG_ERR_INVALID_ARG;
     if (o.flags & ~(CMCG_FLAG_HOST_IO | CMCG_FLAG_TIMING | CMCG_FLAG_INEXACT_RIESZ | CMCG_FLAG_FILTER |
-                    CMCG_FLAG_NO_CG | CMCG_FLAG_FIRST_ORDER))
+                    CMCG_FLAG_NO_CG | CMCG_FLAG_FIRST_ORDER | CMCG_FLAG_L2_KAPPA))
         return CMCG_ERR_INVALID_ARG;
     if ((o.flags & CMCG_FLAG_NO_CG) && o.runup_periods == 0) return CMCG_ERR_INVALID_ARG;
     if ((o.flags & CMCG_FLAG_FIRST_ORDER) &&
@@ -1344,12 +1404,14 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
         }
     }
     if (sync_read(H) != CMCG_OK) return fail(CMCG_ERR_CUDA);
+    if (o.flags & CMCG_FLAG_L2_KAPPA) l2_kappa_begin(H);
     *out = H;
     return CMCG_OK;
 }
 
 int cmcg_destroy(cmcg_handle* h) {
     if (!h) return CMCG_ERR_INVALID_ARG;
+    l2_kappa_end(h);
     if (h->timing)
         for (int e = 0; e < 8; ++e) cudaEventDestroy(h->ev[e]);
     cudaFreeHost(h->hsc);

@@ -65,6 +65,7 @@ struct cmcg_handle {
     // of their buffers; vec32_active is set while such an inner iteration is being enqueued
     bool vec32 = false;
     bool vec32_active = false;
+    bool l2_kappa = false;  // CMCG_FLAG_L2_KAPPA took effect (window set on st, set-aside held)
     // residual history of the last solve: sqrt(gamma_k / gamma_0) per CG iteration, relative to
     // the zero initial guess (hist_scale converts a loop's own relative residual)
     std::vector<double> hist;

@@ -312,6 +312,20 @@ def test_fp64_iterations_and_shift_match_oracle(case):
     assert np.allclose(hist[:k], ref.residual_history[:k], rtol=1e-6, atol=0), name
 
 
+def test_l2_resident_kappa_changes_nothing_but_the_cache():
+    # CMCG_FLAG_L2_KAPPA only sets an L2 access policy on kappa: the same bits, and a handle
+    # created and destroyed with it leaves the next solve unchanged
+    w = wl.sphere_3d(n=24)
+    stream = torch.cuda.Stream()
+    base = solver_of(w, cmcg.MIXED, flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream).solve(w.f, w.g, tol=1e-9)
+    s = solver_of(w, cmcg.MIXED, flags=cmcg.FLAG_INEXACT_RIESZ | cmcg.FLAG_L2_KAPPA, stream=stream)
+    l2 = s.solve(w.f, w.g, tol=1e-9)
+    s.close()
+    after = solver_of(w, cmcg.MIXED, flags=cmcg.FLAG_INEXACT_RIESZ, stream=stream).solve(w.f, w.g, tol=1e-9)
+    assert torch.equal(base[0], l2[0]) and torch.equal(base[0], after[0])
+    assert base[1]["iterations"] == l2[1]["iterations"]
+
+
 @pytest.mark.parametrize("precision,tol", [(cmcg.FP64, 1e-9), (cmcg.MIXED, 1e-9), (cmcg.FP32, 1e-6)])
 def test_graph_replayed_iterations_match_plain_launches(precision, tol):
     # on its own stream a solve replays each flexible-CG iteration as a captured CUDA graph; on
