@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--tile", type=int, nargs=4, default=None, help="cmcg_options.tile (default: autotuned)")
     ap.add_argument("--inner-tol", type=float, default=0.0)
     ap.add_argument("--filter", action="store_true", help="recover U by the fundamental-frequency filter")
+    ap.add_argument("--l2-kappa", action="store_true", help="--profile: keep kappa resident in L2 (CMCG_FLAG_L2_KAPPA)")
     ap.add_argument("--fp64-plain-tol", type=float, default=5e-10,
                     help="tolerance of the plain FP64 comparator (chosen so that its error is about 1e-6)")
     ap.add_argument("--fp64-tuned-tol", type=float, default=1e-10,
@@ -676,6 +677,8 @@ def run_profile(a):
     flags = cmcg.FLAG_FIRST_ORDER if fo else (cmcg.FLAG_INEXACT_RIESZ if a.riesz == "vcycle" else 0)
     if a.filter:
         flags |= cmcg.FLAG_FILTER
+    if a.l2_kappa:
+        flags |= cmcg.FLAG_L2_KAPPA
     s = cmcg.Solver(w.n, w.h, w.c, w.omega, w.faces, mask=w.mask, order=w.order, precision=prec, dt=w.dt_target,
                     max_iter=a.max_iter, flags=flags, runup_periods=a.runup, tile=None if fo else a.tile,
                     inner_tol=a.inner_tol)

@@ -117,7 +117,11 @@ size_t layout(cmcg_handle* H, const Geom& g, const cmcg_options& o, char* base) 
     H->S = c.take<double>(2 * np);
     // FP32 steps read the source in FP32 (GB300 runs FP64 arithmetic at a small fraction of the
     // FP32 rate: an FP64 source term would make a forced FP32 step ALU-bound)
-    H->S32 = o.precision != CMCG_FP64 && !(o.flags & CMCG_FLAG_FIRST_ORDER) ? c.take<float>(2 * np + 4) : nullptr;
+    // (conditions on the options, never on a carved pointer: sizing runs with base == nullptr)
+    const bool f32_copies = o.precision != CMCG_FP64 && !(o.flags & CMCG_FLAG_FIRST_ORDER);
+    H->S32 = f32_copies ? c.take<float>(2 * np + 4) : nullptr;
+    H->mass32 = f32_copies ? c.take<float>(np) : nullptr;
+    H->minv32 = f32_copies ? c.take<float>(np) : nullptr;
     H->scol = g.dim == 3 && !(o.flags & CMCG_FLAG_FIRST_ORDER) ? c.take<unsigned char>((size_t)g.sx * g.sy) : nullptr;
     if (o.flags & CMCG_FLAG_FIRST_ORDER) {
         // first-order state (p, v): CG vectors and the two stepping buffers; no Riesz map
@@ -431,7 +435,7 @@ void fwd_end(cmcg_handle* H, const PeriodBuffers& b, const double* w1, bool src,
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     const double thN = H->omega * H->N * H->dt;
     const int m = fp32_handoff<T>(mode) ? (H->vec32_active ? 3 : 2) : mode;
-    launch_end<T>(g, H->order, m, (const T*)b.cur, (const T*)b.prev, (const T*)b.w0t, w1, kap, H->mass,
+    launch_end<T>(g, H->order, m, (const T*)b.cur, (const T*)b.prev, (const T*)b.w0t, w1, kap, step_mass<T>(H),
                   src ? H->S : nullptr, cos(thN), sin(thN), out0, out1, H->red(), H->dt, zce, H->st);
     H->periods += 1;
 }
@@ -456,14 +460,14 @@ PeriodBuffers adj_begin(cmcg_handle* H, const double* a, const double* bb, int m
     b.w0t = nullptr;
     if constexpr (std::is_same<T, float>::value) {
         if (fp32_handoff<T>(mode)) {  // t = D^-1 z1 came with z0 from the forward end
-            launch_adj_start<float, float>(g, H->order, (const float*)a, (const float*)bb, H->mass, kap,
+            launch_adj_start<float, float>(g, H->order, (const float*)a, (const float*)bb, H->mass32, kap,
                                            (float*)b.cur, (float*)b.prev, H->dt, zce, H->st);
             return b;
         }
     }
     T* t = (T*)H->tmp;
-    launch_adj_prep<T>(g, bb, H->mass, kap, t, zce, H->st);
-    launch_adj_start<T>(g, H->order, a, t, H->mass, kap, (T*)b.cur, (T*)b.prev, H->dt, zce, H->st);
+    launch_adj_prep<T>(g, bb, step_mass<T>(H), kap, t, zce, H->st);
+    launch_adj_start<T>(g, H->order, a, t, step_mass<T>(H), kap, (T*)b.cur, (T*)b.prev, H->dt, zce, H->st);
     return b;
 }
 
@@ -504,7 +508,7 @@ void adj_end(cmcg_handle* H, const PeriodBuffers& b, const double* a, const doub
     const int zce = g.dim == 3 ? kZcEnds : 1;
     const T* kap = std::is_same<T, float>::value ? (const T*)H->kap32 : (const T*)H->kap64;
     const int m = fp32_handoff<T>(mode) ? (H->vec32_active ? 3 : 2) : mode;
-    launch_adj_final<T>(g, H->order, m, (const T*)b.cur, (const T*)b.prev, H->mass, kap, H->minv, a, bb, d0, d1, o0,
+    launch_adj_final<T>(g, H->order, m, (const T*)b.cur, (const T*)b.prev, step_mass<T>(H), kap, H->minv, a, bb, d0, d1, o0,
                         o1, gt1, H->red(), H->dt, zce, H->st);
     H->periods += 1;
 }
@@ -559,7 +563,7 @@ void runup(cmcg_handle* H, int periods, double* w0, double* w1) {
         std::swap(cur, prev);
     }
     const double tN = total * H->dt;
-    launch_end<T>(g, H->order, 1, cur, prev, (const T*)nullptr, nullptr, kap, H->mass, H->S,
+    launch_end<T>(g, H->order, 1, cur, prev, (const T*)nullptr, nullptr, kap, step_mass<T>(H), H->S,
                   ramp(tN, ttr) * cos(H->omega * tN), ramp(tN, ttr) * sin(H->omega * tN), w0, w1, H->red(), H->dt,
                   zce, H->st);
     H->periods += periods;
@@ -687,8 +691,8 @@ void apply_B(cmcg_handle* H, bool first, bool lowp, bool b_ready) {
     }
     vcycle(H, 0);
     if (!H->has_dir) launch_wsum_float(g, H->lv[0].x, red, H->st);
-    launch_fcg_dots(g, H->lv[0].x, H->volume, !H->has_dir, lowp || v32, H->rh0, H->rh1, H->minv, H->gh0, H->gh1, H->r0,
-                    H->r1, red, first, H->st, v32);
+    launch_fcg_dots(g, H->lv[0].x, H->volume, !H->has_dir, lowp || v32, H->rh0, H->rh1,
+                    v32 ? (const double*)H->minv32 : H->minv, H->gh0, H->gh1, H->r0, H->r1, red, first, H->st, v32);
     H->riesz_iters += 1;
 }
 
@@ -1332,7 +1336,12 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     H->st = (cudaStream_t)stream;
     H->omega = omega;
     H->T = 2.0 * kPi / omega;
-    layout(H, H->g, o, (char*)workspace);
+    // carving must take exactly what sizing promised (a layout that depended on a carved
+    // pointer would carve past the caller's workspace)
+    if (layout(H, H->g, o, (char*)workspace) != need) {
+        delete H;
+        return CMCG_ERR_WORKSPACE;
+    }
     H->volume = 1.0;
     for (int a = 0; a < grid->dim; ++a) H->volume *= grid->n[a] * grid->h;
     if (cudaMallocHost((void**)&H->hsc, sizeof(double) * SC_COUNT) != cudaSuccess) {
@@ -1390,6 +1399,10 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     if (!H->has_dir)
         for (int l = 0; l < H->nlev; ++l) H->lv[l].mask = nullptr;
     launch_reciprocal(H->g.np, H->mass, H->minv, H->st);
+    if (H->mass32) {
+        launch_to_float(H->g.np, H->mass, H->mass32, H->st);
+        launch_to_float(H->g.np, H->minv, H->minv32, H->st);
+    }
     H->blk_level = -1;
     for (int l = 0; l < H->nlev; ++l)
         if (H->lv[l].g.np <= mg_block_max_nodes()) {

@@ -45,20 +45,20 @@ void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y
 // (T = float only): mode 2 with w1 pointing to floats (FP32 CG vectors).
 template <typename T>
 void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const T* w0t, const double* w1,
-                const T* kap, const double* mass, const double* S, double cs, double sn, double* out0, double* out1,
+                const T* kap, const T* mass, const double* S, double cs, double sn, double* out0, double* out1,
                 Red red, double dt, int zc, cudaStream_t st);
 template <typename T>
-void launch_adj_prep(const Geom& g, const double* b, const double* mass, const T* kap, T* t, int zc,
+void launch_adj_prep(const Geom& g, const double* b, const T* mass, const T* kap, T* t, int zc,
                      cudaStream_t st);
 // a: double, or (T = float) float for the FP32 hand-off.
 template <typename T, typename A>
-void launch_adj_start(const Geom& g, int order, const A* a, const T* t, const double* mass, const T* kap,
+void launch_adj_start(const Geom& g, int order, const A* a, const T* t, const T* mass, const T* kap,
                       T* cur, T* prev, double dt, int zc, cudaStream_t st);
 // mode 0: gradient (gt1 may be null); mode 1: q; mode 2 (T = float only): mode 0 reading the
 // FP32 hand-off (z0, t) through z0 and z1; mode 3 (T = float only): mode 2 with d0, d1, o0, o1
 // pointing to floats (FP32 CG vectors).
 template <typename T>
-void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass, const T* kap,
+void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const T* mass, const T* kap,
                       const double* minv, const double* z0, const double* z1, const double* d0, const double* d1,
                       double* o0, double* o1, double* gt1, Red red, double dt, int zc, cudaStream_t st);
 // Two leapfrog steps per launch (3D 7-point, FP32, homogeneous): (A = y^{n-1}, B = y^n) ->
@@ -146,7 +146,7 @@ void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double*
 // y += x, x in FP32.
 void launch_add_float(long long n, const float* x, double* y, cudaStream_t st);
 // lowp: FP32 arithmetic with compensated FP32 partial sums (inside an FP32-period solve);
-// f32vec: rh, gh, z point to floats (implies lowp).
+// f32vec: rh, gh, z and minv point to floats (implies lowp).
 void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_mean, bool lowp, const double* rh0,
                      const double* rh1, const double* minv, const double* gh0, const double* gh1, double* z0,
                      double* z1, Red red, bool first, cudaStream_t st, bool f32vec = false);

@@ -328,7 +328,7 @@ __global__ void k_add_float(long long n, const float* __restrict__ x, double* __
 template <typename V>
 __global__ void __launch_bounds__(kT) k_fcg_dots(Geom g, const float* __restrict__ zf, double inv_volume,
                                                  int remove_mean, const V* __restrict__ rh0,
-                                                 const V* __restrict__ rh1, const double* __restrict__ minv,
+                                                 const V* __restrict__ rh1, const V* __restrict__ minv,
                                                  const V* __restrict__ gh0, const V* __restrict__ gh1,
                                                  V* __restrict__ z0, V* __restrict__ z1, Red red,
                                                  int first, int lowp) {
@@ -527,7 +527,8 @@ void launch_fcg_dots(const Geom& g, const float* zf, double volume, bool remove_
     note_launch(1);
     if (f32vec)
         k_fcg_dots<float><<<fcg_dots_blocks<float>(g.np), kT, 0, st>>>(
-            g, zf, 1.0 / volume, remove_mean ? 1 : 0, (const float*)rh0, (const float*)rh1, minv, (const float*)gh0,
+            g, zf, 1.0 / volume, remove_mean ? 1 : 0, (const float*)rh0, (const float*)rh1, (const float*)minv,
+            (const float*)gh0,
             (const float*)gh1, (float*)z0, (float*)z1, red, first ? 1 : 0, 1);
     else
         k_fcg_dots<double><<<fcg_dots_blocks<double>(g.np), kT, 0, st>>>(

@@ -33,6 +33,7 @@ struct cmcg_handle {
     double *kap64 = nullptr, *mass = nullptr, *minv = nullptr, *S = nullptr;
     float* kap32 = nullptr;
     float* S32 = nullptr;  // FP32 copy of S, the source of FP32 leapfrog steps (FP32 / mixed)
+    float *mass32 = nullptr, *minv32 = nullptr;  // FP32 copies of M and M^-1 (FP32 / mixed)
     unsigned char* scol = nullptr;  // 3D: columns with source inside the grid (launch_source_columns)
     unsigned char* mask = nullptr;
     // wave buffers (sized for double; FP32 stepping uses the first half) + FP64 temp
@@ -99,6 +100,12 @@ struct PeriodBuffers {
 int cuda_status();
 // After every change of S: refresh its FP32 copy (FP32 and mixed-precision handles).
 void source_updated(cmcg_handle* H);
+// The lumped mass M in precision T (what the period kernels of that precision read).
+template <typename T>
+const T* step_mass(const cmcg_handle* H) {
+    if constexpr (std::is_same<T, float>::value) return H->mass32;
+    else return H->mass;
+}
 // The source array of leapfrog steps in precision T.
 template <typename T>
 const T* step_source(const cmcg_handle* H) {

@@ -573,7 +573,8 @@ __global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, c
         // stores: a branch on kappa would put its load's latency before all the others
         const T k = kap[j];
         const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
-        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+        const int nbf = num_abc(g, m.ix, m.iy, iz);
+        const T beta = nbf ? (T)nbf * sqrt(k) : T(0);
         const T w0j = w0t[j];
         T v = w0j + dtT * (T(1) - beta) * (T)w1[j] - T(0.5) * k * L;
         if (SRC) v += (T)(0.5 * S[2 * j]);
@@ -597,7 +598,7 @@ constexpr int kEndMinBlocks = std::is_same<T, float>::value ? 5 : 1;
 template <typename T, int ORDER, bool SRC, int MODE, typename V = double>
 __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __restrict__ yN, const T* __restrict__ yNm1,
                                                   const T* __restrict__ w0t, const V* __restrict__ w1,
-                                                  const T* __restrict__ kap, const double* __restrict__ mass,
+                                                  const T* __restrict__ kap, const T* __restrict__ mass,
                                                   const double* __restrict__ S, double cs, double sn,
                                                   double* __restrict__ out0, double* __restrict__ out1,
                                                   Red red, Geom g, double dt, int zc) {
@@ -614,7 +615,8 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __r
             const T k = kap[j];  // Dirichlet (kappa = 0) only selects the stores (see k_start)
             const bool dir = k == T(0);
             const T L = lap_t<ORDER, T>(g, fy, j, m.ix, m.iy, iz);
-            const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+            const int nbf = num_abc(g, m.ix, m.iy, iz);
+        const T beta = nbf ? (T)nbf * sqrt(k) : T(0);
             T src = T(0);
             if (SRC) src = (T)(S[2 * j] * cs + S[2 * j + 1] * sn);
             const T yn = yN[j];
@@ -650,14 +652,15 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __r
 
 // Adjoint start, part 1: t = D^-1 b = b / (M (1 + beta)).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_adj_prep(const double* __restrict__ b, const double* __restrict__ mass,
+__global__ void __launch_bounds__(kThreads) k_adj_prep(const double* __restrict__ b, const T* __restrict__ mass,
                                                        const T* __restrict__ kap, T* __restrict__ t, Geom g, int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid) return;
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
         const T k = kap[j];  // Dirichlet (kappa = 0) only selects the store (see k_start)
-        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+        const int nbf = num_abc(g, m.ix, m.iy, iz);
+        const T beta = nbf ? (T)nbf * sqrt(k) : T(0);
         const T v = (T)b[j] / ((T)mass[j] * (T(1) + beta));  // 0/0 on Dirichlet nodes: not stored
         t[j] = k == T(0) ? T(0) : v;
     }
@@ -667,18 +670,21 @@ __global__ void __launch_bounds__(kThreads) k_adj_prep(const double* __restrict_
 //   ybar_N = a + M t / dt - (dt/2) K t,  u_{N-1} = D^-1 ybar_N,  prev = C u_N / M = t / dt.
 template <typename T, int ORDER, typename A>
 __global__ void __launch_bounds__(kThreads) k_adj_start(const A* __restrict__ a, const T* __restrict__ t,
-                                                        const double* __restrict__ mass, const T* __restrict__ kap,
+                                                        const T* __restrict__ mass, const T* __restrict__ kap,
                                                         T* __restrict__ cur, T* __restrict__ prev, Geom g, double dt,
                                                         int zc) {
     const PlaneMap m = plane_map(g, zc);
     if (!m.valid) return;
     Ld<T> f{t};
     const T dtT = (T)dt;
+    const bool p7 = ORDER == 2 && g.dim == 3;  // column offsets computed once
+    const auto pt = plane_lap<T>(g, f, m.ix, m.iy);
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
         const T k = kap[j];  // Dirichlet (kappa = 0) only selects the stores (see k_start)
-        const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
-        const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+        const T L = p7 ? pt.lap(j, iz) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+        const int nbf = num_abc(g, m.ix, m.iy, iz);
+        const T beta = nbf ? (T)nbf * sqrt(k) : T(0);
         const T tj = t[j];
         const T u = ((T)a[j] / (T)mass[j] + tj / dtT - k * L / (T(2) * dtT)) / (T(1) + beta);  // 0/0 at Dirichlet
         const bool dir = k == T(0);
@@ -695,7 +701,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_start(const A* __restrict__ a,
 // z1 = M (1 + beta) t from t in z1.
 template <typename T, int ORDER, int MODE, typename V = double>
 __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_adj_final(const T* __restrict__ s, const T* __restrict__ u1,
-                                                        const double* __restrict__ mass, const T* __restrict__ kap,
+                                                        const T* __restrict__ mass, const T* __restrict__ kap,
                                                         const double* __restrict__ minv,
                                                         const double* __restrict__ z0, const double* __restrict__ z1,
                                                         const V* __restrict__ d0, const V* __restrict__ d1,
@@ -716,7 +722,8 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_adj_final(const 
             const T k = kap[j];  // Dirichlet (kappa = 0) only selects the stores (see k_start)
             const bool dir = k == T(0);
             const T L = col ? cl.lap(j) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
-            const T beta = (T)num_abc(g, m.ix, m.iy, iz) * sqrt(k);
+            const int nbf = num_abc(g, m.ix, m.iy, iz);
+        const T beta = nbf ? (T)nbf * sqrt(k) : T(0);
             const T W = weight_t<T>(g, m.ix, m.iy, iz);
             const T M = (T)mass[j];
             const T sj = s[j];
@@ -1166,7 +1173,7 @@ void launch_start(const Geom& g, int order, const T* w0t, const double* w1, T* y
 
 template <typename T>
 void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, const T* w0t, const double* w1,
-                const T* kap, const double* mass, const double* S, double cs, double sn, double* out0, double* out1,
+                const T* kap, const T* mass, const double* S, double cs, double sn, double* out0, double* out1,
                 Red red, double dt, int zc, cudaStream_t st) {
     note_launch(1);
     const dim3 grid = plane_grid(g, zc);
@@ -1202,14 +1209,14 @@ void launch_end(const Geom& g, int order, int mode, const T* yN, const T* yNm1, 
 }
 
 template <typename T>
-void launch_adj_prep(const Geom& g, const double* b, const double* mass, const T* kap, T* t, int zc,
+void launch_adj_prep(const Geom& g, const double* b, const T* mass, const T* kap, T* t, int zc,
                      cudaStream_t st) {
     note_launch(1);
     k_adj_prep<T><<<plane_grid(g, zc), kThreads, 0, st>>>(b, mass, kap, t, g, zc);
 }
 
 template <typename T, typename A>
-void launch_adj_start(const Geom& g, int order, const A* a, const T* t, const double* mass, const T* kap,
+void launch_adj_start(const Geom& g, int order, const A* a, const T* t, const T* mass, const T* kap,
                       T* cur, T* prev, double dt, int zc, cudaStream_t st) {
     note_launch(1);
     if (order == 2)
@@ -1219,7 +1226,7 @@ void launch_adj_start(const Geom& g, int order, const A* a, const T* t, const do
 }
 
 template <typename T>
-void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const double* mass, const T* kap,
+void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const T* mass, const T* kap,
                       const double* minv, const double* z0, const double* z1, const double* d0, const double* d1,
                       double* o0, double* o1, double* gt1, Red red, double dt, int zc, cudaStream_t st) {
     note_launch(1);
@@ -1268,18 +1275,18 @@ long long plane_blocks(const Geom& g, int zc) {
     template void launch_start<T>(const Geom&, int, const T*, const double*, T*, T*, const T*, const double*,   \
                                   double, int, cudaStream_t, bool);                                            \
     template void launch_end<T>(const Geom&, int, int, const T*, const T*, const T*, const double*, const T*,   \
-                                const double*, const double*, double, double, double*, double*, Red, double,    \
+                                const T*, const double*, double, double, double*, double*, Red, double,         \
                                 int, cudaStream_t);                                                            \
-    template void launch_adj_prep<T>(const Geom&, const double*, const double*, const T*, T*, int, cudaStream_t); \
-    template void launch_adj_start<T, double>(const Geom&, int, const double*, const T*, const double*, const T*, \
+    template void launch_adj_prep<T>(const Geom&, const double*, const T*, const T*, T*, int, cudaStream_t);    \
+    template void launch_adj_start<T, double>(const Geom&, int, const double*, const T*, const T*, const T*,    \
                                               T*, T*, double, int, cudaStream_t);                               \
-    template void launch_adj_final<T>(const Geom&, int, int, const T*, const T*, const double*, const T*,       \
+    template void launch_adj_final<T>(const Geom&, int, int, const T*, const T*, const T*, const T*,           \
                                       const double*, const double*, const double*, const double*, const double*, \
                                       double*, double*, double*, Red, double, int, cudaStream_t);
 CMCG_INST(float)
 CMCG_INST(double)
 #undef CMCG_INST
-template void launch_adj_start<float, float>(const Geom&, int, const float*, const float*, const double*,
+template void launch_adj_start<float, float>(const Geom&, int, const float*, const float*, const float*,
                                              const float*, float*, float*, double, int, cudaStream_t);
 
 }  // namespace cmcg
