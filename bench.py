@@ -599,11 +599,14 @@ def run_ours(args):
         bc = cmcg.BC()
         for f in range(6):
             bc.face[f] = int(w.faces[f])
-        st_stream = torch.cuda.current_stream(dev)
+        # a created stream, as a C-ABI caller would pass: CG iterations replay as CUDA graphs and
+        # the L2 window applies (neither is available on the legacy default stream)
+        st_stream = torch.cuda.Stream(dev)
 
         def e2e_step():
-            c_dev.copy_(c_host, non_blocking=True)
-            m_dev.copy_(m_host, non_blocking=True)
+            with torch.cuda.stream(st_stream):
+                c_dev.copy_(c_host, non_blocking=True)
+                m_dev.copy_(m_host, non_blocking=True)
             bc.dirichlet_mask = m_dev.data_ptr()
             h = cmcg.cmcg_create(grid, c_dev, w.omega, bc, opts, ws_t, st_stream.cuda_stream)
             st = cmcg.Stats()
@@ -622,8 +625,8 @@ def run_ours(args):
         h2d = c_host.numel() * 8 + m_host.numel() + g_host.numel() * 16
         e2e = {"value": e2e_updates / e_el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(w.num_nodes * 16),
-               "note": "per step: H2D of c, mask, g from pinned memory; cmcg_create; cmcg_solve_host "
-                       "(D2H of U inside); cmcg_destroy"}
+               "note": "per step, on a created stream: H2D of c, mask, g from pinned memory; cmcg_create; "
+                       "cmcg_solve_host (D2H of U inside); cmcg_destroy"}
 
     if rank != 0:
         if ws > 1:
