@@ -136,35 +136,6 @@ __device__ __forceinline__ ColumnLap7<T, F> column_lap(const Geom& g, F f, int i
     return c;
 }
 
-// Unscaled 7-point Laplacian of f at node j of a thread's column, with the column's mirror
-// offsets computed once (the z-neighbours are loaded, not carried: no registers held across
-// planes).  Same sum, in the same order, as lap_t<2> in 3D, so the results are bitwise equal.
-template <typename T, typename F>
-struct PlaneLap7 {
-    F f;
-    long long sZ, oxm, oxp, oym, oyp;
-    int nz;
-    __device__ __forceinline__ T lap(long long j, int iz) const {
-        T acc = f(j + oxm) + f(j + oxp);
-        acc += f(j + oym) + f(j + oyp);
-        acc += f(j + (iz > 0 ? -sZ : sZ)) + f(j + (iz < nz ? sZ : -sZ));
-        return T(6) * f(j) - acc;
-    }
-};
-
-template <typename T, typename F>
-__device__ __forceinline__ PlaneLap7<T, F> plane_lap(const Geom& g, F f, int ix, int iy) {
-    PlaneLap7<T, F> c;
-    c.f = f;
-    c.sZ = (long long)g.sx * g.sy;
-    c.oxm = off_m1(ix, 1);
-    c.oxp = off_p1(ix, g.nx, 1);
-    c.oym = off_m1(iy, g.sx);
-    c.oyp = off_p1(iy, g.ny, g.sx);
-    c.nz = g.nz;
-    return c;
-}
-
 // ---- deterministic block reductions -------------------------------------------------
 // Each block reduces NV doubles; thread 0 stores them in partials[k * gridDim.x + block].
 // The last block to finish (atomic ticket) sums the partials in a fixed order and writes

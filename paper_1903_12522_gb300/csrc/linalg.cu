@@ -315,6 +315,64 @@ __global__ void __launch_bounds__(kT) k_fcg_update(long long n, V* __restrict__ 
     }
 }
 
+// FP32 CG vectors, four nodes per thread and loop trip (float4 loads and stores; the vectors
+// start 256-byte aligned); the last n % 4 nodes take the scalar loop.  Same arithmetic per
+// node as the scalar kernels.
+__global__ void __launch_bounds__(kT) k_fcg_update_f4(long long n, float* __restrict__ w0, float* __restrict__ w1,
+                                                      float* __restrict__ rh0, float* __restrict__ rh1,
+                                                      const float* __restrict__ d0, const float* __restrict__ d1,
+                                                      const float* __restrict__ gh0, const float* __restrict__ gh1,
+                                                      float* __restrict__ bf, double* __restrict__ sc) {
+    const float alpha = (float)(sc[SC_GAMMA] / sc[SC_GD]);
+    const long long n4 = n >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long q = t0; q < n4; q += stride) {
+        float4 a = reinterpret_cast<float4*>(w0)[q], b = reinterpret_cast<float4*>(w1)[q];
+        const float4 e = reinterpret_cast<const float4*>(d0)[q], f = reinterpret_cast<const float4*>(d1)[q];
+        float4 r = reinterpret_cast<float4*>(rh0)[q], u = reinterpret_cast<float4*>(rh1)[q];
+        const float4 g = reinterpret_cast<const float4*>(gh0)[q], h = reinterpret_cast<const float4*>(gh1)[q];
+        a.x -= alpha * e.x, a.y -= alpha * e.y, a.z -= alpha * e.z, a.w -= alpha * e.w;
+        b.x -= alpha * f.x, b.y -= alpha * f.y, b.z -= alpha * f.z, b.w -= alpha * f.w;
+        r.x = r.x - alpha * g.x, r.y = r.y - alpha * g.y, r.z = r.z - alpha * g.z, r.w = r.w - alpha * g.w;
+        u.x -= alpha * h.x, u.y -= alpha * h.y, u.z -= alpha * h.z, u.w -= alpha * h.w;
+        reinterpret_cast<float4*>(w0)[q] = a;
+        reinterpret_cast<float4*>(w1)[q] = b;
+        reinterpret_cast<float4*>(rh0)[q] = r;
+        reinterpret_cast<float4*>(rh1)[q] = u;
+        if (bf) reinterpret_cast<float4*>(bf)[q] = r;
+    }
+    for (long long j = 4 * n4 + t0; j < n; j += stride) {
+        w0[j] -= alpha * d0[j];
+        w1[j] -= alpha * d1[j];
+        const float r = rh0[j] - alpha * gh0[j];
+        rh0[j] = r;
+        rh1[j] -= alpha * gh1[j];
+        if (bf) bf[j] = r;
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_cg_direction_f4(long long n, const float* __restrict__ r0,
+                                                        const float* __restrict__ r1, float* __restrict__ d0,
+                                                        float* __restrict__ d1, const double* __restrict__ sc) {
+    const float beta = (float)sc[SC_BETA];
+    const long long n4 = n >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long q = t0; q < n4; q += stride) {
+        const float4 a = reinterpret_cast<const float4*>(r0)[q], b = reinterpret_cast<const float4*>(r1)[q];
+        float4 c = reinterpret_cast<float4*>(d0)[q], d = reinterpret_cast<float4*>(d1)[q];
+        c.x = a.x + beta * c.x, c.y = a.y + beta * c.y, c.z = a.z + beta * c.z, c.w = a.w + beta * c.w;
+        d.x = b.x + beta * d.x, d.y = b.y + beta * d.y, d.z = b.z + beta * d.z, d.w = b.w + beta * d.w;
+        reinterpret_cast<float4*>(d0)[q] = c;
+        reinterpret_cast<float4*>(d1)[q] = d;
+    }
+    for (long long j = 4 * n4 + t0; j < n; j += stride) {
+        d0[j] = r0[j] + beta * d0[j];
+        d1[j] = r1[j] + beta * d1[j];
+    }
+}
+
 // y += x with x in FP32 (the inner correction of mixed precision added to the FP64 iterate).
 __global__ void k_add_float(long long n, const float* __restrict__ x, double* __restrict__ y) {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -437,7 +495,10 @@ void launch_cg_update(long long n, double* w0, double* w1, double* r0, double* r
 void launch_cg_direction(long long n, const double* r0, const double* r1, double* d0, double* d1, Red red,
                          cudaStream_t st, float* d0f, bool f32vec) {
     note_launch(1);
-    if (f32vec)
+    if (f32vec && !d0f)
+        k_cg_direction_f4<<<vec_blocks((n + 3) / 4), kT, 0, st>>>(n, (const float*)r0, (const float*)r1, (float*)d0,
+                                                                  (float*)d1, red.sc);
+    else if (f32vec)
         k_cg_direction<float><<<vec_blocks(n), kT, 0, st>>>(n, (const float*)r0, (const float*)r1, (float*)d0,
                                                             (float*)d1, d0f, red.sc);
     else
@@ -486,9 +547,9 @@ void launch_fcg_update(long long n, double* w0, double* w1, double* rh0, double*
                        bool f32vec) {
     note_launch(1);
     if (f32vec)
-        k_fcg_update<float><<<vec_blocks(n), kT, 0, st>>>(n, (float*)w0, (float*)w1, (float*)rh0, (float*)rh1,
-                                                          (const float*)d0, (const float*)d1, (const float*)gh0,
-                                                          (const float*)gh1, bf, red.sc);
+        k_fcg_update_f4<<<vec_blocks((n + 3) / 4), kT, 0, st>>>(n, (float*)w0, (float*)w1, (float*)rh0, (float*)rh1,
+                                                                (const float*)d0, (const float*)d1, (const float*)gh0,
+                                                                (const float*)gh1, bf, red.sc);
     else
         k_fcg_update<double><<<vec_blocks(n), kT, 0, st>>>(n, w0, w1, rh0, rh1, d0, d1, gh0, gh1, bf, red.sc);
 }

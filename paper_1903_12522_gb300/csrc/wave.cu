@@ -677,12 +677,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_start(const A* __restrict__ a,
     if (!m.valid) return;
     Ld<T> f{t};
     const T dtT = (T)dt;
-    const bool p7 = ORDER == 2 && g.dim == 3;  // column offsets computed once
-    const auto pt = plane_lap<T>(g, f, m.ix, m.iy);
     for (int iz = m.z0; iz < m.z1; ++iz) {
         const long long j = node(g, m.ix, m.iy, iz);
         const T k = kap[j];  // Dirichlet (kappa = 0) only selects the stores (see k_start)
-        const T L = p7 ? pt.lap(j, iz) : lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
+        const T L = lap_t<ORDER, T>(g, f, j, m.ix, m.iy, iz);
         const int nbf = num_abc(g, m.ix, m.iy, iz);
         const T beta = nbf ? (T)nbf * sqrt(k) : T(0);
         const T tj = t[j];
