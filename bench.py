@@ -227,8 +227,8 @@ def kernel_traffic(profile, kernel_src_hash):
 
 
 def kernel_src_hash(name="k_step3d7("):
-    """Hash of a kernel's source text in wave.cu (the kernel that ncu counters describe)."""
-    fname = "step_bulk.cu" if "bulk" in name else "wave.cu"
+    """Hash of a kernel's source text (the kernel that ncu counters describe)."""
+    fname = "step_bulk.cu" if "bulk" in name else ("step_pair.cu" if "pair" in name else "wave.cu")
     src = open(os.path.join(ROOT, "paper_1903_12522_gb300", "csrc", fname)).read()
     start = src.index(name)
     end = src.index("\n}\n", start) + 2  # the kernel's closing brace
@@ -554,9 +554,10 @@ def run_ours(args):
     pairs = s.opts.tile[3] == 2
     tile_cfg = tile_config(s)
     if n32 > 0 and pairs:
-        # FP32 3D 7-point periods run their homogeneous steps in pairs (k_step3d7_x2)
+        # FP32 3D 7-point periods run their homogeneous steps in pairs (k_step3d7_pair)
         per_launch, bpl, upl = s32 / n32, PAIR_BYTES_FP32, 2
-        name, prof, src = "k_step3d7_x2: two FP32 leapfrog steps, 3D 7-point", "step3d7x2_fp32_sphere.json", "k_step3d7_x2("
+        name, prof, src = ("k_step3d7_pair: two FP32 leapfrog steps, 3D 7-point", "step3d7pair_fp32_sphere.json",
+                           "k_step3d7_pair(")
     elif n32 > 0 and s.opts.tile[3] == 4:
         per_launch, bpl, upl = s32 / n32, STEP_BYTES_FP32, 1
         name, prof, src = ("k_step3d7_bulk<float>: FP32 leapfrog step, 3D 7-point, operands staged by bulk copies",

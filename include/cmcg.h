@@ -160,9 +160,10 @@ typedef struct {
                                launch): 0 = the default, scheme 3 on 3D 7-point grids and
                                scheme 5 on 2D 5-point grids (the fastest measured); 1 = one
                                step per launch, [0] z-planes per thread
-                               (16); 2 = two FP32 steps per launch (temporal blocking), [1]
-                               z-planes per block (24), [2] maximum interior tile height (16, at
-                               most 16); 3 = one step per launch with [2] = 2 (default) or 4
+                               (16); 2 = two FP32 steps per launch (temporal blocking), [0]
+                               planes staged ahead (1..3, 0 = 2), [1] z-planes per block
+                               (0 = 16), [2] interior tile height (0 = the fewest tiles, at
+                               most 60); 3 = one step per launch with [2] = 2 (default) or 4
                                z-planes per loop iteration, [0] z-planes per thread; 4 = FP32
                                steps with operands staged by TMA bulk copies, [0] z-planes per
                                CTA and [1] rows per band (0 = automatic); 5 = FP32 steps in

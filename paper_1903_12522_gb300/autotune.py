@@ -30,15 +30,15 @@ CACHE = os.path.join(HERE, "autotune_cache.json")
 def candidates_3d():
     """cmcg_options.tile candidates on 3D 7-point grids: scheme 1 (one z-plane per loop trip)
     and 3 (two, or four with tile[2] = 4), tile[0] = z-planes per thread; scheme 2 (two steps
-    per launch: temporal-blocking depth 2), tile[1] = z-planes per block and tile[2] = tile
-    height; scheme 4 (bulk-copy staging), tile[0] = planes per CTA and tile[1] = band rows (0 =
+    per launch: temporal-blocking depth 2), tile[0] = planes staged ahead, tile[1] = z-planes
+    per block and tile[2] = tile height; scheme 4 (bulk-copy staging), tile[0] = planes per CTA and tile[1] = band rows (0 =
     automatic); scheme 5 (one float4 of the flat index per thread); scheme 6 (staged by
     asynchronous copies), tile[1] = band rows, tile[2] = planes in flight."""
     out = []
     for scheme in (1, 3):
         out += [(zc, 0, 0, scheme) for zc in (8, 16, 32)]
     out += [(zc, 0, 4, 3) for zc in (8, 16, 32)]  # scheme 3 with four planes per loop iteration
-    out += [(16, 12, 16, 2), (16, 24, 16, 2)]
+    out += [(2, 16, 0, 2), (3, 16, 0, 2), (2, 32, 0, 2)]  # scheme 2: planes staged ahead, z-planes per block
     out += [(zc, ty, 0, 4) for zc in (0, 16, 32, 64) for ty in (0, 4, 8)]
     out += [(0, 0, 0, 5)]
     out += [(0, ty, depth, 6) for ty in (0, 1, 2, 3, 4) for depth in (2, 3)]

@@ -387,8 +387,7 @@ void plain_steps(cmcg_handle* H, PeriodBuffers& b, int count) {
         const int tp = timing_begin(H, true, count / 2);
         while (count >= 2) {
             launch_step2(g, (const float*)b.prev, (const float*)b.cur, (const float*)kap, spare[0], spare[1],
-                         H->opt.tile[1] > 0 ? H->opt.tile[1] : kZcStep2, H->opt.tile[2] > 0 ? H->opt.tile[2] : 16,
-                         H->st);
+                         H->opt.tile[1], H->opt.tile[2], H->opt.tile[0], H->st);
             float* old_prev = (float*)b.prev;
             float* old_cur = (float*)b.cur;
             b.prev = spare[0];
@@ -1379,7 +1378,7 @@ int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg
     if (H->has_dir && H->order == 4) return fail(CMCG_ERR_UNSUPPORTED);
     if (H->has_dir && H->sumW <= 0) return fail(CMCG_ERR_INVALID_ARG);
     if (o.runup_periods < -64 || o.runup_periods > 100000) return fail(CMCG_ERR_INVALID_ARG);
-    if (o.tile[0] < 0 || o.tile[0] > 512 || o.tile[1] < 0 || o.tile[1] > 512 || o.tile[2] < 0 || o.tile[2] > 16 ||
+    if (o.tile[0] < 0 || o.tile[0] > 512 || o.tile[1] < 0 || o.tile[1] > 512 || o.tile[2] < 0 || o.tile[2] > 60 ||
         o.tile[3] < 0 || o.tile[3] > 6)
         return fail(CMCG_ERR_INVALID_ARG);
     // time step: N = ceil(T / dt_target - 1e-9), dt = T / N

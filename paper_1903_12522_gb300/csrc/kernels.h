@@ -61,11 +61,13 @@ template <typename T>
 void launch_adj_final(const Geom& g, int order, int mode, const T* s, const T* u1, const T* mass, const T* kap,
                       const double* minv, const double* z0, const double* z1, const double* d0, const double* d1,
                       double* o0, double* o1, double* gt1, Red red, double dt, int zc, cudaStream_t st);
-// Two leapfrog steps per launch (3D 7-point, FP32, homogeneous): (A = y^{n-1}, B = y^n) ->
-// (C = y^{n+1}, D = y^{n+2}); the four buffers must be distinct.
+// Two leapfrog steps per launch (step_pair.cu; 3D 7-point, FP32, homogeneous): (A = y^{n-1},
+// B = y^n) -> (C = y^{n+1}, D = y^{n+2}); the four buffers must be distinct.  zc: z-planes per
+// block (0: 16); ty: interior tile height (0: fewest tiles); depth: planes staged ahead (1..3,
+// 0: 2).
 bool step2_supported(const Geom& g, int order);
 void launch_step2(const Geom& g, const float* A, const float* B, const float* kap, float* C, float* D, int zc,
-                  int ty_max, cudaStream_t st);
+                  int ty, int depth, cudaStream_t st);
 
 // Batched persistent step loop (wave.cu): one cooperative launch runs the FP32 step loops of
 // many solves.  offset = prefix sum of blocks over the preceding items.

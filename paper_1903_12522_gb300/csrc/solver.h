@@ -14,7 +14,6 @@ namespace cmcg {
 constexpr int kMaxLevels = 16;
 constexpr int kZcStep3D = 16;  // z-planes per thread in the leapfrog step (3D)
 constexpr int kZcEnds = 8;     // z-planes per thread in the period endpoint kernels
-constexpr int kZcStep2 = 24;   // z-planes per block in the two-step kernel
 constexpr double kPi = 3.14159265358979323846;
 }  // namespace cmcg
 

@@ -806,153 +806,6 @@ __global__ void __launch_bounds__(kThreads) k_make_source(const double* __restri
 }
 
 // ---------------------------------------------------------------------------------------
-// Two leapfrog steps per sweep (temporal blocking), 3D 7-point, FP32, homogeneous steps.
-// A block owns an interior tile TX x TY of every plane in its z-chunk and marches z.  Shared
-// memory holds 4-plane rings of y^n over the tile plus a 2-node halo (mirror-filled at the
-// faces) and of y^{n+1} over the tile plus a 1-node halo (computed redundantly at the halo, with
-// the mirrored node's coefficients, so that it equals the mirror value there).  Iteration k:
-//   phase A: load y^n(k+1);  y^{n+2}(k-2) on the interior (from y^{n+1}(k-3..k-1), y^n(k-2))
-//   phase B: y^{n+1}(k) on the 1-halo region (from y^n(k-1..k+1), y^{n-1}(k))
-// with one block barrier after each phase.  y^{n-1} and kappa are read where needed.  Outputs
-// go to two other buffers (y^{n+1} -> C, y^{n+2} -> D): other blocks still read the inputs'
-// halos.  Each output equals two applications of the one-step update.
-constexpr int kTbThreads = 256;
-constexpr int kTbMaxW = 68, kTbMaxH = 20;  // interior tile <= 64 x 16
-constexpr int kTbR2 = (kTbMaxW * kTbMaxH + kTbThreads - 1) / kTbThreads;
-constexpr int kTbR1 = ((kTbMaxW - 2) * (kTbMaxH - 2) + kTbThreads - 1) / kTbThreads;
-constexpr int kTbR0 = ((kTbMaxW - 4) * (kTbMaxH - 4) + kTbThreads - 1) / kTbThreads;
-
-__device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
-__device__ __forceinline__ int ring4(int p) { return p & 3; }  // two's complement: also for p < 0
-
-__device__ __forceinline__ int nb_xy(const Geom& g, int px, int py) {
-    return ((px == 0) & (int)(g.abc & 1u)) + ((px == g.nx) & (int)((g.abc >> 1) & 1u)) +
-           ((py == 0) & (int)((g.abc >> 2) & 1u)) + ((py == g.ny) & (int)((g.abc >> 3) & 1u));
-}
-
-__device__ __forceinline__ float lf_update(float yc, float lap, float kk, float yp, int nb) {
-    const float rhs = 2.f * yc - kk * lap;
-    if (nb == 0) return rhs - yp;
-    const float beta = (float)nb * sqrtf(kk);
-    return (rhs - (1.f - beta) * yp) / (1.f + beta);
-}
-
-__global__ void __launch_bounds__(kTbThreads) k_step3d7_x2(const float* __restrict__ A, const float* __restrict__ B,
-                                                           const float* __restrict__ kap, float* __restrict__ Cout,
-                                                           float* __restrict__ Dout, Geom g, int TX, int TY, int zc) {
-    extern __shared__ float sm[];
-    const int W2 = TX + 4, H2 = TY + 4, W1 = TX + 2, H1 = TY + 2;
-    const int P2 = W2 * H2, P1 = W1 * H1;
-    float* Y = sm;           // 4 x P2
-    float* L = sm + 4 * P2;  // 4 x P1
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.sz);
-    const long long sxy = (long long)g.sx * g.sy;
-    const int tid = threadIdx.x;
-    // per-thread point lists, the same every plane
-    int ph2[kTbR2];                   // R2 (loads): physical (x, y) offset, -1 = none
-    int pk1[kTbR1], ph1[kTbR1];       // R1: Y position | nb << 16 | interior << 19; physical offset
-    int pk0[kTbR0], ph0[kTbR0];       // R0: L position | Y position << 11 | nb << 22; physical offset
-#pragma unroll
-    for (int r = 0; r < kTbR2; ++r) {
-        const int i = tid + r * kTbThreads;
-        ph2[r] = -1;
-        if (i < P2) {
-            const int ly = i / W2, lx = i - ly * W2;
-            const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
-            if (gx <= g.nx + 2 && gy <= g.ny + 2) ph2[r] = mirror(gx, g.nx) + g.sx * mirror(gy, g.ny);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < kTbR1; ++r) {
-        const int i = tid + r * kTbThreads;
-        pk1[r] = -1;
-        if (i < P1) {
-            const int ly = i / W1, lx = i - ly * W1;
-            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-            if (gx <= g.nx + 1 && gy <= g.ny + 1) {
-                const int px = mirror(gx, g.nx), py = mirror(gy, g.ny);
-                const int inner = (lx >= 1 && ly >= 1 && lx <= TX && ly <= TY && gx <= g.nx && gy <= g.ny) ? 1 : 0;
-                pk1[r] = ((lx + 1) + W2 * (ly + 1)) | (nb_xy(g, px, py) << 16) | (inner << 19);
-                ph1[r] = px + g.sx * py;
-            }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < kTbR0; ++r) {
-        const int i = tid + r * kTbThreads;
-        pk0[r] = -1;
-        if (i < TX * TY) {
-            const int ly = i / TX, lx = i - ly * TX;
-            const int gx = x0 + lx, gy = y0 + ly;
-            if (gx <= g.nx && gy <= g.ny) {
-                pk0[r] = ((lx + 1) + W1 * (ly + 1)) | (((lx + 2) + W2 * (ly + 2)) << 11) | (nb_xy(g, gx, gy) << 22);
-                ph0[r] = gx + g.sx * gy;
-            }
-        }
-    }
-    const int zabc0 = (int)((g.abc >> 4) & 1u), zabc1 = (int)((g.abc >> 5) & 1u);
-    auto load_plane = [&](int p) {  // y^n at virtual plane p (mirrored) into the ring
-        float* dst = Y + ring4(p) * P2;
-        const long long base = (long long)mirror(p, g.nz) * sxy;
-#pragma unroll
-        for (int r = 0; r < kTbR2; ++r) {
-            const int i = tid + r * kTbThreads;
-            if (ph2[r] >= 0) dst[i] = B[base + ph2[r]];
-        }
-    };
-    load_plane(z0 - 2);
-    load_plane(z0 - 1);
-    for (int k = z0 - 1; k <= z1 + 1; ++k) {
-        // phase A: next y^n plane; y^{n+2} two planes behind
-        if (k <= g.nz) load_plane(k + 1);
-        const int q = k - 2;
-        if (q >= z0 && q < z1) {
-            const float* Lm = L + ring4(mirror(q - 1, g.nz)) * P1;
-            const float* Lc = L + ring4(q) * P1;
-            const float* Lp = L + ring4(mirror(q + 1, g.nz)) * P1;
-            const float* Yq = Y + ring4(q) * P2;
-            const long long base = (long long)q * sxy;
-            const int nbz = ((q == 0) & zabc0) + ((q == g.nz) & zabc1);
-#pragma unroll
-            for (int r = 0; r < kTbR0; ++r) {
-                const int pk = pk0[r];
-                if (pk < 0) continue;
-                const int c = pk & 2047, cy = (pk >> 11) & 2047, nb = (pk >> 22) + nbz;
-                const float lc = Lc[c];
-                const float lap = 6.f * lc - ((Lc[c - 1] + Lc[c + 1]) + (Lc[c - W1] + Lc[c + W1]) + (Lm[c] + Lp[c]));
-                const long long j = base + ph0[r];
-                Dout[j] = lf_update(lc, lap, kap[j], Yq[cy], nb);
-            }
-        }
-        __syncthreads();
-        // phase B: y^{n+1} at plane k on the 1-halo region
-        if (k >= 0 && k <= g.nz) {
-            const float* Ym = Y + ring4(k - 1) * P2;
-            const float* Yc = Y + ring4(k) * P2;
-            const float* Yp = Y + ring4(k + 1) * P2;
-            float* Lk = L + ring4(k) * P1;
-            const long long base = (long long)k * sxy;
-            const int nbz = ((k == 0) & zabc0) + ((k == g.nz) & zabc1);
-            const bool write_c = k >= z0 && k < z1;
-#pragma unroll
-            for (int r = 0; r < kTbR1; ++r) {
-                const int pk = pk1[r];
-                if (pk < 0) continue;
-                const int c = pk & 65535, nb = ((pk >> 16) & 7) + nbz;
-                const float yc = Yc[c];
-                const float lap = 6.f * yc - ((Yc[c - 1] + Yc[c + 1]) + (Yc[c - W2] + Yc[c + W2]) + (Ym[c] + Yp[c]));
-                const long long j = base + ph1[r];
-                const float out = lf_update(yc, lap, kap[j], A[j], nb);
-                Lk[tid + r * kTbThreads] = out;
-                if (write_c && (pk >> 19)) Cout[j] = out;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // Batched persistent step loop: one cooperative launch advances the step loops of many solves
 // (uneven grids and step counts) together.  Per step, the blocks stride over the work items of
 // every solve that still has steps left (a work item is one block of the solve's own launch
@@ -1321,32 +1174,6 @@ cudaError_t launch_barrier_selftest(unsigned* bar, int* err, long long spin_limi
     note_launch(1);
     k_barrier_selftest<<<1, kThreads, 0, st>>>(bar, err, spin_limit);
     return cudaGetLastError();
-}
-
-}  // namespace cmcg
-
-namespace cmcg {
-
-// Tile of the two-step kernel for a grid: interior <= 64 x ty_max (ty_max <= 16), balanced
-// over the grid.
-void tb_tile(const Geom& g, int ty_max, int* TX, int* TY) {
-    const int tx = (g.sx + 63) / 64, ty = (g.sy + ty_max - 1) / ty_max;
-    *TX = (g.sx + tx - 1) / tx;
-    *TY = (g.sy + ty - 1) / ty;
-}
-
-bool step2_supported(const Geom& g, int order) {
-    return g.dim == 3 && order == 2 && g.nx >= 2 && g.ny >= 2 && g.nz >= 2;
-}
-
-void launch_step2(const Geom& g, const float* A, const float* B, const float* kap, float* C, float* D, int zc,
-                  int ty_max, cudaStream_t st) {
-    note_launch(1);
-    int TX, TY;
-    tb_tile(g, ty_max < 1 ? 1 : (ty_max > 16 ? 16 : ty_max), &TX, &TY);
-    const size_t smem = sizeof(float) * (4 * (size_t)(TX + 4) * (TY + 4) + 4 * (size_t)(TX + 2) * (TY + 2));
-    const dim3 grid((unsigned)((g.sx + TX - 1) / TX), (unsigned)((g.sy + TY - 1) / TY), (unsigned)((g.sz + zc - 1) / zc));
-    k_step3d7_x2<<<grid, kTbThreads, smem, st>>>(A, B, kap, C, D, g, TX, TY, zc);
 }
 
 }  // namespace cmcg

@@ -136,13 +136,13 @@ def test_adjoint_period(case, precision, tol):
     assert rel(g1.cpu().numpy(), q1) <= tol, name
 
 
-@pytest.mark.parametrize("tile", [(0, 0, 0, 2), (0, 8, 8, 2), (0, 3, 16, 2), (16, 0, 0, 3), (3, 0, 0, 3),
+@pytest.mark.parametrize("tile", [(0, 0, 0, 2), (0, 8, 8, 2), (0, 3, 16, 2), (1, 1, 4, 2), (3, 5, 60, 2), (16, 0, 0, 3), (3, 0, 0, 3),
                                   (0, 0, 0, 4), (3, 0, 0, 4), (0, 2, 0, 4), (5, 1, 0, 4), (16, 0, 4, 3), (5, 0, 4, 3),
                                   (0, 0, 0, 5), (0, 0, 0, 6), (3, 1, 3, 6), (5, 2, 2, 6)])
 @pytest.mark.parametrize("name", ["odd3d_13x11x15", "sphere3d_24"])  # the 3D 7-point cases
 def test_step_scheme_variants(name, tile):
     # FP32 periods with the alternative step kernels: two steps per launch (temporal blocking,
-    # scheme 2), two z-planes per thread iteration (scheme 3), operands staged by bulk copies
+    # scheme 2: tile[0] planes staged ahead, tile[1] planes per block, tile[2] tile height), two z-planes per thread iteration (scheme 3), operands staged by bulk copies
     # into a shared-memory ring (scheme 4: tile[0] planes per CTA, tile[1] band rows), and one
     # aligned float4 of the flat node index per thread (scheme 5), and operands staged by
     # asynchronous copies (scheme 6: tile[0] planes per CTA, tile[1] band rows, tile[2] depth);
@@ -516,10 +516,11 @@ def test_full_size_period_sampled(full_size, precision, tol, tile):
         assert abs(vT[sl][local] - vTo[local]) <= tol * scale_v, cidx
 
 
-@pytest.mark.parametrize("tile", [(0, 0, 0, 3), (0, 0, 0, 4), (16, 0, 4, 3), (0, 0, 0, 5), (0, 0, 0, 6), (0, 0, 3, 6)])
+@pytest.mark.parametrize("tile", [(0, 0, 0, 2), (1, 8, 12, 2), (3, 40, 0, 2), (0, 0, 0, 3), (0, 0, 0, 4), (16, 0, 4, 3), (0, 0, 0, 5),
+                                  (0, 0, 0, 6), (0, 0, 3, 6)])
 def test_full_size_step_kernels_agree(full_size, tile):
-    # the z-pair, bulk-copy and vector-form kernels evaluate the single-step kernel's expression
-    # in the same order; their FP32 periods agree with it to rounding
+    # the two-step, z-pair, bulk-copy and vector-form kernels evaluate the single-step kernel's
+    # expression in the same order; their FP32 periods agree with it to rounding
     w, y0, v0 = full_size
     ref = [t.reshape(-1) for t in solver_of(w, cmcg.FP32, tile=(0, 0, 0, 1)).wave_period(y0, v0)]
     out = [t.reshape(-1) for t in solver_of(w, cmcg.FP32, tile=tile).wave_period(y0, v0)]
