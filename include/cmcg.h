@@ -298,6 +298,17 @@ int cmcg_fo_adjoint_period(cmcg_handle* h, const double* y, double* out);
  * context stays usable. */
 int cmcg_bulk_wait_selftest(int spin_limit, void* stream);
 
+/* Compiled-in bounds checks.  libcmcg_checked.so is the same library built with -DCMCG_CHECKED:
+ * its step, period-end, source, two-step, batched-step and multigrid kernels test, per thread,
+ * that every node index they will touch lies inside its array; a thread that fails records the
+ * check site and the index and skips its accesses.  This reads the records since the last call
+ * and clears them (synchronising the device): *count failed checks, *site the first one's site
+ * (1 column kernels, 2 float4 step, 3 batched step, 4 two-step node or plane, 5 two-step shared
+ * neighbour, 6 multigrid; -1 when none), *index its offending index.  Any pointer may be null.
+ * Returns CMCG_OK in the checked build; in the normal build (no checks compiled) it writes
+ * zeros and returns CMCG_ERR_UNSUPPORTED. */
+int cmcg_check_status(long long* count, long long* site, long long* index);
+
 /* ---- multi-solve engine (batched solves and serving) -------------------------------- */
 /* Many solves advance together, one CG iteration per cmcg_engine_tick.  Each admitted solve
  * keeps its own handle (its workspace holds the resident CG state).  Per tick, the FP32

@@ -2,6 +2,8 @@
 
 Each translation unit is compiled in parallel, then linked into
 paper_1903_12522_gb300/libcmcg.so.  Objects go to paper_1903_12522_gb300/_build/.
+build(checked=True) makes libcmcg_checked.so, the same sources with -DCMCG_CHECKED (the
+kernels' compiled-in bounds checks, read through cmcg_check_status), objects in _build_checked/.
 """
 from __future__ import annotations
 
@@ -16,6 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcmcg.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libcmcg_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -34,8 +38,8 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, out_dir: str) -> str:
+    obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -45,21 +49,33 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra=(), checked: bool = False) -> str:
+    out_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    extra = list(extra) + (["-DCMCG_CHECKED"] if checked else [])
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    tmp = LIB + ".tmp"
+    with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 1), len(srcs), 16)) as ex:
+        objs = list(ex.map(lambda s: _compile(s, extra, out_dir), srcs))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}")
-    return LIB
+        print(f"built {lib}")
+    return lib
+
+
+def build_all(verbose: bool = False) -> None:
+    """Both libraries, their translation units compiled side by side."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        for f in [ex.submit(build, verbose, (), c) for c in (False, True)]:
+            f.result()
 
 
 if __name__ == "__main__":
-    build(verbose=True, extra=sys.argv[1:])
+    if "--checked" in sys.argv:
+        build(verbose=True, extra=[a for a in sys.argv[1:] if a != "--checked"], checked=True)
+    else:
+        build(verbose=True, extra=sys.argv[1:])

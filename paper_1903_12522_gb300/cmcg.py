@@ -17,6 +17,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcmcg.so")
+# the same library with the kernels' compiled-in bounds checks (build(checked=True)); loaded
+# instead of LIB_PATH when the environment sets CMCG_CHECKED=1
+LIB_CHECKED_PATH = os.path.join(HERE, "libcmcg_checked.so")
 
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID_ARG, ERR_CFL, ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_CUDA, ERR_DIVERGED = -1, -2, -3, -4, -5, -6
@@ -39,7 +42,7 @@ EXPORTED = (
     "cmcg_engine_workspace_size", "cmcg_engine_create", "cmcg_engine_destroy", "cmcg_engine_submit",
     "cmcg_engine_tick", "cmcg_engine_result", "cmcg_engine_active", "cmcg_engine_info", "cmcg_engine_set_shape",
     "cmcg_engine_barrier_selftest", "cmcg_engine_cuda_error", "cmcg_fo_period", "cmcg_fo_adjoint_period",
-    "cmcg_bulk_wait_selftest",
+    "cmcg_bulk_wait_selftest", "cmcg_check_status",
 )
 
 
@@ -80,13 +83,16 @@ class Info(C.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libcmcg.so and declare its signatures.  Raises if it is missing."""
+def load(path: str = None):
+    """Load libcmcg.so (libcmcg_checked.so when CMCG_CHECKED=1) and declare its signatures.
+    Raises if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_CHECKED_PATH if os.environ.get("CMCG_CHECKED") == "1" else LIB_PATH
     if not os.path.exists(path):
-        raise RuntimeError(f"libcmcg.so not built ({path}); run __graft_entry__.build()")
+        raise RuntimeError(f"{os.path.basename(path)} not built ({path}); run __graft_entry__.build()")
     lib = C.CDLL(path)
     P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
     lib.cmcg_workspace_size.argtypes = [C.POINTER(Grid), C.POINTER(Options)]
@@ -139,6 +145,9 @@ def load(path: str = LIB_PATH):
     lib.cmcg_engine_barrier_selftest.restype = I
     lib.cmcg_engine_cuda_error.argtypes = [P]
     lib.cmcg_engine_cuda_error.restype = C.c_char_p
+    LL = C.POINTER(C.c_longlong)
+    lib.cmcg_check_status.argtypes = [LL, LL, LL]
+    lib.cmcg_check_status.restype = I
     _lib = lib
     return lib
 
@@ -226,6 +235,14 @@ def cmcg_bulk_wait_selftest(spin_limit: int, stream=None) -> int:
     """Bounded-wait self-test of the bulk-copy step kernel; returns the status code
     (ERR_DEVICE_TIMEOUT is the expected outcome)."""
     return int(load().cmcg_bulk_wait_selftest(int(spin_limit), stream))
+
+
+def cmcg_check_status():
+    """(code, count, site, index) of the compiled-in bounds checks since the last call; code is
+    OK in the checked library and ERR_UNSUPPORTED in the normal one."""
+    c, si, ix = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    code = load().cmcg_check_status(C.byref(c), C.byref(si), C.byref(ix))
+    return int(code), int(c.value), int(si.value), int(ix.value)
 
 
 def cmcg_fo_period(h, s0, f, g, sT) -> None:

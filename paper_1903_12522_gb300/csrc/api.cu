@@ -1494,6 +1494,29 @@ int cmcg_bulk_wait_selftest(int spin_limit, void* stream) {
     return bulk_wait_selftest(spin_limit, (cudaStream_t)stream);
 }
 
+int cmcg_check_status(long long* count, long long* site, long long* index) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return CMCG_ERR_CUDA;
+    long long total = 0, first_site = -1, first_index = 0;
+    for (auto read : {check_read_wave, check_read_riesz, check_read_pair}) {
+        long long w[3];
+        read(w);
+        if (w[0] > 0 && first_site < 0) {
+            first_site = w[1];
+            first_index = w[2];
+        }
+        total += w[0];
+    }
+    if (count) *count = total;
+    if (site) *site = first_site;
+    if (index) *index = first_index;
+    if (cudaGetLastError() != cudaSuccess) return CMCG_ERR_CUDA;
+#ifdef CMCG_CHECKED
+    return CMCG_OK;
+#else
+    return CMCG_ERR_UNSUPPORTED;
+#endif
+}
+
 int cmcg_fo_period(cmcg_handle* h, const double* s0, const double* f, const double* g, double* sT) {
     if (!h || !s0 || !sT) return CMCG_ERR_INVALID_ARG;
     if (!h->first_order) return CMCG_ERR_UNSUPPORTED;

@@ -65,6 +65,107 @@ __device__ __forceinline__ long long off_p2(int i, int n, long long s) {
     return (long long)(k - i) * s;
 }
 
+// ---- compiled-in bounds checks --------------------------------------------------------
+// The checked build (libcmcg_checked.so, compiled with -DCMCG_CHECKED) tests, in the kernels
+// that derive node indices from their launch coordinates, that every index a thread will touch
+// lies inside its arrays.  A thread that fails records the check site and the offending index
+// in its translation unit's error word and skips its accesses (it is treated as outside the
+// grid); cmcg_check_status reads and clears the words.  In the normal build the checks compile
+// to `true` and the words do not exist.
+#ifdef CMCG_CHECKED
+namespace {
+__device__ unsigned long long g_check_count;
+__device__ long long g_check_site;
+__device__ long long g_check_index;
+}  // namespace
+__device__ __forceinline__ bool check_range(long long lo, long long hi, long long n, int site) {
+    if (lo >= 0 && hi < n && lo <= hi) return true;
+    if (atomicAdd(&g_check_count, 1ull) == 0ull) {
+        g_check_site = site;
+        g_check_index = lo < 0 ? lo : hi;
+    }
+    return false;
+}
+// Reads (count, site, index) of this translation unit's word into out[0..2] and clears it.
+#define CMCG_CHECK_TU(name)                                                                   \
+    void check_read_##name(long long* out) {                                                  \
+        unsigned long long c = 0;                                                             \
+        long long si = -1, ix = 0;                                                            \
+        cudaMemcpyFromSymbol(&c, g_check_count, sizeof(c));                                   \
+        cudaMemcpyFromSymbol(&si, g_check_site, sizeof(si));                                  \
+        cudaMemcpyFromSymbol(&ix, g_check_index, sizeof(ix));                                 \
+        const unsigned long long zero = 0;                                                    \
+        cudaMemcpyToSymbol(g_check_count, &zero, sizeof(zero));                               \
+        out[0] = (long long)c;                                                                \
+        out[1] = c ? si : -1;                                                                 \
+        out[2] = c ? ix : 0;                                                                  \
+    }
+#define CMCG_RANGE_OK(lo, hi, n, site) ::cmcg::check_range((lo), (hi), (n), (site))
+#else
+#define CMCG_CHECK_TU(name)                \
+    void check_read_##name(long long* out) { \
+        out[0] = 0;                          \
+        out[1] = -1;                         \
+        out[2] = 0;                          \
+    }
+#define CMCG_RANGE_OK(lo, hi, n, site) true
+#endif
+
+// Check sites (the kernel families that test their index ranges).
+enum CheckSite {
+    kSiteColumn = 1,     // column-marching kernels of wave.cu (steps, period ends, source)
+    kSiteVector = 2,     // the float4 step (flat chunks)
+    kSiteBatch = 3,      // a work item of the batched step kernel
+    kSitePairGlobal = 4, // two-step kernel: a column's node or plane
+    kSitePairShared = 5, // two-step kernel: a shared-memory neighbour
+    kSiteMultigrid = 6,  // column-marching multigrid kernels of riesz.cu
+};
+
+// Does the index range of a column-marching thread lie inside the grid: node (ix, iy, iz) for
+// z0 <= iz < z1 and its mirror neighbours up to `radius` nodes away along each axis?
+__device__ __forceinline__ bool column_in_range(const Geom& g, int ix, int iy, int z0, int z1, int radius, int site) {
+#ifdef CMCG_CHECKED
+    if (z0 >= z1) return true;  // no planes: nothing is touched
+    if (ix < 0 || ix > g.nx || iy < 0 || iy > g.ny || z0 < 0 || z1 > g.sz)
+        return check_range(-1, -1, 0, site);
+    const long long sY = g.sx, sZ = (long long)g.sx * g.sy;
+    long long dmin = 0, dmax = 0;  // in-plane offsets
+    auto take = [&](long long d) {
+        dmin = d < dmin ? d : dmin;
+        dmax = d > dmax ? d : dmax;
+    };
+    take(off_m1(ix, 1));
+    take(off_p1(ix, g.nx, 1));
+    take(off_m1(iy, sY));
+    take(off_p1(iy, g.ny, sY));
+    if (radius >= 2) {
+        take(off_m2(ix, 1));
+        take(off_p2(ix, g.nx, 1));
+        take(off_m2(iy, sY));
+        take(off_p2(iy, g.ny, sY));
+    }
+    long long zlo = 0, zhi = 0;  // z offsets at the first and the last plane
+    if (g.dim == 3) {
+        zlo = off_m1(z0, sZ);
+        zlo = off_p1(z0, g.nz, sZ) < zlo ? off_p1(z0, g.nz, sZ) : zlo;
+        zhi = off_p1(z1 - 1, g.nz, sZ);
+        zhi = off_m1(z1 - 1, sZ) > zhi ? off_m1(z1 - 1, sZ) : zhi;
+        if (radius >= 2) {
+            zlo = off_m2(z0, sZ) < zlo ? off_m2(z0, sZ) : zlo;
+            zhi = off_p2(z1 - 1, g.nz, sZ) > zhi ? off_p2(z1 - 1, g.nz, sZ) : zhi;
+        }
+        zlo = zlo < 0 ? zlo : 0;
+        zhi = zhi > 0 ? zhi : 0;
+    }
+    const long long lo = node(g, ix, iy, z0) + (dmin < zlo ? dmin : zlo);
+    const long long hi = node(g, ix, iy, z1 - 1) + (dmax > zhi ? dmax : zhi);
+    return check_range(lo, hi, g.np, site);
+#else
+    (void)g, (void)ix, (void)iy, (void)z0, (void)z1, (void)radius, (void)site;
+    return true;
+#endif
+}
+
 // Unscaled Laplacian Lt(f) at node j for a value functor f(index) -> R.
 template <int ORDER, typename R, typename F>
 __device__ __forceinline__ R lap_t(const Geom& g, F f, long long j, int ix, int iy, int iz) {

@@ -24,6 +24,11 @@ constexpr int kZcFlat = 1 << 20;
 
 // Process-wide count of kernels launched by this library (every launcher records its launches).
 void note_launch(long long k);
+// Compiled-in bounds checks (CMCG_CHECKED builds): (count, first site, first index) of the
+// failed checks in each translation unit since the last read; the read clears them.
+void check_read_wave(long long* out);
+void check_read_riesz(long long* out);
+void check_read_pair(long long* out);
 long long launch_count();
 
 // ---- wave.cu --------------------------------------------------------------------------

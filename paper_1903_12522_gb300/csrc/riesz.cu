@@ -233,6 +233,7 @@ __device__ __forceinline__ PlaneIt plane_it(const Geom& g, int zc) {
     m.ix = (int)(pp - (unsigned)m.iy * (unsigned)g.sx);
     m.z0 = blockIdx.y * zc;
     m.z1 = min(m.z0 + zc, g.sz);
+    if (m.valid && !column_in_range(g, m.ix, m.iy, m.z0, m.z1, 1, kSiteMultigrid)) m.valid = false;
     return m;
 }
 
@@ -806,4 +807,8 @@ void launch_mean_remove(const Geom& g, double* x, double volume, Red red, cudaSt
     k_sub_const<<<vec_blocks(g.np), kT, 0, st>>>(g.np, x, red.sc, 1.0 / volume);
 }
 
+}  // namespace cmcg
+
+namespace cmcg {
+CMCG_CHECK_TU(riesz)
 }  // namespace cmcg

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kPairThreads)
     const int nz = g.nz;
     const long long sxy = (long long)g.sx * g.sy;
     const int tid = threadIdx.x;
+    if (!CMCG_RANGE_OK(z0, z1 - 1, g.sz, kSitePairGlobal)) return;  // uniform over the block
 
     // Column r of this thread: in-plane offset of its (mirror) node, -1 outside the region;
     // role bit 0: 1-halo region (computes y^{n+1}), bit 1: interior (computes y^{n+2}, stores);
@@ -99,6 +100,13 @@ __global__ void __launch_bounds__(kPairThreads)
             const int nb = ((px == 0) & (int)(g.abc & 1u)) + ((px == g.nx) & (int)((g.abc >> 1) & 1u)) +
                            ((py == 0) & (int)((g.abc >> 2) & 1u)) + ((py == g.ny) & (int)((g.abc >> 3) & 1u));
             role[r] = (h1 ? 1 : 0) | (in ? 2 : 0) | (nb << 2);
+            // checked build: the node lies in its plane, and a first-step column's neighbours
+            // lie in the staged region
+            if (!CMCG_RANGE_OK(ph[r], ph[r], sxy, kSitePairGlobal) ||
+                ((role[r] & 1) && !CMCG_RANGE_OK(i - W, i + W, W * H, kSitePairShared))) {
+                ph[r] = -1;
+                role[r] = 0;
+            }
         }
     }
     const int zabc0 = (int)((g.abc >> 4) & 1u), zabc1 = (int)((g.abc >> 5) & 1u);
@@ -275,4 +283,8 @@ void launch_step2(const Geom& g, const float* A, const float* B, const float* ka
         launch_pair<2>(g, A, B, kap, C, D, zc, ty, st);
 }
 
+}  // namespace cmcg
+
+namespace cmcg {
+CMCG_CHECK_TU(pair)
 }  // namespace cmcg

@@ -34,7 +34,9 @@ struct PlaneMap {
     bool valid;
 };
 
-__device__ __forceinline__ PlaneMap plane_map(const Geom& g, int zc) {
+// radius: the stencil's reach along each axis (the checked build tests the column's index
+// range against the grid and drops a column that would leave it)
+__device__ __forceinline__ PlaneMap plane_map(const Geom& g, int zc, int radius = 1) {
     PlaneMap m;
     const long long plane = (long long)g.sx * g.sy;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -44,6 +46,7 @@ __device__ __forceinline__ PlaneMap plane_map(const Geom& g, int zc) {
     m.ix = (int)(pp - (long long)m.iy * g.sx);
     m.z0 = blockIdx.y * zc;
     m.z1 = min(m.z0 + zc, g.sz);
+    if (m.valid && !column_in_range(g, m.ix, m.iy, m.z0, m.z1, radius, kSiteColumn)) m.valid = false;
     return m;
 }
 
@@ -73,7 +76,7 @@ template <typename T, int ORDER, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step(const T* __restrict__ cur, T* __restrict__ prev_out,
                                                    const T* __restrict__ kap, const T* __restrict__ S,
                                                    double cs, double sn, Geom g, int zc) {
-    const PlaneMap m = plane_map(g, zc);
+    const PlaneMap m = plane_map(g, zc, ORDER / 2);
     if (!m.valid) return;
     Ld<T> f{cur};
     for (int iz = m.z0; iz < m.z1; ++iz) {
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_step_filter(const double* __restri
                                                           const double* __restrict__ kap, const double* __restrict__ S,
                                                           double cs, double sn, double* __restrict__ acc, double fc,
                                                           double fs, double cv, Geom g, int zc) {
-    const PlaneMap m = plane_map(g, zc);
+    const PlaneMap m = plane_map(g, zc, ORDER / 2);
     if (!m.valid) return;
     Ld<double> f{cur};
     for (int iz = m.z0; iz < m.z1; ++iz) {
@@ -318,6 +321,8 @@ __global__ void __launch_bounds__(kThreads) k_step_v4(const float* __restrict__ 
     const long long nch = (g.np + 3) >> 2;
     const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
     if (c >= nch) return;
+    // chunks read: c and the windows at flat offsets +-sx (+-sx sy), clamped into [0, nch)
+    if (!CMCG_RANGE_OK(4 * c, 4 * c + 3, 4 * nch, kSiteVector)) return;
     const long long sY = g.sx, sZ = (long long)g.sx * g.sy;
     const long long i0 = 4 * c;
     const float4 yc4 = ld4g(cur, c);
@@ -495,7 +500,7 @@ template <typename T, int FLAGS>
 __global__ void __launch_bounds__(kThreads) k_step3d13(const T* __restrict__ cur, T* __restrict__ prev_out,
                                                        const T* __restrict__ kap, const T* __restrict__ S,
                                                        double cs, double sn, Geom g, int zc) {
-    const PlaneMap m = plane_map(g, zc);
+    const PlaneMap m = plane_map(g, zc, 2);
     if (!m.valid || m.z0 >= m.z1) return;
     const long long sZ = (long long)g.sx * g.sy;
     const long long col = (long long)m.ix + (long long)g.sx * m.iy;
@@ -560,7 +565,7 @@ __global__ void __launch_bounds__(kThreads) k_start(const T* __restrict__ w0t, c
                                                     T* __restrict__ y0, T* __restrict__ y1,
                                                     const T* __restrict__ kap, const double* __restrict__ S,
                                                     Geom g, double dt, int zc) {
-    const PlaneMap m = plane_map(g, zc);
+    const PlaneMap m = plane_map(g, zc, ORDER / 2);
     if (!m.valid || m.z0 >= m.z1) return;
     Ld<T> f{w0t};
     const T dtT = (T)dt;
@@ -602,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_end(const T* __r
                                                   const double* __restrict__ S, double cs, double sn,
                                                   double* __restrict__ out0, double* __restrict__ out1,
                                                   Red red, Geom g, double dt, int zc) {
-    const PlaneMap m = plane_map(g, zc);
+    const PlaneMap m = plane_map(g, zc, ORDER / 2);
     double acc[1] = {0.0};
     KahanF accf;  // FP32 periods: the thread's part of J without FP64 arithmetic
     if (m.valid) {
@@ -673,7 +678,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_start(const A* __restrict__ a,
                                                         const T* __restrict__ mass, const T* __restrict__ kap,
                                                         T* __restrict__ cur, T* __restrict__ prev, Geom g, double dt,
                                                         int zc) {
-    const PlaneMap m = plane_map(g, zc);
+    const PlaneMap m = plane_map(g, zc, ORDER / 2);
     if (!m.valid) return;
     Ld<T> f{t};
     const T dtT = (T)dt;
@@ -705,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, kEndMinBlocks<T>) k_adj_final(const 
                                                         const V* __restrict__ d0, const V* __restrict__ d1,
                                                         V* __restrict__ o0, V* __restrict__ o1,
                                                         double* __restrict__ gt1, Red red, Geom g, double dt, int zc) {
-    const PlaneMap m = plane_map(g, zc);
+    const PlaneMap m = plane_map(g, zc, ORDER / 2);
     double acc[2] = {0.0, 0.0};
     KahanF accf0, accf1;
     if (m.valid && m.z0 < m.z1) {
@@ -855,6 +860,7 @@ __device__ __forceinline__ void step_item(const float* __restrict__ cur, float* 
     const int iy = (int)(p / g.sx);
     const int ix = (int)(p - (long long)iy * g.sx);
     const int z0 = bz * zc, z1 = min(z0 + zc, g.sz);
+    if (!column_in_range(g, ix, iy, z0, z1, ORDER / 2, kSiteBatch)) return;
     Ld<float> f{cur};
     for (int iz = z0; iz < z1; ++iz) {
         const long long j = node(g, ix, iy, iz);
@@ -1203,4 +1209,8 @@ void launch_scale_complex(long long n, double* u, double s, cudaStream_t st) {
     k_scale_complex<<<blocks, kThreads, 0, st>>>(n, u, s);
 }
 
+}  // namespace cmcg
+
+namespace cmcg {
+CMCG_CHECK_TU(wave)
 }  // namespace cmcg

@@ -38,6 +38,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(cmcg.EXPORTED) <= set(names)
 
 
+def test_checked_library_exports_the_same_symbols():
+    # libcmcg_checked.so: the same sources with the kernels' compiled-in bounds checks
+    if not os.path.exists(cmcg.LIB_CHECKED_PATH):
+        from paper_1903_12522_gb300 import build
+
+        build.build(checked=True)
+    chk = C.CDLL(cmcg.LIB_CHECKED_PATH)
+    for name in declared_functions():
+        assert hasattr(chk, name), name
+
+
 def test_workspace_size(lib):
     g = cmcg.make_grid((64, 48), 1 / 64)
     s64 = cmcg.cmcg_workspace_size(g, cmcg.make_options(cmcg.FP64))
