@@ -330,13 +330,14 @@ PeriodBuffers fwd_begin(cmcg_handle* H, const double* w0, const double* w1, bool
 // z-planes per thread of the one-step kernels; negative selects the variant that processes two
 // planes per loop iteration (tile[3] == 3), kZcFlat the FP32 vector form (tile[3] == 5)
 // tile[3] == 0 takes the scheme the autotuner found fastest on every measured class: the
-// z-pair kernel on 3D 7-point grids, the vector form on 2D 5-point grids (FP64 steps fall
-// back to their one-step kernels).
+// z-pair kernel on 3D 7- and 13-point grids, the vector form on 2D 5-point grids (FP64 steps
+// fall back to their one-step kernels).
 int step_zc(const cmcg_handle* H) {
     const int scheme = H->opt.tile[3];
     if (H->order == 2 && (scheme == 5 || (scheme == 0 && H->g.dim == 2))) return kZcFlat;
     if (H->g.dim != 3) return 1;
     const int zc = H->opt.tile[0] > 0 ? H->opt.tile[0] : kZcStep3D;
+    if (H->order == 4) return (scheme == 3 || scheme == 0) ? -zc : zc;  // the 13-point z-pair kernel
     if (H->order != 2 || (scheme != 3 && scheme != 0)) return zc;
     return H->opt.tile[2] == 4 ? -(zc + kZk4) : -zc;  // tile[2]: planes per loop iteration (2 or 4)
 }

@@ -165,6 +165,26 @@ def test_step_scheme_variants(name, tile):
         assert rel(uF.cpu().numpy(), yF) <= 2e-5 and rel(uVF.cpu().numpy(), vF) <= 2e-5
 
 
+@pytest.mark.parametrize("tile", [(0, 0, 0, 1), (3, 0, 0, 1), (0, 0, 0, 3), (3, 0, 0, 3), (5, 0, 0, 0)])
+def test_step13_variants(tile):
+    # the 4th-order (13-point) step: one z-plane per loop trip (scheme 1) and two (scheme 3,
+    # the default); tile[0] z-planes per block gives ragged chunks on the 17^3 grid.  FP32 and
+    # FP64, forced and homogeneous periods, and the adjoint
+    w = CASES["layered3d_o4_16"]()
+    dz = dz_of(w)
+    assert w.order == 4 and w.dim == 3
+    y0, v0 = rand_state(dz, 8)
+    F = dz.load(w.f, w.g)
+    yF, vF = wave.period(dz, y0, v0, F)
+    q0, q1 = wave.transposed_period(dz, y0, v0)
+    for precision, tol in ((cmcg.FP64, 1e-12), (cmcg.FP32, 2e-5)):
+        s = solver_of(w, precision, tile=tile)
+        uF, uVF = s.wave_period(y0, v0, w.f, w.g)
+        assert rel(uF.cpu().numpy(), yF) <= tol and rel(uVF.cpu().numpy(), vF) <= tol, (tile, precision)
+        g0, g1 = s.adjoint_period(y0, v0)
+        assert rel(g0.cpu().numpy(), q0) <= tol and rel(g1.cpu().numpy(), q1) <= tol, (tile, precision)
+
+
 @pytest.mark.parametrize("name", ["gauss2d_40", "odd2d_37x29", "mixed2d"])
 def test_vector_step_2d(name):
     # the vector-form step (scheme 5) on 2D 5-point grids: forced and homogeneous FP32 periods
