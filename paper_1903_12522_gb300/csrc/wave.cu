@@ -922,6 +922,60 @@ __device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, long lon
     return ok != 0;
 }
 
+// The 3D 7-point step of one work item's column: two z-planes per loop trip with every load
+// issued first and the z-neighbours in registers, as in k_step3d7_z2 (the same expression in
+// the same order as the generic work-item step below).
+template <int FLAGS>
+__device__ __forceinline__ void step_item3d7(const float* __restrict__ cur, float* __restrict__ prev,
+                                             const float* __restrict__ kap, const Geom& g, int ix, int iy, int z0,
+                                             int z1) {
+    const long long sZ = (long long)g.sx * g.sy;
+    long long j = node(g, ix, iy, z0);
+    const long long oxm = off_m1(ix, 1), oxp = off_p1(ix, g.nx, 1);
+    const long long oym = off_m1(iy, g.sx), oyp = off_p1(iy, g.ny, g.sx);
+    int nbxy = 0;
+    nbxy += (ix == 0) & (int)(g.abc & 1u);
+    nbxy += (ix == g.nx) & (int)((g.abc >> 1) & 1u);
+    nbxy += (iy == 0) & (int)((g.abc >> 2) & 1u);
+    nbxy += (iy == g.ny) & (int)((g.abc >> 3) & 1u);
+    auto update = [&](float yc, float ym, float yz, long long jj, int iz, float sxy, float k, float yp) {
+        const float L = 6.f * yc - (sxy + (ym + yz));
+        const float rhs = 2.f * yc - k * L;
+        const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
+        float out;
+        if (nb == 0) {
+            out = rhs - yp;
+        } else {
+            const float beta = (float)nb * sqrtf(k);
+            const float v = rhs - ((FLAGS & kStepPrevScaled) ? yp : (1.f - beta) * yp);
+            out = (FLAGS & kStepNoDiv) ? v : v / (1.f + beta);
+        }
+        prev[jj] = out;
+    };
+    float ym = cur[j + (z0 > 0 ? -sZ : sZ)];
+    float yc = cur[j];
+    int iz = z0;
+    for (; iz + 1 < z1; iz += 2) {
+        const long long j1 = j + sZ;
+        const float y1 = cur[j1];
+        const float y2 = cur[j1 + (iz + 1 < g.nz ? sZ : -sZ)];
+        const float s0 = (cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]);
+        const float s1 = (cur[j1 + oxm] + cur[j1 + oxp]) + (cur[j1 + oym] + cur[j1 + oyp]);
+        const float k0 = kap[j], k1 = kap[j1];
+        const float p0 = prev[j], p1 = prev[j1];
+        update(yc, ym, y1, j, iz, s0, k0, p0);
+        update(y1, yc, y2, j1, iz + 1, s1, k1, p1);
+        ym = y1;
+        yc = y2;
+        j += 2 * sZ;
+    }
+    if (iz < z1) {
+        const float yz = cur[j + (iz < g.nz ? sZ : -sZ)];
+        const float s0 = (cur[j + oxm] + cur[j + oxp]) + (cur[j + oym] + cur[j + oyp]);
+        update(yc, ym, yz, j, iz, s0, kap[j], prev[j]);
+    }
+}
+
 // The step of one work item (block-sized piece of one solve's grid).
 template <int ORDER, int FLAGS>
 __device__ __forceinline__ void step_item(const float* __restrict__ cur, float* __restrict__ prev,
@@ -933,6 +987,10 @@ __device__ __forceinline__ void step_item(const float* __restrict__ cur, float* 
     const int ix = (int)(p - (long long)iy * g.sx);
     const int z0 = bz * zc, z1 = min(z0 + zc, g.sz);
     if (!column_in_range(g, ix, iy, z0, z1, ORDER / 2, kSiteBatch)) return;
+    if (ORDER == 2 && g.dim == 3) {
+        step_item3d7<FLAGS>(cur, prev, kap, g, ix, iy, z0, z1);
+        return;
+    }
     Ld<float> f{cur};
     for (int iz = z0; iz < z1; ++iz) {
         const long long j = node(g, ix, iy, iz);
