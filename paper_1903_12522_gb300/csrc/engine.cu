@@ -111,6 +111,8 @@ BatchItem make_item(cmcg_handle* h, const PeriodBuffers& b, bool adjoint, int zc
     it.zc = h->g.dim == 3 ? zc3 : 1;
     const long long plane = (long long)h->g.sx * h->g.sy;
     it.blocks_xy = (int)((plane + 255) / 256);
+    it.vec4 = h->g.dim == 2 && h->order == 2 && step_vec4_ok(h->g, it.buf0, it.buf1, it.kap);
+    if (it.vec4) it.blocks_xy = (int)((((h->g.np + 3) >> 2) + 255) / 256);
     it.blocks = it.blocks_xy * ((h->g.sz + it.zc - 1) / it.zc);
     return it;
 }

@@ -82,7 +82,9 @@ struct BatchItem {
     float* buf0;  // y^n at step 0
     float* buf1;  // y^{n-1} at step 0
     int order, nsteps, adjoint, zc, blocks_xy, blocks, offset;
+    int vec4;  // 2D 5-point: work items are 256 aligned float4 chunks of the flat index
 };
+bool step_vec4_ok(const Geom& g, const void* cur, const void* prev, const void* kap);
 int batch_steps_max_blocks();
 cudaError_t launch_batch_steps(const BatchItem* items, int nitems, int total_blocks, int max_steps, unsigned* bar,
                                int* err, int grid, cudaStream_t st);

@@ -315,11 +315,10 @@ __device__ __forceinline__ Win4 window4(const float* __restrict__ f, long long c
 }
 
 template <int DIM, int FLAGS>
-__global__ void __launch_bounds__(kThreads) k_step_v4(const float* __restrict__ cur, float* __restrict__ prev_out,
-                                                      const float* __restrict__ kap, const float* __restrict__ S,
-                                                      double cs, double sn, Geom g) {
+__device__ __forceinline__ void step_v4_chunk(const float* __restrict__ cur, float* __restrict__ prev_out,
+                                              const float* __restrict__ kap, const float* __restrict__ S, double cs,
+                                              double sn, const Geom& g, long long c) {
     const long long nch = (g.np + 3) >> 2;
-    const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
     if (c >= nch) return;
     // chunks read: c and the windows at flat offsets +-sx (+-sx sy), clamped into [0, nch)
     if (!CMCG_RANGE_OK(4 * c, 4 * c + 3, 4 * nch, kSiteVector)) return;
@@ -408,6 +407,13 @@ __global__ void __launch_bounds__(kThreads) k_step_v4(const float* __restrict__ 
         for (int e = 0; e < 4; ++e)
             if (i0 + e < g.np) prev_out[i0 + e] = out[e];
     }
+}
+
+template <int DIM, int FLAGS>
+__global__ void __launch_bounds__(kThreads) k_step_v4(const float* __restrict__ cur, float* __restrict__ prev_out,
+                                                      const float* __restrict__ kap, const float* __restrict__ S,
+                                                      double cs, double sn, Geom g) {
+    step_v4_chunk<DIM, FLAGS>(cur, prev_out, kap, S, cs, sn, g, (long long)blockIdx.x * kThreads + threadIdx.x);
 }
 
 // Can the vector-form step run on these fields?  16-byte aligned fields (each carries at
@@ -979,7 +985,12 @@ __device__ __forceinline__ void step_item3d7(const float* __restrict__ cur, floa
 // The step of one work item (block-sized piece of one solve's grid).
 template <int ORDER, int FLAGS>
 __device__ __forceinline__ void step_item(const float* __restrict__ cur, float* __restrict__ prev,
-                                          const float* __restrict__ kap, const Geom& g, int zc, int bx, int bz) {
+                                          const float* __restrict__ kap, const Geom& g, int zc, int bx, int bz,
+                                          int vec4) {
+    if (ORDER == 2 && g.dim == 2 && vec4) {  // 2D: one aligned float4 chunk of the flat index per thread
+        step_v4_chunk<2, FLAGS>(cur, prev, kap, nullptr, 0.0, 0.0, g, (long long)bx * kThreads + threadIdx.x);
+        return;
+    }
     const long long plane = (long long)g.sx * g.sy;
     const long long p = (long long)bx * kThreads + threadIdx.x;
     if (p >= plane) return;
@@ -1013,12 +1024,12 @@ __device__ __forceinline__ void step_item(const float* __restrict__ cur, float* 
 
 template <int ORDER>
 __device__ __forceinline__ void step_item_flags(const float* cur, float* prev, const float* kap, const Geom& g, int zc,
-                                                int bx, int bz, int flags) {
+                                                int bx, int bz, int flags, int vec4) {
     switch (flags) {
-        case 0: step_item<ORDER, 0>(cur, prev, kap, g, zc, bx, bz); break;
-        case kStepPrevScaled: step_item<ORDER, kStepPrevScaled>(cur, prev, kap, g, zc, bx, bz); break;
-        case kStepNoDiv: step_item<ORDER, kStepNoDiv>(cur, prev, kap, g, zc, bx, bz); break;
-        default: step_item<ORDER, kStepPrevScaled | kStepNoDiv>(cur, prev, kap, g, zc, bx, bz); break;
+        case 0: step_item<ORDER, 0>(cur, prev, kap, g, zc, bx, bz, vec4); break;
+        case kStepPrevScaled: step_item<ORDER, kStepPrevScaled>(cur, prev, kap, g, zc, bx, bz, vec4); break;
+        case kStepNoDiv: step_item<ORDER, kStepNoDiv>(cur, prev, kap, g, zc, bx, bz, vec4); break;
+        default: step_item<ORDER, kStepPrevScaled | kStepNoDiv>(cur, prev, kap, g, zc, bx, bz, vec4); break;
     }
 }
 
@@ -1044,8 +1055,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_steps(const BatchItem* __res
                 if (s == 0) flags |= kStepPrevScaled;
                 if (s == it.nsteps - 1) flags |= kStepNoDiv;
             }
-            if (it.order == 2) step_item_flags<2>(cur, prev, it.kap, it.g, it.zc, bx, bz, flags);
-            else step_item_flags<4>(cur, prev, it.kap, it.g, it.zc, bx, bz, flags);
+            if (it.order == 2) step_item_flags<2>(cur, prev, it.kap, it.g, it.zc, bx, bz, flags, it.vec4);
+            else step_item_flags<4>(cur, prev, it.kap, it.g, it.zc, bx, bz, flags, 0);
         }
         if (s + 1 < max_steps && !grid_barrier(bar, err, gridDim.x, spin_limit)) return;
     }
@@ -1288,6 +1299,10 @@ int batch_steps_max_blocks() {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_steps, kThreads, 0);
     return per_sm * sms;
+}
+
+bool step_vec4_ok(const Geom& g, const void* cur, const void* prev, const void* kap) {
+    return step_v4_ok(g, cur, prev, kap);
 }
 
 cudaError_t launch_batch_steps(const BatchItem* items, int nitems, int total_blocks, int max_steps, unsigned* bar,
