@@ -375,9 +375,10 @@ int cmcg_engine_barrier_selftest(cmcg_engine* e, long long spin_limit);
  * cudaStream_t, NULL = default stream).  It calls no cudaMalloc, cudaFree or other allocating
  * routine.  Its scratch is one static 18 MiB device array inside this library, which every GPU
  * that loads the library holds until the process exits; grids above 262,144 nodes (for example
- * larger than 511^2 in 2D or 63^3 in 3D) are rejected with CMCG_ERR_WORKSPACE.  The first call
- * on a device looks up the array's device address with cudaGetSymbolAddress (make that first
- * call before any stream capture on that device); the address is kept for the life of the
+ * larger than 511^2 in 2D or 63^3 in 3D) are rejected with CMCG_ERR_WORKSPACE.  Every call
+ * reads scalars back to the host and synchronises its stream, so no call may be made while its
+ * stream is being captured into a CUDA graph.  The first call on a device looks up the
+ * array's device address with cudaGetSymbolAddress; the address is kept for the life of the
  * process, so a device reset (cudaDeviceReset) on a device this entry point has used leaves
  * it unusable on that device.  Every call on a device shares the array and
  * clears the parts that must start at zero; calls that overlap on the GPU (other streams or
