@@ -269,6 +269,17 @@ int cmcg_riesz(cmcg_handle* h, const double* rhs, double* s);
 int cmcg_solve(cmcg_handle* h, const double* f, const double* g, double tol, double* u,
                cmcg_stats* stats);
 
+/* cmcg_solve started from a given field instead of zero or the run-up: on entry u (device,
+ * complex interleaved, N_p) holds the start field, for example a checkpointed iterate or the
+ * solution at a nearby frequency; CG starts from its periodic initial state (v0, v1) =
+ * (Re u, omega_hat Im u), the relation of step (6) read backwards.  On exit u holds the
+ * solution, as with cmcg_solve.  The tolerance stays relative to the zero guess's gradient
+ * (one extra gradient evaluation), so tol means the same as in a cold solve; the run-up
+ * option is not used.  CMCG_ERR_UNSUPPORTED for the first-order formulation and the
+ * do-nothing solver. */
+int cmcg_solve_warm(cmcg_handle* h, const double* f, const double* g, double tol, double* u,
+                    cmcg_stats* stats);
+
 /* cmcg_solve with HOST buffers: f_host, g_host (nullable) and u_host are host complex
  * double[N_p] arrays (pinned memory gives full copy speed).  Copies the inputs into the
  * workspace, solves, copies U back; all copies are on the handle's stream.  Needs a handle

@@ -38,7 +38,7 @@ ENGINE_NO_GRAPH = 1
 
 EXPORTED = (
     "cmcg_workspace_size", "cmcg_create", "cmcg_destroy", "cmcg_get_info", "cmcg_get_history", "cmcg_wave_period",
-    "cmcg_adjoint_period", "cmcg_riesz", "cmcg_solve", "cmcg_solve_host", "cmcg_status_string",
+    "cmcg_adjoint_period", "cmcg_riesz", "cmcg_solve", "cmcg_solve_warm", "cmcg_solve_host", "cmcg_status_string",
     "cmcg_engine_workspace_size", "cmcg_engine_create", "cmcg_engine_destroy", "cmcg_engine_submit",
     "cmcg_engine_tick", "cmcg_engine_result", "cmcg_engine_active", "cmcg_engine_info", "cmcg_engine_set_shape",
     "cmcg_engine_barrier_selftest", "cmcg_engine_cuda_error", "cmcg_fo_period", "cmcg_fo_adjoint_period",
@@ -119,6 +119,8 @@ def load(path: str = None):
     lib.cmcg_riesz.restype = I
     lib.cmcg_solve.argtypes = [P, P, P, D, P, C.POINTER(Stats)]
     lib.cmcg_solve.restype = I
+    lib.cmcg_solve_warm.argtypes = [P, P, P, D, P, C.POINTER(Stats)]
+    lib.cmcg_solve_warm.restype = I
     lib.cmcg_solve_host.argtypes = [P, P, P, D, P, C.POINTER(Stats)]
     lib.cmcg_solve_host.restype = I
     lib.cmcg_status_string.argtypes = [I]
@@ -260,6 +262,13 @@ def cmcg_riesz(h, rhs, s) -> int:
 def cmcg_solve(h, f, g, tol, u, stats: Optional[Stats] = None) -> int:
     st = stats if stats is not None else Stats()
     return _check(load().cmcg_solve(h, _ptr(f), _ptr(g), float(tol), _ptr(u), C.byref(st)), "cmcg_solve",
+                  allow_not_converged=True)
+
+
+def cmcg_solve_warm(h, f, g, tol, u, stats: Optional[Stats] = None) -> int:
+    """cmcg_solve started from the field in u (complex, device); u receives the solution."""
+    st = stats if stats is not None else Stats()
+    return _check(load().cmcg_solve_warm(h, _ptr(f), _ptr(g), float(tol), _ptr(u), C.byref(st)), "cmcg_solve_warm",
                   allow_not_converged=True)
 
 
@@ -416,13 +425,18 @@ class Solver:
         """Relative residual per CG iteration of the last solve."""
         return cmcg_get_history(self.handle)
 
-    def solve(self, f=None, g=None, tol=1e-6):
+    def solve(self, f=None, g=None, tol=1e-6, u0=None):
+        """Solve; u0 (optional) is a start field (a checkpointed iterate, a nearby solution)."""
         torch = self.torch
         f, g = self._dev(f, torch.complex128), self._dev(g, torch.complex128)
-        u = torch.empty(int(np.prod(self.shape)), dtype=torch.complex128, device=self.device)
+        if u0 is None:
+            u = torch.empty(int(np.prod(self.shape)), dtype=torch.complex128, device=self.device)
+        else:
+            u = self._dev(u0, torch.complex128).clone()
         st = Stats()
         self._after_caller()
-        code = cmcg_solve(self.handle, f, g, tol, u, st)
+        code = (cmcg_solve(self.handle, f, g, tol, u, st) if u0 is None
+                else cmcg_solve_warm(self.handle, f, g, tol, u, st))
         self._before_caller()
         out = st.as_dict()
         out["status"] = code

@@ -886,14 +886,24 @@ int gradient_norm(cmcg_handle* H, double* gamma) {
     return (*gamma == *gamma && *gamma >= 0) ? CMCG_OK : CMCG_ERR_DIVERGED;
 }
 
-// With a run-up: the zero-guess gradient norm (the tolerance reference), then the run-up
-// state into (w0, w1).  Without: (w0, w1) = 0 and gamma_zero = -1.
+// With a warm start (cmcg_solve_warm) or a run-up: the zero-guess gradient norm (the
+// tolerance reference), then the start state into (w0, w1): the given field's periodic
+// initial state, or the run-up state.  Otherwise: (w0, w1) = 0 and gamma_zero = -1.
 template <typename T>
 int initial_guess(cmcg_handle* H, double* w0, double* w1, double* gamma_zero, cmcg_stats* stats) {
     const long long n = H->g.np;
     launch_fill(w0, n, 0.0, H->st);
     launch_fill(w1, n, 0.0, H->st);
     *gamma_zero = -1.0;
+    if (H->warm) {
+        stats->runup_periods = 0;
+        int rc = gradient<T>(H, w0, w1, true, w0, w1, !inexact(H));
+        if (rc < 0) return rc;
+        rc = gradient_norm(H, gamma_zero);
+        if (rc != CMCG_OK) return rc;
+        launch_warm_start(n, H->warm, H->kap64, H->wh, w0, w1, H->st);
+        return cuda_status();
+    }
     const int ell = runup_count(H);
     stats->runup_periods = ell;
     if (ell <= 0) return CMCG_OK;
@@ -1549,6 +1559,15 @@ int cmcg_solve(cmcg_handle* h, const double* f, const double* g, double tol, dou
     cmcg_stats* st = stats ? stats : &local;
     const int rc = solve_prepared(h, tol, u, st, stats != nullptr);
     st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+int cmcg_solve_warm(cmcg_handle* h, const double* f, const double* g, double tol, double* u, cmcg_stats* stats) {
+    if (!h || !u || !(tol > 0)) return CMCG_ERR_INVALID_ARG;
+    if (h->first_order || (h->opt.flags & CMCG_FLAG_NO_CG)) return CMCG_ERR_UNSUPPORTED;
+    h->warm = u;  // read by the first gradient's set-up, before u is written
+    const int rc = cmcg_solve(h, f, g, tol, u, stats);
+    h->warm = nullptr;
     return rc;
 }
 

@@ -129,6 +129,9 @@ void launch_setup_coeffs(const Geom& g, const double* c, const unsigned char* us
                          cudaStream_t st);
 void launch_mask_copy(const Geom& g, const double* in, const double* kap64, double* out, cudaStream_t st);
 void launch_fill(double* p, long long n, double v, cudaStream_t st);
+// (w0, w1) = (Re u, wh Im u) on active nodes, 0 on Dirichlet nodes (kap64 = 0); u interleaved.
+void launch_warm_start(long long n, const double* u, const double* kap64, double wh, double* w0, double* w1,
+                       cudaStream_t st);
 
 // CG recurrences (Step (4) and Steps 5.3-5.8), scalars on the device.
 void launch_cg_init(long long n, const double* gt0, const double* gt1, const double* gh0, const double* gh1,

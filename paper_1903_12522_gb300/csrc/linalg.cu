@@ -98,6 +98,19 @@ __global__ void k_fill(double* p, long long n, double v) {
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) p[j] = v;
 }
 
+// Warm start: the periodic initial state of a time-harmonic field U (interleaved re, im) is
+// (v0, v1) = (Re U, omega_hat Im U), the fixed-point relation of step (6) read backwards;
+// Dirichlet nodes (kappa = 0) hold 0.
+__global__ void k_warm_start(long long n, const double* __restrict__ u, const double* __restrict__ kap64, double wh,
+                             double* __restrict__ w0, double* __restrict__ w1) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const bool act = kap64[j] != 0.0;
+        w0[j] = act ? u[2 * j] : 0.0;
+        w1[j] = act ? wh * u[2 * j + 1] : 0.0;
+    }
+}
+
 // ---- CG -----------------------------------------------------------------------------------
 // Step (4): r = d = g~, rhat = ghat (= E r), gamma = r . rhat = ||r||_E^2.
 __global__ void __launch_bounds__(kT) k_cg_init(long long n, const double* __restrict__ gt0,
@@ -476,6 +489,12 @@ void launch_mask_copy(const Geom& g, const double* in, const double* kap64, doub
 void launch_fill(double* p, long long n, double v, cudaStream_t st) {
     note_launch(1);
     k_fill<<<vec_blocks(n), kT, 0, st>>>(p, n, v);
+}
+
+void launch_warm_start(long long n, const double* u, const double* kap64, double wh, double* w0, double* w1,
+                       cudaStream_t st) {
+    note_launch(1);
+    k_warm_start<<<vec_blocks(n), kT, 0, st>>>(n, u, kap64, wh, w0, w1);
 }
 
 void launch_cg_init(long long n, const double* gt0, const double* gt1, const double* gh0, const double* gh1,

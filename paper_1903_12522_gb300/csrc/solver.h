@@ -35,6 +35,7 @@ struct cmcg_handle {
     float *mass32 = nullptr, *minv32 = nullptr;  // FP32 copies of M and M^-1 (FP32 / mixed)
     unsigned char* scol = nullptr;  // 3D: columns with source inside the grid (launch_source_columns)
     unsigned char* mask = nullptr;
+    const double* warm = nullptr;  // cmcg_solve_warm: the start field U (complex, interleaved) of this solve
     // wave buffers (sized for double; FP32 stepping uses the first half) + FP64 temp
     void *ya = nullptr, *yb = nullptr;
     double* tmp = nullptr;
