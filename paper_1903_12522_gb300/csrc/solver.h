@@ -5,6 +5,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "cmcg.h"
 #include "common.cuh"
@@ -171,4 +172,14 @@ int fo_period(cmcg_handle* H, const double* s0, bool src, double* out);
 int fo_adjoint(cmcg_handle* H, const double* y, double* out);
 
 }  // namespace detail
+// Named NVTX range over a host scope (a solve, a period, a Riesz map, an engine tick): the
+// profilers group the kernels launched inside it (ncu --nvtx --nvtx-include "cmcg/<name>/").
+// Without an attached tool the push and pop cost a branch each.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+
 }  // namespace cmcg
