@@ -443,7 +443,7 @@ void fwd_end(cmcg_handle* H, const PeriodBuffers& b, const double* w1, bool src,
 template <typename T>
 void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src, int mode, double* out0,
                     double* out1, bool w0f_ready) {
-    Range range("cmcg/forward period");
+    Range range("cmcg forward period");
     PeriodBuffers b = fwd_begin<T>(H, w0, w1, src, w0f_ready);
     fwd_steps<T>(H, b, src);
     fwd_end<T>(H, b, w1, src, mode, out0, out1);
@@ -517,7 +517,7 @@ void adj_end(cmcg_handle* H, const PeriodBuffers& b, const double* a, const doub
 template <typename T>
 void adjoint_period(cmcg_handle* H, const double* a, const double* bb, int mode, const double* d0, const double* d1,
                     double* o0, double* o1, double* gt1) {
-    Range range("cmcg/adjoint period");
+    Range range("cmcg adjoint period");
     PeriodBuffers b = adj_begin<T>(H, a, bb, mode);
     adj_steps<T>(H, b);
     adj_end<T>(H, b, a, bb, mode, d0, d1, o0, o1, gt1);
@@ -546,7 +546,7 @@ double ramp(double t, double ttr) {
 // return (y, y_t) at t = periods T in (w0, w1).
 template <typename T>
 void runup(cmcg_handle* H, int periods, double* w0, double* w1) {
-    Range range("cmcg/run-up");
+    Range range("cmcg run-up");
     const Geom& g = H->g;
     const int zc = step_zc(H);
     const int zce = g.dim == 3 ? kZcEnds : 1;
@@ -614,14 +614,13 @@ void vcycle(cmcg_handle* H, int l) {
 }
 
 void precondition(cmcg_handle* H, const double* r) {
-    Range range("cmcg/riesz V-cycle");
     launch_to_float(H->g.np, r, H->lv[0].b, H->st);
     vcycle(H, 0);
 }
 
 // K s = rhs (K singular without Dirichlet nodes: rhs projected, s with W-mean zero).
 int riesz_solve(cmcg_handle* H, const double* rhs, double* x, int* iters_out) {
-    Range range("cmcg/riesz MG-PCG");
+    Range range("cmcg riesz MG-PCG");
     const Geom& g = H->g;
     const long long n = g.np;
     const bool project = !H->has_dir;
@@ -687,6 +686,7 @@ bool inexact(const cmcg_handle* H) { return (H->opt.flags & CMCG_FLAG_INEXACT_RI
 // is singular), M^-1 rhat1; reduces gamma = z . rhat (and the Polak-Ribiere beta unless first).
 // lowp: inside a solve with FP32 periods, the pointwise work and the dots run in FP32.
 void apply_B(cmcg_handle* H, bool first, bool lowp, bool b_ready) {
+    Range range("cmcg riesz V-cycle");
     const Geom& g = H->g;
     Red red = H->red();
     const bool v32 = H->vec32_active;  // rhat, ghat and z are FP32 vectors
@@ -1114,7 +1114,7 @@ int filter_recover(cmcg_handle* h, double* u, cmcg_stats* st) {
 
 // Steps (1)-(6) with the source S already in the workspace; U into u (device).
 int solve_prepared(cmcg_handle* h, double tol, double* u, cmcg_stats* st, bool want_J) {
-    Range range("cmcg/solve");
+    Range range("cmcg solve");
     memset(st, 0, sizeof(*st));
     const long long launches0 = launch_count();
     h->step_s[0] = h->step_s[1] = 0.0;

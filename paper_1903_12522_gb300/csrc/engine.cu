@@ -443,7 +443,7 @@ int cmcg_engine_submit(cmcg_engine* e, cmcg_handle* h, const double* f, const do
 }
 
 int cmcg_engine_tick(cmcg_engine* e, int* finished, int max_finished, int* n_finished) {
-    cmcg::Range range("cmcg/engine tick");
+    cmcg::Range range("cmcg engine tick");
     if (!e || !n_finished || (max_finished > 0 && !finished)) return CMCG_ERR_INVALID_ARG;
     *n_finished = 0;
     std::vector<int> act;

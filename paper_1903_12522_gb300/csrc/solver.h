@@ -173,8 +173,10 @@ int fo_adjoint(cmcg_handle* H, const double* y, double* out);
 
 }  // namespace detail
 // Named NVTX range over a host scope (a solve, a period, a Riesz map, an engine tick): the
-// profilers group the kernels launched inside it (ncu --nvtx --nvtx-include "cmcg/<name>/").
-// Without an attached tool the push and pop cost a branch each.
+// profilers group the kernels launched inside it (ncu --nvtx --nvtx-include "cmcg <name>/";
+// no slash inside a name, which ncu reads as nesting).  Kernels of a captured iteration graph
+// launch at its replay, outside these host ranges.  Without an attached tool the push and pop
+// cost a branch each.
 struct Range {
     explicit Range(const char* name) { nvtxRangePushA(name); }
     ~Range() { nvtxRangePop(); }
