@@ -5,7 +5,7 @@ Workload (one "step" = one complete CMCG solve, Steps (1)-(6) of the CMCG Algori
   c(x) = 1 + 0.3 sin(2 pi x) sin(2 pi y) sin(2 pi z), omega = 2 pi * 17.92 (10 points per
   wavelength at c_min = 0.7), sound-soft sphere r = 0.1 at the centre, plane wave
   d = (1/2, 0, sqrt(3)/2) entering through first-order absorbing faces, dt = 0.4 h
-  (N = 36 steps per period).  The solve starts from the run-up of Sec. 4.3 (ceil(diam/(T c_min))
+  (N = 36 steps per period).  The solve starts from the run-up of Sec. 4.2.3 (ceil(diam/(T c_min))
   = 45 periods with ramped sources) and stops at a relative CG residual of 5e-10 with respect to
   the zero initial guess, the tolerance at which the solution is within 1e-6 of the plain FP64
   GPU solve.  Precision: FP32 leapfrog fields with FP64 CG vectors, inner products and energy
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--riesz", default="vcycle", choices=["vcycle", "exact"])
     ap.add_argument("--max-iter", type=int, default=0, help="CG iteration cap (profiling runs)")
     ap.add_argument("--runup", type=int, default=-4,
-                    help="run-up periods (Sec. 4.3); -k = k domain crossings at c_min, ceil(k diam/(T c_min))")
+                    help="run-up periods (Sec. 4.2.3); -k = k domain crossings at c_min, ceil(k diam/(T c_min))")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--no-error-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -110,7 +110,7 @@ def method_config(args):
         "riesz": {"vcycle": "one FP32 multigrid V-cycle per CG iteration (flexible CG)",
                   "exact": "FP64 MG-PCG to 1e-12"}[args.riesz],
         "runup_periods": args.runup,
-        "runup": (f"{-args.runup} domain crossings at c_min, ramped sources (Sec. 4.3)" if args.runup < 0
+        "runup": (f"{-args.runup} domain crossings at c_min, ramped sources (Sec. 4.2.3)" if args.runup < 0
                   else f"{args.runup} periods" if args.runup > 0 else "none"),
         "l2_kappa": "off" if getattr(args, "no_l2_kappa", False) else
                     "FP32 kappa kept in an L2 set-aside across steps (CMCG_FLAG_L2_KAPPA)",

@@ -14,7 +14,7 @@
  *     w = 1/2 on the two end nodes of an axis, 1 elsewhere; stiffness K = W (-Lap_h) with
  *     mirror (Neumann) ghosts, 2nd order (5/7-point) or 4th order (9/13-point, even
  *     reflection); M = diag(W/c^2); absorbing faces add B = diag(A/c), A = lumped face area.
- *   - leapfrog in time with the absorbing term centred (Sec. 4.4.1: explicit, T/dt an
+ *   - leapfrog in time with the absorbing term centred (Sec. 4.3.1: explicit, T/dt an
  *     integer): N = ceil(T/dt_target - 1e-9) steps of dt = T/N per period.
  *   - discrete time-harmonic solution: (K - wt^2 M - i wh B) U = W f + A g with
  *     wt = (2/dt) sin(omega dt/2), wh = sin(omega dt)/dt; returned U = v0 + i v1 / wh
@@ -81,7 +81,7 @@ extern "C" {
                                comparator the paper uses to show why controllability is needed:
                                integrate the forced wave equation from rest for runup_periods = l
                                periods (or the automatic count for -k; 0 is CMCG_ERR_INVALID_ARG)
-                               with the sources ramped by theta_tr over [0, l T] (Sec. 4.3) and
+                               with the sources ramped by theta_tr over [0, l T] (Sec. 4.2.3) and
                                recover U from the state at t = l T as in step (6), without CG.
                                Near trapped modes (nonconvex obstacles) U converges very slowly
                                in l; stats J_final is the periodicity misfit of that state. */
@@ -97,8 +97,8 @@ extern "C" {
                                CMCG_FP64, CMCG_FP32 and CMCG_MIXED (FP64 defect correction around
                                FP32 CG, as for the second-order scheme; with FP32 periods use
                                CMCG_FLAG_FILTER: rounding excites the nearly periodic spurious
-                               modes of Sec. 3.3, which Eq. mix_solution keeps and the filter
-                               removes), order 2, and the run-up of Sec. 4.3 (runup_periods);
+                               modes of Sec. 3.2, which Eq. mix_solution keeps and the filter
+                               removes), order 2, and the run-up of Sec. 4.2.3 (runup_periods);
                                order 4, CMCG_FLAG_INEXACT_RIESZ and CMCG_FLAG_NO_CG are
                                CMCG_ERR_UNSUPPORTED.  cmcg_wave_period, cmcg_adjoint_period and
                                cmcg_riesz return CMCG_ERR_UNSUPPORTED on such a handle; use
@@ -145,7 +145,7 @@ typedef struct {
     double inner_tol;       /* CMCG_MIXED: relative tolerance of each inner FP32 solve
                                (0 = 1e-3)                                                 */
     int flags;              /* CMCG_FLAG_* bits; other bits must be 0                      */
-    int runup_periods;      /* initial run-up of Sec. 4.3: integrate the wave equation from rest
+    int runup_periods;      /* initial run-up of Sec. 4.2.3: integrate the wave equation from rest
                                for this many periods with the sources ramped in by
                                theta(t) = (2 - sin(pi t / (2 t_tr))) sin(pi t / (2 t_tr)),
                                t_tr = runup_periods T, and start CG from the final state.
@@ -222,7 +222,7 @@ size_t cmcg_workspace_size(const cmcg_grid* grid, const cmcg_options* opts);
  * cudaStream_t (NULL = default stream).  Validates sizes and the CFL condition
  * dt^2 c_max^2 rho < 4 (rho = 4d/h^2, 2nd order; 16d/(3h^2), 4th order) and returns
  * CMCG_ERR_CFL if violated.  4th order with Dirichlet nodes is CMCG_ERR_UNSUPPORTED.
- * Sec. 2.1 (problem), Sec. 4.4.1 (leapfrog, mass lumping, T/dt integer). */
+ * Sec. 2.1 (problem), Sec. 4.3.1 (leapfrog, mass lumping, T/dt integer). */
 int cmcg_create(const cmcg_grid* grid, const double* c, double omega, const cmcg_bc* bc,
                 const cmcg_options* opts, void* workspace, size_t ws_bytes, void* stream,
                 cmcg_handle** out);

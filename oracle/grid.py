@@ -1,7 +1,7 @@
 """Oracle discretisation (test infrastructure only; see oracle/__init__.py).
 
-The paper discretises in space with mass-lumped P1/P2 finite elements (Sec. 4.1, Sec. 4.4)
-and in time with leapfrog and T/dt an integer (Sec. 4.4.1).  On a Cartesian grid the
+The paper discretises in space with mass-lumped P1/P2 finite elements (Sec. 4.1, Sec. 4.3)
+and in time with leapfrog and T/dt an integer (Sec. 4.3.1).  On a Cartesian grid the
 mass-lumped Q1 element is the vertex-centred finite-difference scheme written out here:
 
   nodes         x_j = j h, j in {0..n}^d
@@ -18,7 +18,7 @@ mass-lumped Q1 element is the vertex-centred finite-difference scheme written ou
   Dirichlet     nodes on Dirichlet faces or in the obstacle mask are held at 0 and dropped from
                 every vector (homogeneous g_D only); their links still enter K rows of active
                 neighbours through y_j - 0.
-  time          T = 2 pi / omega, N = ceil(T/dt_target - 1e-9), dt = T/N (T/dt integer, Sec. 4.4.1)
+  time          T = 2 pi / omega, N = ceil(T/dt_target - 1e-9), dt = T/N (T/dt integer, Sec. 4.3.1)
   CFL           dt^2 max c^2 rho < 4 with rho = 4d/h^2 (2nd order) or 16d/(3h^2) (4th order)
 
 Parity: K is pinned to the closed-form Neumann eigenpairs (cosine modes, eigenvalues

@@ -1,7 +1,7 @@
 """Oracle wave solver (test infrastructure only; see oracle/__init__.py).
 
 Semi-discrete wave equation of Eq. WE after mass lumping:  M y'' + B y' + K y = F(t), with
-initial data y(0) = v0, y'(0) = v1 (Eq. WE_INIT).  Time stepping: leapfrog (LF, Sec. 4.4.1)
+initial data y(0) = v0, y'(0) = v1 (Eq. WE_INIT).  Time stepping: leapfrog (LF, Sec. 4.3.1)
 with the absorbing term centred in time, run here in its velocity-Verlet (kick-drift-kick)
 form, one step Phi: (y^n, v^n) -> (y^{n+1}, v^{n+1}):
 
@@ -56,7 +56,7 @@ def period(dz: Discretization, y0, v0, F_hat=None):
 
 
 def theta_tr(t: float, t_tr: float) -> float:
-    """Smooth switch-on of the sources for the initial run-up (Sec. 4.3, Eq. transientfunction):
+    """Smooth switch-on of the sources for the initial run-up (Sec. 4.2.3, Eq. transientfunction):
     with s = sin(pi t / (2 t_tr)), theta = (2 - s) s on [0, t_tr] and 1 afterwards.  It rises
     from 0 at t = 0 to 1 at t = t_tr, where its slope vanishes."""
     if t >= t_tr:
@@ -68,7 +68,7 @@ def theta_tr(t: float, t_tr: float) -> float:
 def long_time(dz: Discretization, F_hat, periods: int, smooth: bool = True, trajectory: bool = False):
     """The forced wave equation (Eq. WE) integrated from rest, y(0) = y'(0) = 0, up to
     t = periods * T: the time-dependent solution w(., t) whose state at t = l T the
-    do-nothing solver of Sec. 4.2 reads (Eq. AP_SOLUTION) and the initial run-up of Sec. 4.3
+    do-nothing solver of Sec. 4.2 reads (Eq. AP_SOLUTION) and the initial run-up of Sec. 4.2.3
     hands to CMCG.  With smooth=True the load is theta_tr(t) F(t), t_tr = periods * T.
     Returns (y, v) at t = periods * T, and with trajectory=True also the list of every y^n."""
     total = periods * dz.N

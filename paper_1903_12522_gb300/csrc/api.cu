@@ -523,7 +523,7 @@ void adjoint_period(cmcg_handle* H, const double* a, const double* bb, int mode,
     adj_end<T>(H, b, a, bb, mode, d0, d1, o0, o1, gt1);
 }
 
-// ---- initial run-up (Sec. 4.3) ---------------------------------------------------------------
+// ---- initial run-up (Sec. 4.2.3) ---------------------------------------------------------------
 // Run-up periods: runup_periods itself when positive; -k = the periods waves at the slowest
 // speed need to cross the domain's diagonal k times, ceil(k diam / (T c_min)).
 int runup_count(const cmcg_handle* H) {

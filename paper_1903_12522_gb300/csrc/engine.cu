@@ -28,7 +28,7 @@ using namespace cmcg::detail;
 
 namespace {
 
-// U_RUNUP: the initial run-up (Sec. 4.3) of a mixed-precision slot, between its first outer
+// U_RUNUP: the initial run-up (Sec. 4.2.3) of a mixed-precision slot, between its first outer
 // unit (the zero guess, which sets the tolerance reference) and its second.
 enum Unit { U_FREE = 0, U_INIT32, U_OUTER, U_INNER, U_DONE, U_RUNUP };
 

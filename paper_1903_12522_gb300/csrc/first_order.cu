@@ -519,7 +519,7 @@ int fo_cg_start(cmcg_handle* H, double* x) {
     return sync_read(H) == CMCG_OK ? CMCG_OK : CMCG_ERR_CUDA;
 }
 
-// Initial run-up (Sec. 4.3) on the first-order state: the forced staggered leapfrog from rest for
+// Initial run-up (Sec. 4.2.3) on the first-order state: the forced staggered leapfrog from rest for
 // `periods` periods with the sources ramped in by theta_tr over [0, periods T]; the state at
 // t = periods T goes to out (FP64).
 template <typename T>

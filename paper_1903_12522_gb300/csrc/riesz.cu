@@ -1,6 +1,6 @@
 // Riesz map of Eq. CMCG_PRECONDITIONIER: K s = rhs with K = W (-Lap_h) (the discrete
 // (grad s, grad phi)), solved matrix-free on the GPU.  The paper solves this SPD,
-// omega-independent problem with a two-level Schwarz method (Sec. 4.4); here it is FP64
+// omega-independent problem with a two-level Schwarz method (Sec. 4.3); here it is FP64
 // flexible PCG whose preconditioner is one geometric multigrid V-cycle in FP32:
 //   - vertex-centred coarsening n -> ceil(n/2) per axis (nested 2:1 for even n, general
 //     linear interpolation for odd n), rediscretised K on each level, Dirichlet mask taken

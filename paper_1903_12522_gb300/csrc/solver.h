@@ -152,7 +152,7 @@ void forward_period(cmcg_handle* H, const double* w0, const double* w1, bool src
 // lambda fields.  Synchronises the stream.
 int recover(cmcg_handle* h, double* u, cmcg_stats* st);
 int timing_begin(cmcg_handle* H, bool fp32, int steps);
-// Run-up (Sec. 4.3): its number of periods, and the source ramp theta_tr(t) over [0, ttr].
+// Run-up (Sec. 4.2.3): its number of periods, and the source ramp theta_tr(t) over [0, ttr].
 int runup_count(const cmcg_handle* H);
 // The run-up itself: (y, y_t) at t = periods T into (w0, w1).
 template <typename T>

@@ -1,5 +1,5 @@
 // Two leapfrog steps per launch (temporal blocking, depth 2): 3D 7-point, FP32, homogeneous
-// steps of Eq. WE (Sec. 4.4.1), (A = y^{n-1}, B = y^n) -> (C = y^{n+1}, D = y^{n+2}).
+// steps of Eq. WE (Sec. 4.3.1), (A = y^{n-1}, B = y^n) -> (C = y^{n+1}, D = y^{n+2}).
 //
 // A block owns the interior tile [tx TX, tx TX + TX) x [ty TY, ty TY + TY) of every plane of
 // its z-chunk [z0, z1) and marches z.  Its columns are the tile plus a 2-node halo, at most

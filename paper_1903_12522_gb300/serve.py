@@ -345,7 +345,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--runup", type=int, default=-2,
-                    help="run-up periods per solve (Sec. 4.3; -k = k domain crossings; mixed precision only)")
+                    help="run-up periods per solve (Sec. 4.2.3; -k = k domain crossings; mixed precision only)")
     ap.add_argument("--max-3d", type=int, default=256)
     ap.add_argument("--fp64-tol", type=float, default=5e-10, help="batch-compare: tolerance of the plain FP64 solves")
     ap.add_argument("--fp64-tuned-tol", type=float, default=1e-10,

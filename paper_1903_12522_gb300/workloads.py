@@ -13,7 +13,7 @@ DIRICHLET=2.
 The problem statement these workloads instantiate is the Helmholtz boundary-value problem
 of Sec. 2.1 (Eq. HE): -Lap u - k^2 u = f, du/dn - i k u = g_S on the absorbing part, with
 k = omega/c and time convention exp(-i omega t).  The synthetic inputs stand in for the
-paper's Marmousi model and obstacle meshes (Sec. 4.4), which are not available here.
+paper's Marmousi model and obstacle meshes (Sec. 4.3), which are not available here.
 """
 from __future__ import annotations
 
@@ -232,7 +232,7 @@ def square_obstacle_2d(n: int = 128, cavity: bool = False, wavelengths: float = 
 
 
 def neumann_box_2d(n: int = 64, dt_frac: float = 0.5) -> Workload:
-    """The physically bounded domain of Sec. 3.4 lifted to the unit square: homogeneous Neumann
+    """The physically bounded domain of Sec. 3.5 lifted to the unit square: homogeneous Neumann
     on all four sides, c = 1, k = omega = pi/4, and the source f = -u'' - k^2 u of the exact
     solution u(x, y) = 16 x^2 (x - 1)^2 (constant in y, zero normal derivative on every side).
     (4k)^2 = pi^2 is a Neumann eigenvalue: the wave equation has a mode of period T/4."""

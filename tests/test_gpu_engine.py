@@ -124,7 +124,7 @@ def test_graph_and_plain_launches_agree():
 
 
 def test_runup_in_the_engine():
-    # Sec. 4.3 inside the engine (mixed precision): the zero guess sets the tolerance reference,
+    # Sec. 4.2.3 inside the engine (mixed precision): the zero guess sets the tolerance reference,
     # then each slot runs its ramped run-up as one unit; same fixed point, fewer CG iterations
     ws = mix()
     out0, _ = run_engine(ws, cmcg.MIXED, 1e-9)

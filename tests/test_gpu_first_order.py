@@ -132,7 +132,7 @@ def test_fo_dot_product_on_device(case):
 def test_fo_solve_matches_second_order_direct(case, precision, flags, tol, bound):
     # the first-order fixed point is the second-order scheme's discrete Helmholtz solution.
     # Recovery by Eq. mix_solution reads the state at t = 0, which keeps whatever part of the
-    # nearly periodic spurious modes (Sec. 3.3) the CG has not removed; the filter removes
+    # nearly periodic spurious modes (Sec. 3.2) the CG has not removed; the filter removes
     # them.  On the 25^3 sphere at tol 1e-12 the oracle's own first-order CG gives 1.3e-8 by
     # Eq. mix_solution and 3e-13 by the filter, hence the looser FP64 bound for the former.
     # With FP32 periods only the filter is tested: rounding excites the nearly periodic
@@ -172,7 +172,7 @@ def test_fo_iterations_match_oracle(name):
                                                        (cmcg.MIXED, cmcg.FLAG_FILTER, 1e-10, 1e-8)])
 @pytest.mark.parametrize("runup", [-1, -4])
 def test_fo_runup_keeps_the_fixed_point_and_saves_iterations(precision, flags, tol, bound, runup):
-    # Sec. 4.3 on the first-order state: the ramped run-up gives the initial guess, the
+    # Sec. 4.2.3 on the first-order state: the ramped run-up gives the initial guess, the
     # tolerance stays referenced to the zero guess, so the answer's accuracy is unchanged
     w = wl.sphere_3d(n=24)
     dz = Discretization(w.n, w.h, w.c, w.omega, w.faces, w.dt_target, mask=w.mask)

@@ -258,7 +258,7 @@ def test_inexact_riesz_solve_matches_direct(case, precision, tol, bound):
 @pytest.mark.parametrize("precision,flags,tol,bound", [(cmcg.FP64, 0, 1e-12, 1e-9),
                                                        (cmcg.MIXED, cmcg.FLAG_INEXACT_RIESZ, 1e-9, 1e-6)])
 def test_runup_keeps_the_fixed_point_and_saves_iterations(precision, flags, tol, bound, runup):
-    # Sec. 4.3: a run-up from rest with ramped sources gives the initial guess; the tolerance
+    # Sec. 4.2.3: a run-up from rest with ramped sources gives the initial guess; the tolerance
     # refers to the zero-guess residual, so the answer's accuracy is unchanged
     w = wl.sphere_3d(n=24)
     dz = dz_of(w)
@@ -303,7 +303,7 @@ def test_pure_neumann_after_runup(flags):
 @pytest.mark.parametrize("precision,bound", [(cmcg.FP64, 1e-11), (cmcg.FP32, 1e-4)])
 def test_do_nothing_matches_oracle_long_time(case, precision, bound):
     # Sec. 4.2 (Eq. AP_SOLUTION): l = 3 periods of the forced wave equation from rest with the
-    # ramped sources of Sec. 4.3, recovered as in step (6); no CG
+    # ramped sources of Sec. 4.2.3, recovered as in step (6); no CG
     name, w, dz = case
     F = dz.load(w.f, w.g)
     y, v = wave.long_time(dz, F, 3)

@@ -271,7 +271,7 @@ def test_lambda_real_and_filter_agrees():
     assert rel_err(dz, u_filter, res.u) <= 1e-10
 
 
-# P13: the physically bounded domain of Sec. 3.4 (pure Neumann, k = pi/4, exact solution
+# P13: the physically bounded domain of Sec. 3.5 (pure Neumann, k = pi/4, exact solution
 # u = 16 x^2 (x - 1)^2) lifted to 2D.  (a) The discrete solution converges to u at order 2.
 # (b) Started from a run-up, the minimiser carries a linear growth eta t (the constant mode
 # has no restoring force): the filter alone is then off by a constant, and the discrete
@@ -340,7 +340,7 @@ def test_paper_recovery_converges_second_order():
 
 
 # ----------------------------------------------------------------------------------------
-# P10: the smooth switch-on of Sec. 4.3 against its closed form: theta(0) = 0, theta(t_tr) = 1
+# P10: the smooth switch-on of Sec. 4.2.3 against its closed form: theta(0) = 0, theta(t_tr) = 1
 # with zero slope there, theta'(0) = pi / t_tr (derivative of (2 - s) s with
 # s' = pi / (2 t_tr)), strictly increasing on (0, t_tr) and 1 afterwards.  Dropping the
 # (2 - s) factor breaks the slope at t_tr; a wrong argument scale breaks theta(t_tr).
@@ -384,7 +384,7 @@ def test_long_time_converges_to_direct(faces):
     assert np.allclose(v, q, rtol=0, atol=1e-13 * np.abs(q).max())
 
 
-# P12: the ramped run-up trajectory satisfies the three-level leapfrog scheme of Sec. 4.4.1
+# P12: the ramped run-up trajectory satisfies the three-level leapfrog scheme of Sec. 4.3.1
 # (the form the oracle does not run) with the load theta_tr(t_n) F^n at every level n:
 #   M (y^{n+1} - 2 y^n + y^{n-1}) / dt^2 + B (y^{n+1} - y^{n-1}) / (2 dt) + K y^n = theta_n F^n.
 # A ramp taken at the wrong time level leaves a residual of the size of theta's increment.
@@ -485,10 +485,10 @@ def test_first_order_matches_second_order_direct(case):
     assert res.J_history[-1] <= 1e-20 * max(res.J_history[0], 1e-300)
 
 
-# P18: pure Neumann (Sec. 3.4 lifted to 2D): from a run-up-like start with a constant velocity
+# P18: pure Neumann (Sec. 3.5 lifted to 2D): from a run-up-like start with a constant velocity
 # eta (a steady state of the homogeneous first-order system) the minimiser keeps eta; the
 # recovery of Eq. mix_solution is then off by i eta / wt, while the filter removes it
-# (the proposition of Sec. 3.3).
+# (the proposition of Sec. 3.2).
 def test_first_order_pure_neumann_needs_the_filter():
     w = wl.neumann_box_2d(12)
     dz = make(w)
