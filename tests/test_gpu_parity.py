@@ -417,6 +417,39 @@ def test_warm_start_resumes_a_solve(name, precision, flags, tol, bound):
     assert wrel(dz, u4.cpu().numpy(), U) <= bound
 
 
+@pytest.mark.parametrize("precision,tol,bound", [(cmcg.FP64, 1e-13, 1e-10), (cmcg.MIXED, 1e-10, 1e-6)])
+def test_paper_example_sec4_1_on_the_gpu(precision, tol, bound):
+    # the printed example of Sec. 4.1 (tests/golden/sec4_1_semidiscrete_example.txt): u = e^{ikx},
+    # omega = k = 6 pi, on the unit square (256 x 256 intervals) with absorbing x-faces (the
+    # exact datum at x = 0) and Neumann y-faces, where it stays constant in y.  The GPU solve matches the direct solve, and its distance to the printed
+    # solution is the discretisation error the oracle has.
+    import os
+    fx = {}
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                  "sec4_1_semidiscrete_example.txt")):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            key, value = (x.strip() for x in line.split("=", 1))
+            fx[key] = value
+    k = float(fx["k_over_pi"]) * math.pi
+    m = 256
+    n, h = (m, m), 1.0 / m
+    faces = (ABC, ABC, NEU, NEU, NEU, NEU)
+    g = wl.plane_wave_boundary_datum(n, h, k, 1.0, (1.0, 0.0), faces)
+    w = wl.Workload(name="sec4_1_square", n=n, h=h, c=np.ones((m + 1, m + 1)), omega=k, faces=faces,
+                    dt_target=0.4 * h, g=g)
+    dz = dz_of(w)
+    U = direct.solve(dz, dz.load(None, g))
+    s = solver_of(w, precision, flags=cmcg.FLAG_INEXACT_RIESZ if precision == cmcg.MIXED else 0)
+    u, st = s.solve(None, g, tol=tol)
+    assert st["status"] == cmcg.OK, st
+    ug = u.cpu().numpy()
+    assert wrel(dz, ug, U) <= bound, st
+    exact = np.exp(1j * k * wl.coords(n, h)[0]) * np.ones(dz.shape)
+    e_gpu, e_oracle = wrel(dz, ug, exact), wrel(dz, U, exact)
+    assert abs(e_gpu - e_oracle) <= 1e-3 * e_oracle + bound and e_oracle < 3e-3, (e_gpu, e_oracle)
+
+
 def test_solve_host_matches_device():
     w = wl.gaussian_2d(n=48)
     s = solver_of(w, flags=cmcg.FLAG_HOST_IO)
