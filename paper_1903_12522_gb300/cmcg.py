@@ -358,7 +358,8 @@ class Solver:
             return None
         if isinstance(a, torch.Tensor):
             return a.to(device=self.device, dtype=dtype).contiguous().reshape(-1)
-        return torch.as_tensor(np.ascontiguousarray(a)).to(device=self.device, dtype=dtype).reshape(-1)
+        # writeable C-contiguous host array (torch does not take read-only numpy buffers)
+        return torch.as_tensor(np.require(a, requirements=["C", "W"])).to(device=self.device, dtype=dtype).reshape(-1)
 
     def close(self):
         if getattr(self, "handle", None) is not None:
