@@ -85,6 +85,7 @@ def test_create_rejects_null_arguments_without_a_gpu(lib):
     code = lib.cmcg_create(C.byref(g), None, 1.0, C.byref(bc), C.byref(o), None, 0, None, C.byref(h))
     assert code == cmcg.ERR_INVALID_ARG and not h.value
     assert lib.cmcg_solve(None, None, None, 1e-6, None, None) == cmcg.ERR_INVALID_ARG
+    assert lib.cmcg_solve_warm(None, None, None, 1e-6, None, None) == cmcg.ERR_INVALID_ARG
     assert lib.cmcg_wave_period(None, None, None, None, None, None, None) == cmcg.ERR_INVALID_ARG
     assert lib.cmcg_destroy(None) == cmcg.ERR_INVALID_ARG
 
@@ -93,6 +94,16 @@ def test_status_strings(lib):
     assert cmcg.cmcg_status_string(cmcg.OK) == "ok"
     assert "CFL" in cmcg.cmcg_status_string(cmcg.ERR_CFL)
     assert cmcg.cmcg_status_string(12345) == "unknown status"
+
+
+def test_check_status_reports_no_checks_in_the_normal_build(lib):
+    # the normal build compiles no bounds checks: zeros and ERR_UNSUPPORTED (the call only
+    # synchronises the device, which a host without a GPU answers with an error code)
+    c, si, ix = C.c_longlong(7), C.c_longlong(7), C.c_longlong(7)
+    code = lib.cmcg_check_status(C.byref(c), C.byref(si), C.byref(ix))
+    assert code in (cmcg.ERR_UNSUPPORTED, cmcg.ERR_CUDA)
+    if code == cmcg.ERR_UNSUPPORTED:
+        assert c.value == 0 and si.value == -1 and ix.value == 0
 
 
 def test_missing_library_fails_loudly(tmp_path):
