@@ -572,6 +572,27 @@ void runup(cmcg_handle* H, int periods, double* w0, double* w1) {
     H->periods += periods;
 }
 
+// The FP32 run-up split around a step loop that runs elsewhere (the engine's batched
+// kernel): the start sets both wave buffers to rest (y^n in yb, y^{n-1} in ya at step 1); the
+// finish reads the state after periods N - 1 steps and writes (y, y_t) at t = periods T.
+void runup_start_f32(cmcg_handle* H) {
+    cudaMemsetAsync(H->yb, 0, sizeof(float) * H->g.np, H->st);
+    cudaMemsetAsync(H->ya, 0, sizeof(float) * H->g.np, H->st);
+}
+
+void runup_finish_f32(cmcg_handle* H, int periods, double* w0, double* w1) {
+    const Geom& g = H->g;
+    const long long total = (long long)periods * H->N;
+    const bool odd = ((total - 1) & 1) != 0;  // the buffers swap roles after every step
+    const float* cur = (const float*)(odd ? H->ya : H->yb);
+    const float* prev = (const float*)(odd ? H->yb : H->ya);
+    const double ttr = periods * H->T, tN = total * H->dt;
+    launch_end<float>(g, H->order, 1, cur, prev, (const float*)nullptr, nullptr, H->kap32, step_mass<float>(H), H->S,
+                      ramp(tN, ttr) * cos(H->omega * tN), ramp(tN, ttr) * sin(H->omega * tN), w0, w1, H->red(),
+                      H->dt, g.dim == 3 ? kZcEnds : 1, H->st);
+    H->periods += periods;
+}
+
 // ---- Riesz map: FP64 flexible PCG with a FP32 multigrid V-cycle --------------------------
 float jacobi_omega(const Geom& g) { return g.dim == 3 ? 6.0f / 7.0f : 0.8f; }
 

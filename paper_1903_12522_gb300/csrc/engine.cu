@@ -55,12 +55,13 @@ struct cmcg_engine {
     int max_slots = 0;
     std::vector<EngineSlot> slots;
     // device
-    BatchItem* items_dev = nullptr;  // [2 * max_slots]: forward items, then adjoint items
+    BatchItem* items_dev = nullptr;  // [3 * max_slots]: forward, adjoint, then run-up items
     unsigned* bar = nullptr;         // barrier counter + generation
     int* err = nullptr;              // barrier time-out flag
     int* err_host = nullptr;         // pinned
     int grid = 0;      // blocks of the batched step kernel (at most the co-resident maximum)
     int grid_max = 0;  // co-resident maximum
+    int grid_forced = 0;  // blocks of the batched run-up kernel (its co-resident maximum)
     int zc3 = kZcStep3D;  // z-planes per work item of 3D grids in the batched kernel
     bool use_graph = true;
     // graph cache
@@ -88,7 +89,7 @@ size_t engine_layout(cmcg_engine* e, int max_slots, char* base) {
         off += bytes;
         return p;
     };
-    char* items = take(sizeof(BatchItem) * 2 * (size_t)max_slots);
+    char* items = take(sizeof(BatchItem) * 3 * (size_t)max_slots);
     char* bar = take(sizeof(unsigned) * 4);
     char* err = take(sizeof(int) * 4);
     if (e) {
@@ -114,6 +115,20 @@ BatchItem make_item(cmcg_handle* h, const PeriodBuffers& b, bool adjoint, int zc
     it.vec4 = h->g.dim == 2 && h->order == 2 && step_vec4_ok(h->g, it.buf0, it.buf1, it.kap);
     if (it.vec4) it.blocks_xy = (int)((((h->g.np + 3) >> 2) + 255) / 256);
     it.blocks = it.blocks_xy * ((h->g.sz + it.zc - 1) / it.zc);
+    return it;
+}
+
+// The run-up of a slot as one item of the batched run-up kernel: the forced ramped steps
+// n = 1 .. periods N - 1 from rest (step n = s + 1 of the item), y^1 in yb and y^0 in ya at
+// the first step, as in the one-solve run-up.
+BatchItem make_runup_item(cmcg_handle* h, int periods, int zc3) {
+    PeriodBuffers b{h->yb, h->ya, nullptr};
+    BatchItem it = make_item(h, b, false, zc3);
+    it.nsteps = (int)((long long)periods * h->N - 1);
+    it.S = h->S32;
+    it.scol = h->scol;
+    it.steps_per_period = h->N;
+    it.runup_steps = periods * h->N;
     return it;
 }
 
@@ -165,7 +180,7 @@ void on_side(cmcg_engine* e, cmcg_handle* h, int k, F f) {
 cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
     cudaMemsetAsync(e->err, 0, sizeof(int), e->st);
     fork_sides(e);
-    std::vector<int> inner;
+    std::vector<int> inner, runups;
     int lane = 0;
     for (int s : act) {
         EngineSlot& sl = e->slots[s];
@@ -187,11 +202,33 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
                 reset_direction(h);
             });
         } else if (sl.unit == U_RUNUP) {
-            const int periods = sl.runup;
-            on_side(e, sl.h, lane++, [periods](cmcg_handle* h) { runup<float>(h, periods, h->wo0, h->wo1); });
+            runups.push_back(s);
+            on_side(e, sl.h, lane++, [](cmcg_handle* h) { runup_start_f32(h); });
         } else if (sl.unit == U_INNER) {
             inner.push_back(s);
         }
+    }
+    if (!runups.empty()) {
+        // every run-up slot's forced steps in one cooperative launch (items uploaded before the
+        // tick), then each slot's end state into its FP64 iterate
+        const int r = (int)runups.size();
+        int total = 0, maxs = 0;
+        for (int s : runups) {
+            const BatchItem it = make_runup_item(e->slots[s].h, e->slots[s].runup, e->zc3);
+            total += it.blocks;
+            maxs = std::max(maxs, it.nsteps);
+        }
+        join_sides(e);
+        cudaError_t ce = launch_batch_steps(e->items_dev + 2 * e->max_slots, r, total, maxs, e->bar, e->err,
+                                            e->grid_forced, e->st, true);
+        if (ce != cudaSuccess) return ce;
+        fork_sides(e);
+        for (int i = 0; i < r; ++i) {
+            const int periods = e->slots[runups[i]].runup;
+            on_side(e, e->slots[runups[i]].h, lane + i,
+                    [periods](cmcg_handle* h) { runup_finish_f32(h, periods, h->wo0, h->wo1); });
+        }
+        lane += r;
     }
     if (!inner.empty()) {
         const int m = (int)inner.size();
@@ -258,14 +295,22 @@ cudaError_t enqueue_tick(cmcg_engine* e, const std::vector<int>& act) {
     return cudaGetLastError();
 }
 
-// Batch descriptors of the INNER slots (forward and adjoint): the buffer roles at step 0 are
-// fixed per handle (fwd: cur = yb, prev = ya; adjoint: cur = ya, prev = yb), so they can be
-// uploaded before the tick and stay valid across graph replays.
+// Batch descriptors of the INNER slots (forward and adjoint) and of the RUNUP slots: the
+// buffer roles at step 0 are fixed per handle (fwd and run-up: cur = yb, prev = ya; adjoint:
+// cur = ya, prev = yb), so they can be uploaded before the tick and stay valid across graph
+// replays.
 void upload_items(cmcg_engine* e, const std::vector<int>& act) {
-    std::vector<BatchItem> items(2 * (size_t)e->max_slots);
-    int m = 0, tf = 0, ta = 0;
+    std::vector<BatchItem> items(3 * (size_t)e->max_slots);
+    int m = 0, tf = 0, ta = 0, r = 0, tr = 0;
     for (int s : act) {
         EngineSlot& sl = e->slots[s];
+        if (sl.unit == U_RUNUP) {
+            BatchItem& it = items[2 * (size_t)e->max_slots + r++];
+            it = make_runup_item(sl.h, sl.runup, e->zc3);
+            it.offset = tr;
+            tr += it.blocks;
+            continue;
+        }
         if (sl.unit != U_INNER) continue;
         cmcg_handle* h = sl.h;
         PeriodBuffers f{h->yb, h->ya, nullptr}, a{h->ya, h->yb, nullptr};
@@ -277,7 +322,7 @@ void upload_items(cmcg_engine* e, const std::vector<int>& act) {
         ta += items[e->max_slots + m].blocks;
         ++m;
     }
-    cudaMemcpyAsync(e->items_dev, items.data(), sizeof(BatchItem) * 2 * (size_t)e->max_slots, cudaMemcpyHostToDevice,
+    cudaMemcpyAsync(e->items_dev, items.data(), sizeof(BatchItem) * 3 * (size_t)e->max_slots, cudaMemcpyHostToDevice,
                     e->st);
     cudaStreamSynchronize(e->st);
 }
@@ -346,13 +391,14 @@ int cmcg_engine_create(int max_slots, void* workspace, size_t ws_bytes, void* st
     }
     cudaMemsetAsync(e->bar, 0, sizeof(unsigned) * 4, e->st);
     cudaMemsetAsync(e->err, 0, sizeof(int) * 4, e->st);
-    e->grid = e->grid_max = batch_steps_max_blocks();
+    e->grid = e->grid_max = batch_steps_max_blocks(false);
+    e->grid_forced = batch_steps_max_blocks(true);
     bool ok = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; k < cmcg_engine::kSide; ++k) {
         ok = ok && cudaStreamCreateWithFlags(&e->side[k], cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&e->join[k], cudaEventDisableTiming) == cudaSuccess;
     }
-    if (!ok || cudaStreamSynchronize(e->st) != cudaSuccess || e->grid <= 0) {
+    if (!ok || cudaStreamSynchronize(e->st) != cudaSuccess || e->grid <= 0 || e->grid_forced <= 0) {
         for (int k = 0; k < cmcg_engine::kSide; ++k) {
             if (e->side[k]) cudaStreamDestroy(e->side[k]);
             if (e->join[k]) cudaEventDestroy(e->join[k]);

@@ -83,11 +83,18 @@ struct BatchItem {
     float* buf1;  // y^{n-1} at step 0
     int order, nsteps, adjoint, zc, blocks_xy, blocks, offset;
     int vec4;  // 2D 5-point: work items are 256 aligned float4 chunks of the flat index
+    // run-up items (forced steps): FP32 source, 3D source columns, steps per period N and
+    // the run-up's steps l N; step n = s + 1 has phase omega t_n = 2 pi (n mod N) / N and
+    // ramp theta_tr(t_n) = (2 - r) r with r = sin(pi n / (2 l N))
+    const float* S;
+    const unsigned char* scol;
+    int steps_per_period, runup_steps;
 };
 bool step_vec4_ok(const Geom& g, const void* cur, const void* prev, const void* kap);
-int batch_steps_max_blocks();
+// forced: the run-up kernel (forced, ramped steps) instead of the period step loops
+int batch_steps_max_blocks(bool forced = false);
 cudaError_t launch_batch_steps(const BatchItem* items, int nitems, int total_blocks, int max_steps, unsigned* bar,
-                               int* err, int grid, cudaStream_t st);
+                               int* err, int grid, cudaStream_t st, bool forced = false);
 cudaError_t launch_barrier_selftest(unsigned* bar, int* err, long long spin_limit, cudaStream_t st);
 // Fundamental-frequency filter (Sec. 2.2) fused into a forced FP64 forward period.
 void launch_filter_init(long long n, const double* w0, const double* w1, const double* kap64, double inv_wh,

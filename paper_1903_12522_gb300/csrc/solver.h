@@ -157,6 +157,10 @@ int runup_count(const cmcg_handle* H);
 // The run-up itself: (y, y_t) at t = periods T into (w0, w1).
 template <typename T>
 void runup(cmcg_handle* H, int periods, double* w0, double* w1);
+// The FP32 run-up around a step loop run elsewhere: buffers at rest (yb = y^1, ya = y^0), then
+// after periods N - 1 steps (y, y_t) at t = periods T into (w0, w1).
+void runup_start_f32(cmcg_handle* H);
+void runup_finish_f32(cmcg_handle* H, int periods, double* w0, double* w1);
 double ramp(double t, double ttr);
 void timing_end(cmcg_handle* H, int p);
 

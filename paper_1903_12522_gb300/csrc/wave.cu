@@ -934,7 +934,8 @@ __device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, long lon
 template <int FLAGS>
 __device__ __forceinline__ void step_item3d7(const float* __restrict__ cur, float* __restrict__ prev,
                                              const float* __restrict__ kap, const Geom& g, int ix, int iy, int z0,
-                                             int z1) {
+                                             int z1, const float* __restrict__ S, float csf, float snf,
+                                             bool col_src) {
     const long long sZ = (long long)g.sx * g.sy;
     long long j = node(g, ix, iy, z0);
     const long long oxm = off_m1(ix, 1), oxp = off_p1(ix, g.nx, 1);
@@ -946,7 +947,8 @@ __device__ __forceinline__ void step_item3d7(const float* __restrict__ cur, floa
     nbxy += (iy == g.ny) & (int)((g.abc >> 3) & 1u);
     auto update = [&](float yc, float ym, float yz, long long jj, int iz, float sxy, float k, float yp) {
         const float L = 6.f * yc - (sxy + (ym + yz));
-        const float rhs = 2.f * yc - k * L;
+        float rhs = 2.f * yc - k * L;
+        if ((FLAGS & kStepSrc) && (col_src || iz == 0 || iz == g.nz)) rhs += S[2 * jj] * csf + S[2 * jj + 1] * snf;
         const int nb = nbxy + ((iz == 0) & (int)((g.abc >> 4) & 1u)) + ((iz == g.nz) & (int)((g.abc >> 5) & 1u));
         float out;
         if (nb == 0) {
@@ -983,12 +985,15 @@ __device__ __forceinline__ void step_item3d7(const float* __restrict__ cur, floa
 }
 
 // The step of one work item (block-sized piece of one solve's grid).
+// With kStepSrc (the forced steps of a run-up), S is the FP32 source and (cs, sn) the step's
+// source factors, as in the one-solve step kernels.
 template <int ORDER, int FLAGS>
 __device__ __forceinline__ void step_item(const float* __restrict__ cur, float* __restrict__ prev,
                                           const float* __restrict__ kap, const Geom& g, int zc, int bx, int bz,
-                                          int vec4) {
+                                          int vec4, const float* __restrict__ S, double cs, double sn,
+                                          const unsigned char* __restrict__ scol) {
     if (ORDER == 2 && g.dim == 2 && vec4) {  // 2D: one aligned float4 chunk of the flat index per thread
-        step_v4_chunk<2, FLAGS>(cur, prev, kap, nullptr, 0.0, 0.0, g, (long long)bx * kThreads + threadIdx.x);
+        step_v4_chunk<2, FLAGS>(cur, prev, kap, S, cs, sn, g, (long long)bx * kThreads + threadIdx.x);
         return;
     }
     const long long plane = (long long)g.sx * g.sy;
@@ -999,7 +1004,8 @@ __device__ __forceinline__ void step_item(const float* __restrict__ cur, float* 
     const int z0 = bz * zc, z1 = min(z0 + zc, g.sz);
     if (!column_in_range(g, ix, iy, z0, z1, ORDER / 2, kSiteBatch)) return;
     if (ORDER == 2 && g.dim == 3) {
-        step_item3d7<FLAGS>(cur, prev, kap, g, ix, iy, z0, z1);
+        const bool col_src = !(FLAGS & kStepSrc) || !scol || scol[ix + (long long)g.sx * iy];
+        step_item3d7<FLAGS>(cur, prev, kap, g, ix, iy, z0, z1, S, (float)cs, (float)sn, col_src);
         return;
     }
     Ld<float> f{cur};
@@ -1008,7 +1014,8 @@ __device__ __forceinline__ void step_item(const float* __restrict__ cur, float* 
         const float L = lap_t<ORDER, float>(g, f, j, ix, iy, iz);
         const float k = kap[j];
         const float yp = prev[j];
-        const float rhs = 2.f * cur[j] - k * L;
+        float rhs = 2.f * cur[j] - k * L;
+        if (FLAGS & kStepSrc) rhs += S[2 * j] * (float)cs + S[2 * j + 1] * (float)sn;
         const int nb = num_abc(g, ix, iy, iz);
         float out;
         if (nb == 0) {
@@ -1026,13 +1033,41 @@ template <int ORDER>
 __device__ __forceinline__ void step_item_flags(const float* cur, float* prev, const float* kap, const Geom& g, int zc,
                                                 int bx, int bz, int flags, int vec4) {
     switch (flags) {
-        case 0: step_item<ORDER, 0>(cur, prev, kap, g, zc, bx, bz, vec4); break;
-        case kStepPrevScaled: step_item<ORDER, kStepPrevScaled>(cur, prev, kap, g, zc, bx, bz, vec4); break;
-        case kStepNoDiv: step_item<ORDER, kStepNoDiv>(cur, prev, kap, g, zc, bx, bz, vec4); break;
-        default: step_item<ORDER, kStepPrevScaled | kStepNoDiv>(cur, prev, kap, g, zc, bx, bz, vec4); break;
+        case 0: step_item<ORDER, 0>(cur, prev, kap, g, zc, bx, bz, vec4, nullptr, 0.0, 0.0, nullptr); break;
+        case kStepPrevScaled:
+            step_item<ORDER, kStepPrevScaled>(cur, prev, kap, g, zc, bx, bz, vec4, nullptr, 0.0, 0.0, nullptr);
+            break;
+        case kStepNoDiv:
+            step_item<ORDER, kStepNoDiv>(cur, prev, kap, g, zc, bx, bz, vec4, nullptr, 0.0, 0.0, nullptr);
+            break;
+        default:
+            step_item<ORDER, kStepPrevScaled | kStepNoDiv>(cur, prev, kap, g, zc, bx, bz, vec4, nullptr, 0.0, 0.0,
+                                                           nullptr);
+            break;
     }
 }
 
+// Source factors (theta_tr(t_n) cos(omega t_n), theta_tr(t_n) sin(omega t_n)) of run-up step n
+// (Eq. transientfunction): since omega dt = 2 pi / N, the phase is 2 pi (n mod N) / N, which
+// the FP32 sin(pi x) / cos(pi x) evaluate without the large-argument reduction; the ramp
+// argument pi t_n / (2 t_tr) is pi n / (2 l N) with t_tr = l T.  The steps take these factors
+// in FP32, as they take the host's FP64 ones.
+__device__ __forceinline__ void runup_factors(int n, int N, int total, double* cs, double* sn) {
+    const int k = n % N;
+    float sw, cw;
+    sincospif(2.0f * (float)k / (float)N, &sw, &cw);
+    float th = 1.0f;
+    if (n < total) {
+        const float r = sinpif(0.5f * (float)n / (float)total);
+        th = (2.0f - r) * r;
+    }
+    *cs = (double)(th * cw);
+    *sn = (double)(th * sw);
+}
+
+// FORCED: the run-ups of several solves stepping together (steps n = s + 1 of the ramped
+// forced leapfrog from rest); otherwise homogeneous period step loops.
+template <bool FORCED>
 __global__ void __launch_bounds__(kThreads) k_batch_steps(const BatchItem* __restrict__ items, int nitems,
                                                           int total_blocks, int max_steps, unsigned* bar, int* err,
                                                           long long spin_limit) {
@@ -1050,6 +1085,15 @@ __global__ void __launch_bounds__(kThreads) k_batch_steps(const BatchItem* __res
             const int bz = lb / it.blocks_xy, bx = lb - bz * it.blocks_xy;
             const float* cur = (s & 1) ? it.buf1 : it.buf0;
             float* prev = (s & 1) ? it.buf0 : it.buf1;
+            if (FORCED) {
+                double cs, sn;
+                runup_factors(s + 1, it.steps_per_period, it.runup_steps, &cs, &sn);
+                if (it.order == 2)
+                    step_item<2, kStepSrc>(cur, prev, it.kap, it.g, it.zc, bx, bz, it.vec4, it.S, cs, sn, it.scol);
+                else
+                    step_item<4, kStepSrc>(cur, prev, it.kap, it.g, it.zc, bx, bz, 0, it.S, cs, sn, it.scol);
+                continue;
+            }
             int flags = 0;
             if (it.adjoint) {
                 if (s == 0) flags |= kStepPrevScaled;
@@ -1293,11 +1337,12 @@ template void launch_adj_start<float, float>(const Geom&, int, const float*, con
 
 namespace cmcg {
 
-int batch_steps_max_blocks() {
+int batch_steps_max_blocks(bool forced) {
     int per_sm = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_steps, kThreads, 0);
+    if (forced) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_steps<true>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_steps<false>, kThreads, 0);
     return per_sm * sms;
 }
 
@@ -1306,7 +1351,7 @@ bool step_vec4_ok(const Geom& g, const void* cur, const void* prev, const void* 
 }
 
 cudaError_t launch_batch_steps(const BatchItem* items, int nitems, int total_blocks, int max_steps, unsigned* bar,
-                               int* err, int grid, cudaStream_t st) {
+                               int* err, int grid, cudaStream_t st, bool forced) {
     note_launch(1);
     long long spin = kBarrierSpinLimit;
     void* args[] = {(void*)&items, (void*)&nitems, (void*)&total_blocks, (void*)&max_steps, (void*)&bar, (void*)&err,
@@ -1320,7 +1365,7 @@ cudaError_t launch_batch_steps(const BatchItem* items, int nitems, int total_blo
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, (const void*)k_batch_steps, args);
+    return cudaLaunchKernelExC(&cfg, forced ? (const void*)k_batch_steps<true> : (const void*)k_batch_steps<false>, args);
 }
 
 cudaError_t launch_barrier_selftest(unsigned* bar, int* err, long long spin_limit, cudaStream_t st) {
