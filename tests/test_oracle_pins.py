@@ -233,6 +233,27 @@ def test_functional_J(case):
     assert fd == pytest.approx(float(np.sum(g0 * d0) + np.sum(g1 * d1)), rel=1e-8)
 
 
+# P7b: on a box with absorbing faces only K is singular, and the periodic state is fixed only
+# up to a constant displacement (Theorem 1): (Re U, omega_hat Im U) from the direct solve is a
+# fixed point of the period map, and so is (Re U + lambda 1, omega_hat Im U) for any real
+# lambda, because a constant displacement at rest solves the homogeneous wave equation
+# (K 1 = 0, and B acts on velocities).  A constant velocity does not.  A warm start from a
+# solution field relies on the first statement.
+def test_functional_J_zero_at_the_field_without_lambda():
+    w = wl.gaussian_2d(n=12)
+    dz = make(w)
+    assert not dz.has_dirichlet
+    F = dz.load(w.f, None)
+    U = direct.solve(dz, F)
+    v0s, v1s = direct.periodic_state(dz, U)
+    J0 = wave.functional_J(dz, 0 * v0s, 0 * v1s, F)
+    assert J0 > 0
+    assert wave.functional_J(dz, v0s, v1s, F) <= 1e-22 * J0
+    assert wave.functional_J(dz, v0s + 0.37 * dz.act, v1s, F) <= 1e-22 * J0
+    # but not a constant velocity: that grows y linearly and breaks periodicity
+    assert wave.functional_J(dz, v0s, v1s + 0.37 * dz.act, F) > 1e-6 * J0
+
+
 # ----------------------------------------------------------------------------------------
 # P3: manufactured discrete plane wave U = exp(i kt x) with (2c/h) sin(kt h/2) = wt.
 # The time-discrete Helmholtz residual is zero at every interior node (closed form of the
