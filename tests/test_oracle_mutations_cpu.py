@@ -68,9 +68,41 @@ def test_flipped_damping_sign_fails_the_energy_pin(monkeypatch):
     fails(pins.test_energy_identity, False)
 
 
+def test_ramp_without_its_quadratic_factor_fails_the_ramp_pin(monkeypatch):
+    # theta = s instead of (2 - s) s: the slope at t_tr no longer vanishes
+    import math
+
+    monkeypatch.setattr(wave, "theta_tr",
+                        lambda t, t_tr: 1.0 if t >= t_tr else math.sin(0.5 * math.pi * t / t_tr))
+    fails(pins.test_theta_tr_closed_form)
+
+
+def test_boundary_rows_of_K_scaled_fail_the_eigenmode_pin(monkeypatch):
+    # a wrong lumped weight on the faces: K's rows at the boundary nodes 10 % too large
+    from oracle.grid import Discretization
+
+    orig = Discretization.K
+
+    def mutant(self, y):
+        out = orig(self, y)
+        face = np.zeros(self.shape, dtype=bool)
+        for ax in range(face.ndim):
+            idx = [slice(None)] * face.ndim
+            idx[ax] = 0
+            face[tuple(idx)] = True
+            idx[ax] = -1
+            face[tuple(idx)] = True
+        return np.where(face, 1.1 * out, out)
+
+    monkeypatch.setattr(Discretization, "K", mutant)
+    fails(pins.test_K_cosine_eigenmodes, (6, 9), 2)
+
+
 def test_the_pins_pass_unmutated():
     pins.test_functional_J("2d_mixed_faces")
     pins.test_functional_J("3d_sphere")
     pins.test_adjoint_dot_product("mixed2d")
     pins.test_adjoint_dot_product("abc2d")
     pins.test_energy_identity(False)
+    pins.test_theta_tr_closed_form()
+    pins.test_K_cosine_eigenmodes((6, 9), 2)
