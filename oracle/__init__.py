@@ -10,7 +10,7 @@ scipy.sparse on whole arrays, float64 and complex128 throughout, no blocking, no
 
 Modules
   grid     the finite-difference discretisation (mass-lumped vertex-centred analogue of the
-           paper's P1/Q1 FE with mass lumping, Sec. 4.1 and 4.4): weights W, boundary areas A,
+           paper's P1/Q1 FE with mass lumping, Sec. 4.1 and 4.3): weights W, boundary areas A,
            stiffness K, mass M, damping B, load F, period length and time step.
   wave     the leapfrog period map (velocity-Verlet form), its literal transpose, the energy
            functional J (Eq. cost_functional_J).

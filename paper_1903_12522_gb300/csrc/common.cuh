@@ -4,7 +4,7 @@
 // sz = 1.  Lumped weights W_j = h^d prod_a w(j_a) with w = 1/2 on the two end nodes of an
 // axis; the unscaled mirror Laplacian Lt(y)_j = sum_a (2 y_j - y_{j-e_a} - y_{j+e_a})
 // (2nd order) or sum_a (5/2 y_j - 4/3 (y_{j-e_a} + y_{j+e_a}) + 1/12 (y_{j-2e_a} + y_{j+2e_a}))
-// (4th order) with even reflection at the faces; K = W Lt / h^2 (Sec. 4.1/4.4 mass lumping
+// (4th order) with even reflection at the faces; K = W Lt / h^2 (Sec. 4.1/4.3 mass lumping
 // on a Cartesian grid).
 #pragma once
 

@@ -287,7 +287,7 @@ def test_filter_recovery_matches_direct(case, precision, tol, bound):
 
 @pytest.mark.parametrize("flags", [0, cmcg.FLAG_FILTER])
 def test_pure_neumann_after_runup(flags):
-    # Sec. 2.2 and 3.4: pure Neumann box (k = pi/4); from a run-up the minimiser grows
+    # Sec. 2.2 and 3.5: pure Neumann box (k = pi/4); from a run-up the minimiser grows
     # linearly (eta t).  Plain recovery removes the constant with lambda; the filter removes
     # the rest and fixes the constant by the discrete form of Eq. cc_neumann_eta
     w = wl.neumann_box_2d(40)
